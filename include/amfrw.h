@@ -1,0 +1,202 @@
+/*
+ * amfrw.h -- C ABI of the GB300 (sm_103a) AMFR-W2 sparse-grid solver for the
+ * SABR-LMM pricing PDE.
+ *
+ * Method: J.G. Lopez-Salas, S. Perez-Rodriguez, C. Vazquez, "AMFR-W numerical
+ * methods for solving high dimensional SABR/LIBOR PDE models"
+ * (arXiv 2408.00559).  The library computes, for each pricing instance:
+ *   - the component grids of the standard (eq. standardCombTechnique, psi = 0)
+ *     or modified (eq. modifiedCombTechnique, psi >= 1) combination technique,
+ *     or one full grid;
+ *   - on every grid, the finite-difference semi-discretisation of Sec. 3
+ *     (Sketch 1: central differences, Dirichlet data on the lower faces,
+ *     homogeneous Neumann conditions on the upper faces, eq. bound1);
+ *   - n_steps AMFR-W2 steps (Sec. 4.1, eqs. row-s, Wmat1, amfrw, coef_W2),
+ *     each stage made of explicit evaluations of F and the directional
+ *     tridiagonal solves of Lemma ls / Algorithm 1;
+ *   - multilinear interpolation of every grid at the spot point and the
+ *     combination sum  price = discount * sum_l c_l u_l(x*).
+ * All arithmetic runs in CUDA kernels on the device; the host only validates
+ * parameters, enumerates grids and launches.
+ *
+ * Conventions for every entry point
+ *   - Axes: the paper's F_1..F_{N-1} (forward rates) are axes 0..N-2, the
+ *     volatility V = F_N is axis N-1.  N = n_rates + 1, 2 <= N <= 8.
+ *   - Ownership: the caller owns every pointer it passes.  Inputs are copied
+ *     (to the device) before the call returns; no input pointer is retained.
+ *     Device memory the library allocates belongs to the handle that
+ *     allocated it and is released by the matching destroy call.
+ *   - Streams: cuda_stream is a cudaStream_t (NULL = legacy default stream).
+ *     Work is stream-ordered.  Calls that write host memory synchronise the
+ *     stream before returning.
+ *   - Errors: every int-returning call returns an AMFRW_* status; nothing is
+ *     thrown across the ABI.  On error, output arguments are left untouched
+ *     and *out handles are set to NULL.  amfrw_status_string() names a status
+ *     and amfrw_last_error() gives a one-line detail for the calling thread.
+ *   - Device: the current CUDA device of the calling thread at create time.
+ */
+#ifndef AMFRW_H
+#define AMFRW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AMFRW_MAX_DIM 8
+
+enum amfrw_status {
+    AMFRW_OK = 0,
+    AMFRW_EINVAL = 1,     /* invalid argument (range, NULL, non-finite input)  */
+    AMFRW_ENOTPSD = 2,    /* correlation of (F_1..F_{N-1}, V) not PSD          */
+    AMFRW_ENOMEM = 3,     /* device or host allocation failed                 */
+    AMFRW_ECUDA = 4,      /* a CUDA runtime call failed                       */
+    AMFRW_ETIMEOUT = 5,   /* reserved: a bounded device wait gave up          */
+    AMFRW_ENONFINITE = 6, /* a computed price is NaN or infinite              */
+    AMFRW_ETOOBIG = 7     /* a component grid exceeds the on-chip capacity    */
+};
+
+enum amfrw_payoff {
+    AMFRW_CAPLET = 0,   /* (F_1 - K)^+ (Sec. 2; tau and discounting via discount) */
+    AMFRW_SWAPTION = 1  /* max{sum_i tau_i (F_i - K) / prod_{l<=i}(1+tau_l F_l), 0} (Sec. 2) */
+};
+
+enum amfrw_precision {
+    AMFRW_FP64 = 0,  /* every operation in double precision                      */
+    AMFRW_MIXED = 1  /* F and the line solves in FP32; stage accumulation of Y,
+                        the evaluation of F on the payoff, interpolation and the
+                        combination sum in FP64                                 */
+};
+
+/*
+ * Problem statement of one pricing instance (Sec. 2 and Sec. 6).
+ *   n_rates   N-1 >= 1 forward rates; the PDE has N = n_rates + 1 axes.
+ *   alpha     [n_rates]  alpha_i >= 0, instantaneous volatility coefficients.
+ *   phi       [n_rates]  rate/volatility correlations phi_i in [-1, 1].
+ *   rho       [n_rates*n_rates] row-major rate correlations rho_ij, symmetric,
+ *             unit diagonal; [[rho, phi],[phi^T, 1]] must be PSD.
+ *   tau       [n_rates]  accrual fractions tau_i > 0 (drift eq. coef_adv and
+ *             swaption payoff).
+ *   F0        [n_rates]  spot forward rates, 0 <= F0_i <= Fmax_i.
+ *   Fmax      [n_rates]  upper domain bounds F_i^max > 0 (Neumann faces).
+ *   sigma     volatility of the volatility (>= 0).
+ *   beta      elasticity in [0, 1].
+ *   V0, Vmax  spot volatility and its upper bound, 0 <= V0 <= Vmax, Vmax > 0.
+ *   K, T      strike and maturity T > 0.
+ *   discount  price = discount * sum_l c_l u_l(x*)  (e.g. P(0,T_1)).
+ *   n_steps   uniform AMFR-W2 steps over [0, T] (dt = T / n_steps), >= 1.
+ *   level     combination level n >= 0 (or the full-grid level).
+ *   psi       0: standard combination; >= 1: modified combination.
+ *   full_grid nonzero: one full grid with `level` on every axis.
+ *   precision AMFRW_FP64 or AMFRW_MIXED.
+ *   theta     W-method parameter; AMFR-W2 has order 3 for (3+sqrt(3))/6.
+ *   nu_amf    AMF parameter nu > 0 of eq. (Wmat1) (the paper's nu; named so
+ *             apart from the volatility of volatility).
+ */
+typedef struct amfrw_params {
+    int32_t n_rates;
+    int32_t payoff;
+    int32_t n_steps;
+    int32_t level;
+    int32_t psi;
+    int32_t full_grid;
+    int32_t precision;
+    int32_t reserved0;
+    const double *alpha;
+    const double *phi;
+    const double *rho;
+    const double *tau;
+    const double *F0;
+    const double *Fmax;
+    double sigma;
+    double beta;
+    double V0;
+    double Vmax;
+    double K;
+    double T;
+    double discount;
+    double theta;
+    double nu_amf;
+} amfrw_params;
+
+typedef struct amfrw_problem amfrw_problem;
+typedef struct amfrw_batch amfrw_batch;
+
+/* Validate *p, enumerate its component grids, copy the parameters to the
+ * device and set every grid to the payoff (eq. icNd).  No time step is taken.
+ * Errors: EINVAL, ENOTPSD, ETOOBIG (a grid does not fit the on-chip solver),
+ * ENOMEM, ECUDA. */
+int amfrw_problem_create(const amfrw_params *p, void *cuda_stream, amfrw_problem **out);
+
+/* Advance every component grid by n_steps AMFR-W2 steps of size T/p->n_steps
+ * (eq. amfrw with eq. coef_W2), then interpolate each grid at the spot.  The
+ * grid functions stay on the device, so repeated calls continue in time.
+ * Asynchronous on the handle's stream.  Errors: EINVAL (NULL, n_steps < 0),
+ * ECUDA. */
+int amfrw_step(amfrw_problem *h, int32_t n_steps);
+
+/* price = discount * sum_l c_l u_l(x*) in FP64 in a fixed grid order
+ * (eq. standardCombTechnique / modifiedCombTechnique).  Synchronises.
+ * Errors: EINVAL, ECUDA, ENONFINITE. */
+int amfrw_combine(amfrw_problem *h, double *price_out);
+
+/* Number of component grids and the dimension N. */
+int amfrw_problem_num_grids(const amfrw_problem *h, int32_t *n_grids, int32_t *dim);
+
+/* Grid levels [n_grids * N] (log2 M_i per axis) and coefficients c_l
+ * [n_grids], in the library's grid order.  Host outputs, caller-allocated. */
+int amfrw_problem_grid_info(const amfrw_problem *h, int32_t *levels_out, double *coefs_out);
+
+/* Interpolated values u_l(x*) after the last amfrw_step [n_grids], host
+ * output.  Synchronises. */
+int amfrw_problem_grid_values(amfrw_problem *h, double *u_out);
+
+/* The grid function Y of grid `grid` on its Inner nodes (all j_i >= 1),
+ * prod_i M_i doubles in lexicographic order with axis 0 fastest (the paper's
+ * theta_1 order, Sec. 3).  Outer nodes are not returned (they hold the
+ * payoff).  Host output.  Synchronises.  Errors: EINVAL, ECUDA. */
+int amfrw_problem_read_grid(amfrw_problem *h, int32_t grid, double *Y_out);
+
+void amfrw_problem_destroy(amfrw_problem *h);
+
+/* Price n independent instances in one go: upload, one persistent launch per
+ * kernel class over all their component grids, combination, download.
+ * prices_out: host array [n].  Synchronises.  Errors as create/combine. */
+int amfrw_solve_batch(const amfrw_params *ps, int32_t n, double *prices_out, void *cuda_stream);
+
+/* The same split in two: amfrw_batch_create validates, enumerates and uploads
+ * everything once; amfrw_batch_run prices all instances with device-resident
+ * inputs and writes the prices to the DEVICE array d_prices_out [n]
+ * (asynchronous, stream-ordered; the array must stay valid until the stream
+ * reaches that point).  amfrw_batch_run may be called any number of times. */
+int amfrw_batch_create(const amfrw_params *ps, int32_t n, void *cuda_stream, amfrw_batch **out);
+int amfrw_batch_run(amfrw_batch *b, double *d_prices_out);
+/* Number of kernel launches one amfrw_batch_run issues (for accounting). */
+int amfrw_batch_launches(const amfrw_batch *b, int32_t *n_launches);
+
+/* Kernel timing (tracing).  With timing on, every amfrw_batch_run records a
+ * CUDA event pair on the batch's stream around each solver launch (one launch
+ * per (N, precision, work-group) class).  amfrw_batch_kernel_times
+ * synchronises and writes, for the last run, the device milliseconds of each
+ * solver launch to ms_out[0..*n_out-1] (at most cap entries) and the
+ * Inner-node-steps that launch advanced (sum over its grids of Inner nodes x
+ * steps) to node_steps_out (may be NULL); N of each launch goes to
+ * dims_out (may be NULL). */
+int amfrw_batch_enable_timing(amfrw_batch *b, int32_t on);
+int amfrw_batch_kernel_times(amfrw_batch *b, float *ms_out, double *node_steps_out,
+                             int32_t *dims_out, int32_t cap, int32_t *n_out);
+
+/* Bytes one amfrw_solve_batch call of this problem set copies host->device
+ * (instance records, grid list, coefficients) and device->host (prices and
+ * the non-finite flag). */
+int amfrw_batch_io_bytes(const amfrw_batch *b, int64_t *h2d_bytes, int64_t *d2h_bytes);
+void amfrw_batch_destroy(amfrw_batch *b);
+
+const char *amfrw_status_string(int status);
+const char *amfrw_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AMFRW_H */

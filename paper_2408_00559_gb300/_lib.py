@@ -1,0 +1,259 @@
+"""ctypes binding of libamfrw.so (include/amfrw.h).  Argument marshalling only:
+every step of the method runs in the library's CUDA kernels.
+
+The library is loaded from this package directory.  If it is missing the
+binding raises; there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libamfrw.so")
+
+AMFRW_OK = 0
+STATUS = {0: "AMFRW_OK", 1: "AMFRW_EINVAL", 2: "AMFRW_ENOTPSD", 3: "AMFRW_ENOMEM",
+          4: "AMFRW_ECUDA", 5: "AMFRW_ETIMEOUT", 6: "AMFRW_ENONFINITE", 7: "AMFRW_ETOOBIG"}
+PAYOFF = {"caplet": 0, "swaption": 1}
+PRECISION = {"fp64": 0, "mixed": 1}
+
+# every symbol include/amfrw.h declares
+EXPORTS = [
+    "amfrw_problem_create", "amfrw_step", "amfrw_combine", "amfrw_problem_num_grids",
+    "amfrw_problem_grid_info", "amfrw_problem_grid_values", "amfrw_problem_read_grid",
+    "amfrw_problem_destroy", "amfrw_solve_batch", "amfrw_batch_create", "amfrw_batch_run",
+    "amfrw_batch_launches", "amfrw_batch_destroy", "amfrw_status_string", "amfrw_last_error",
+    "amfrw_batch_enable_timing", "amfrw_batch_kernel_times", "amfrw_batch_io_bytes",
+]
+
+
+class AmfrwError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {detail}")
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("n_rates", C.c_int32), ("payoff", C.c_int32), ("n_steps", C.c_int32),
+        ("level", C.c_int32), ("psi", C.c_int32), ("full_grid", C.c_int32),
+        ("precision", C.c_int32), ("reserved0", C.c_int32),
+        ("alpha", C.POINTER(C.c_double)), ("phi", C.POINTER(C.c_double)),
+        ("rho", C.POINTER(C.c_double)), ("tau", C.POINTER(C.c_double)),
+        ("F0", C.POINTER(C.c_double)), ("Fmax", C.POINTER(C.c_double)),
+        ("sigma", C.c_double), ("beta", C.c_double), ("V0", C.c_double), ("Vmax", C.c_double),
+        ("K", C.c_double), ("T", C.c_double), ("discount", C.c_double), ("theta", C.c_double),
+        ("nu_amf", C.c_double),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"CUDA library {LIB_PATH} is missing; build it with "
+                "`python -m paper_2408_00559_gb300.build` (there is no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        vp = C.c_void_p
+        pp = C.POINTER(Params)
+        L.amfrw_problem_create.argtypes = [pp, vp, C.POINTER(vp)]
+        L.amfrw_step.argtypes = [vp, C.c_int32]
+        L.amfrw_combine.argtypes = [vp, C.POINTER(C.c_double)]
+        L.amfrw_problem_num_grids.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+        L.amfrw_problem_grid_info.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_double)]
+        L.amfrw_problem_grid_values.argtypes = [vp, C.POINTER(C.c_double)]
+        L.amfrw_problem_read_grid.argtypes = [vp, C.c_int32, C.POINTER(C.c_double)]
+        L.amfrw_problem_destroy.argtypes = [vp]
+        L.amfrw_problem_destroy.restype = None
+        L.amfrw_solve_batch.argtypes = [pp, C.c_int32, C.POINTER(C.c_double), vp]
+        L.amfrw_batch_create.argtypes = [pp, C.c_int32, vp, C.POINTER(vp)]
+        L.amfrw_batch_run.argtypes = [vp, vp]
+        L.amfrw_batch_launches.argtypes = [vp, C.POINTER(C.c_int32)]
+        L.amfrw_batch_destroy.argtypes = [vp]
+        L.amfrw_batch_destroy.restype = None
+        L.amfrw_batch_enable_timing.argtypes = [vp, C.c_int32]
+        L.amfrw_batch_kernel_times.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(C.c_double),
+                                               C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_int32)]
+        L.amfrw_batch_io_bytes.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+        L.amfrw_status_string.restype = C.c_char_p
+        L.amfrw_status_string.argtypes = [C.c_int]
+        L.amfrw_last_error.restype = C.c_char_p
+        L.amfrw_last_error.argtypes = []
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, where: str):
+    if rc != AMFRW_OK:
+        raise AmfrwError(rc, where, lib().amfrw_last_error().decode())
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class _Marshal:
+    """amfrw_params records for a list of instance dicts; keeps the arrays alive."""
+
+    def __init__(self, insts: list[dict]):
+        self.keep = []
+        self.arr = (Params * len(insts))()
+        for k, inst in enumerate(insts):
+            self._fill(self.arr[k], inst)
+
+    def _vec(self, x) -> np.ndarray:
+        a = np.ascontiguousarray(np.asarray(x, dtype=np.float64).ravel())
+        self.keep.append(a)
+        return a
+
+    def _fill(self, p: Params, inst: dict):
+        N = int(inst["N"])
+        p.n_rates = N - 1
+        p.payoff = PAYOFF[inst["payoff"]]
+        p.n_steps = int(inst["n_steps"])
+        p.level = int(inst["level"])
+        p.psi = int(inst.get("psi", 0))
+        p.full_grid = int(bool(inst.get("full", False)))
+        p.precision = PRECISION[inst.get("precision", "fp64")]
+        for name in ("alpha", "phi", "tau", "F0", "Fmax"):
+            setattr(p, name, _dp(self._vec(inst[name])))
+        p.rho = _dp(self._vec(inst["rho"]))
+        p.sigma = float(inst["sigma"])
+        p.beta = float(inst["beta"])
+        p.V0 = float(inst["V0"])
+        p.Vmax = float(inst["Vmax"])
+        p.K = float(inst["K"])
+        p.T = float(inst["T"])
+        p.discount = float(inst.get("discount", 1.0))
+        p.theta = float(inst["theta"])
+        p.nu_amf = float(inst["nu"])
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return int(torch.cuda.current_stream().cuda_stream)
+        except Exception:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+class Problem:
+    """amfrw_problem: one instance, stepped in time, state kept on the device."""
+
+    def __init__(self, inst: dict, stream=None):
+        self._m = _Marshal([inst])
+        self.h = C.c_void_p()
+        _check(lib().amfrw_problem_create(self._m.arr, _stream_ptr(stream), C.byref(self.h)),
+               "amfrw_problem_create")
+        ng, dim = C.c_int32(), C.c_int32()
+        _check(lib().amfrw_problem_num_grids(self.h, C.byref(ng), C.byref(dim)),
+               "amfrw_problem_num_grids")
+        self.n_grids, self.dim = ng.value, dim.value
+
+    def step(self, n_steps: int):
+        _check(lib().amfrw_step(self.h, int(n_steps)), "amfrw_step")
+
+    def combine(self) -> float:
+        v = C.c_double()
+        _check(lib().amfrw_combine(self.h, C.byref(v)), "amfrw_combine")
+        return v.value
+
+    def grid_info(self):
+        lv = np.zeros((self.n_grids, self.dim), dtype=np.int32)
+        cf = np.zeros(self.n_grids)
+        _check(lib().amfrw_problem_grid_info(self.h, lv.ctypes.data_as(C.POINTER(C.c_int32)), _dp(cf)),
+               "amfrw_problem_grid_info")
+        return lv, cf
+
+    def grid_values(self) -> np.ndarray:
+        u = np.zeros(self.n_grids)
+        _check(lib().amfrw_problem_grid_values(self.h, _dp(u)), "amfrw_problem_grid_values")
+        return u
+
+    def read_grid(self, g: int, levels) -> np.ndarray:
+        L = int(np.prod([1 << int(x) for x in levels]))
+        Y = np.zeros(L)
+        _check(lib().amfrw_problem_read_grid(self.h, int(g), _dp(Y)), "amfrw_problem_read_grid")
+        return Y
+
+    def close(self):
+        if self.h:
+            lib().amfrw_problem_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve_batch(insts: list[dict], stream=None) -> np.ndarray:
+    """amfrw_solve_batch: host params in, host prices out."""
+    m = _Marshal(insts)
+    out = np.zeros(len(insts))
+    _check(lib().amfrw_solve_batch(m.arr, len(insts), _dp(out), _stream_ptr(stream)),
+           "amfrw_solve_batch")
+    return out
+
+
+class Batch:
+    """amfrw_batch: inputs uploaded once, run() prices into a device array."""
+
+    def __init__(self, insts: list[dict], stream=None):
+        self._m = _Marshal(insts)
+        self.n = len(insts)
+        self.h = C.c_void_p()
+        _check(lib().amfrw_batch_create(self._m.arr, self.n, _stream_ptr(stream), C.byref(self.h)),
+               "amfrw_batch_create")
+
+    def run(self, d_prices_ptr: int):
+        _check(lib().amfrw_batch_run(self.h, C.c_void_p(int(d_prices_ptr))), "amfrw_batch_run")
+
+    def launches(self) -> int:
+        n = C.c_int32()
+        _check(lib().amfrw_batch_launches(self.h, C.byref(n)), "amfrw_batch_launches")
+        return n.value
+
+    def enable_timing(self, on: bool = True):
+        _check(lib().amfrw_batch_enable_timing(self.h, int(bool(on))), "amfrw_batch_enable_timing")
+
+    def kernel_times(self):
+        """[(N, device ms, Inner-node-steps)] of each solver launch of the last run."""
+        cap = 64
+        ms = (C.c_float * cap)()
+        ns = (C.c_double * cap)()
+        dims = (C.c_int32 * cap)()
+        n = C.c_int32()
+        _check(lib().amfrw_batch_kernel_times(self.h, ms, ns, dims, cap, C.byref(n)),
+               "amfrw_batch_kernel_times")
+        return [(dims[i], ms[i], ns[i]) for i in range(n.value)]
+
+    def io_bytes(self):
+        h2d, d2h = C.c_int64(), C.c_int64()
+        _check(lib().amfrw_batch_io_bytes(self.h, C.byref(h2d), C.byref(d2h)), "amfrw_batch_io_bytes")
+        return h2d.value, d2h.value
+
+    def close(self):
+        if self.h:
+            lib().amfrw_batch_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

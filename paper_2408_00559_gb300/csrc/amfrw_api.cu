@@ -1,0 +1,700 @@
+// Host side of the C ABI declared in include/amfrw.h: parameter validation,
+// component-grid enumeration, work partitioning, device buffers and launches.
+// No arithmetic of the method runs here; it all runs in the kernels.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/amfrw.h"
+#include "amfrw_internal.h"
+
+using namespace amfrw;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int status, const std::string& msg)
+{
+    g_last_error = msg;
+    return status;
+}
+
+#define CUDA_TRY(expr)                                                                   \
+    do {                                                                                 \
+        cudaError_t e_ = (expr);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(AMFRW_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+constexpr int kWarpMaxL = 256;         // grids up to this many Inner nodes: one warp each
+constexpr int kWarpsPerBlock = 4;
+
+bool finite(double x) { return std::isfinite(x); }
+
+// Smallest eigenvalue check of the joint correlation of (F_1..F_{N-1}, V) by a
+// Cholesky factorisation with a small tolerance (PSD, not only PD).
+bool joint_correlation_psd(int nr, const double* rho, const double* phi)
+{
+    const int n = nr + 1;
+    std::vector<double> A(n * n), Lc(n * n, 0.0);
+    for (int i = 0; i < nr; ++i)
+        for (int k = 0; k < nr; ++k) A[i * n + k] = rho[i * nr + k];
+    for (int i = 0; i < nr; ++i) {
+        A[i * n + nr] = phi[i];
+        A[nr * n + i] = phi[i];
+    }
+    A[nr * n + nr] = 1.0;
+    const double tol = 1e-10;
+    for (int j = 0; j < n; ++j) {
+        double d = A[j * n + j];
+        for (int k = 0; k < j; ++k) d -= Lc[j * n + k] * Lc[j * n + k];
+        if (d < -tol) return false;
+        const double ljj = d > 0.0 ? std::sqrt(d) : 0.0;
+        Lc[j * n + j] = ljj;
+        for (int i = j + 1; i < n; ++i) {
+            double v = A[i * n + j];
+            for (int k = 0; k < j; ++k) v -= Lc[i * n + k] * Lc[j * n + k];
+            if (ljj > 0.0) {
+                Lc[i * n + j] = v / ljj;
+            } else if (std::fabs(v) > tol) {
+                return false;  // zero pivot with a non-zero remainder: not PSD
+            }
+        }
+    }
+    return true;
+}
+
+int validate(const amfrw_params* p)
+{
+    if (!p) return fail(AMFRW_EINVAL, "params is NULL");
+    const int nr = p->n_rates;
+    if (nr < 1 || nr > kMaxDim - 1) return fail(AMFRW_EINVAL, "n_rates must be in [1, 7]");
+    if (!p->alpha || !p->phi || !p->rho || !p->tau || !p->F0 || !p->Fmax)
+        return fail(AMFRW_EINVAL, "a parameter array is NULL");
+    if (p->payoff != AMFRW_CAPLET && p->payoff != AMFRW_SWAPTION)
+        return fail(AMFRW_EINVAL, "unknown payoff");
+    if (p->precision != AMFRW_FP64 && p->precision != AMFRW_MIXED)
+        return fail(AMFRW_EINVAL, "unknown precision");
+    if (p->n_steps < 1) return fail(AMFRW_EINVAL, "n_steps must be >= 1");
+    if (p->level < 0 || p->psi < 0) return fail(AMFRW_EINVAL, "level and psi must be >= 0");
+    const double sc[] = {p->sigma, p->beta, p->V0, p->Vmax, p->K, p->T, p->discount, p->theta, p->nu_amf};
+    for (double v : sc)
+        if (!finite(v)) return fail(AMFRW_EINVAL, "a scalar parameter is not finite");
+    if (p->sigma < 0.0) return fail(AMFRW_EINVAL, "sigma must be >= 0");
+    if (p->beta < 0.0 || p->beta > 1.0) return fail(AMFRW_EINVAL, "beta must be in [0, 1]");
+    if (!(p->Vmax > 0.0) || p->V0 < 0.0 || p->V0 > p->Vmax)
+        return fail(AMFRW_EINVAL, "need 0 <= V0 <= Vmax and Vmax > 0");
+    if (!(p->T > 0.0)) return fail(AMFRW_EINVAL, "T must be > 0");
+    if (!(p->theta > 0.0) || !(p->nu_amf > 0.0)) return fail(AMFRW_EINVAL, "theta and nu_amf must be > 0");
+    for (int i = 0; i < nr; ++i) {
+        if (!finite(p->alpha[i]) || !finite(p->phi[i]) || !finite(p->tau[i]) || !finite(p->F0[i]) ||
+            !finite(p->Fmax[i]))
+            return fail(AMFRW_EINVAL, "a per-rate parameter is not finite");
+        if (p->alpha[i] < 0.0) return fail(AMFRW_EINVAL, "alpha_i must be >= 0");
+        if (!(p->tau[i] > 0.0)) return fail(AMFRW_EINVAL, "tau_i must be > 0");
+        if (!(p->Fmax[i] > 0.0) || p->F0[i] < 0.0 || p->F0[i] > p->Fmax[i])
+            return fail(AMFRW_EINVAL, "need 0 <= F0_i <= Fmax_i and Fmax_i > 0");
+        if (p->phi[i] < -1.0 || p->phi[i] > 1.0) return fail(AMFRW_EINVAL, "phi_i must be in [-1, 1]");
+        for (int k = 0; k < nr; ++k) {
+            const double r = p->rho[i * nr + k];
+            if (!finite(r)) return fail(AMFRW_EINVAL, "rho is not finite");
+            if (std::fabs(r - p->rho[k * nr + i]) > 1e-12) return fail(AMFRW_EINVAL, "rho is not symmetric");
+        }
+        if (std::fabs(p->rho[i * nr + i] - 1.0) > 1e-12) return fail(AMFRW_EINVAL, "rho must have a unit diagonal");
+    }
+    if (!joint_correlation_psd(nr, p->rho, p->phi))
+        return fail(AMFRW_ENOTPSD, "correlation of (F_1..F_{N-1}, V) is not positive semi-definite");
+    return AMFRW_OK;
+}
+
+struct GridSpec {
+    int8_t lv[kMaxDim];
+    double coef;
+};
+
+// Component grids of the combination technique: every composition l of
+// n - q into d non-negative parts for q = 0..d-1, coefficient (-1)^q C(d-1,q),
+// levels psi + l_i; or the single full grid.  Order: q ascending, then the
+// compositions with the last axis varying slowest.
+void compositions(int d, int m, int axis, int8_t* cur, int psi, double coef, std::vector<GridSpec>& out)
+{
+    if (axis == d - 1) {
+        cur[axis] = (int8_t)(psi + m);
+        GridSpec g{};
+        memcpy(g.lv, cur, sizeof(g.lv));
+        g.coef = coef;
+        out.push_back(g);
+        return;
+    }
+    for (int v = 0; v <= m; ++v) {
+        cur[axis] = (int8_t)(psi + v);
+        compositions(d, m - v, axis + 1, cur, psi, coef, out);
+    }
+}
+
+std::vector<GridSpec> enumerate(int d, int n, int psi, bool full)
+{
+    std::vector<GridSpec> out;
+    if (full) {
+        GridSpec g{};
+        for (int i = 0; i < d; ++i) g.lv[i] = (int8_t)n;
+        g.coef = 1.0;
+        out.push_back(g);
+        return out;
+    }
+    int8_t cur[kMaxDim] = {0};
+    double binom = 1.0;  // C(d-1, q)
+    for (int q = 0; q < d; ++q) {
+        if (q > 0) binom = binom * (double)(d - q) / (double)q;
+        if (n - q < 0) break;
+        compositions(d, n - q, 0, cur, psi, (q & 1 ? -1.0 : 1.0) * binom, out);
+    }
+    return out;
+}
+
+InstDev to_device(const amfrw_params* p)
+{
+    InstDev I;
+    memset(&I, 0, sizeof(I));
+    const int nr = p->n_rates;
+    I.N = nr + 1;
+    I.payoff = p->payoff;
+    I.n_steps = p->n_steps;
+    I.precision = p->precision;
+    for (int i = 0; i < nr; ++i) {
+        I.alpha[i] = p->alpha[i];
+        I.phi[i] = p->phi[i];
+        I.tau[i] = p->tau[i];
+        I.F0[i] = p->F0[i];
+        I.Fmax[i] = p->Fmax[i];
+        for (int k = 0; k < nr; ++k) I.rho[i * kMaxDim + k] = p->rho[i * nr + k];
+    }
+    I.Fmax[nr] = p->Vmax;
+    I.sigma = p->sigma;
+    I.beta = p->beta;
+    I.V0 = p->V0;
+    I.K = p->K;
+    I.T = p->T;
+    I.discount = p->discount;
+    I.theta = p->theta;
+    I.nu = p->nu_amf;
+    I.dt = p->T / (double)p->n_steps;
+    return I;
+}
+
+LaunchFn launch_for(int N)
+{
+    static const LaunchFn t[] = {nullptr, nullptr, launch_n2, launch_n3, launch_n4,
+                                 launch_n5, launch_n6, launch_n7, launch_n8};
+    return t[N];
+}
+OccFn occ_for(int N)
+{
+    static const OccFn t[] = {nullptr, nullptr, occupancy_n2, occupancy_n3, occupancy_n4,
+                              occupancy_n5, occupancy_n6, occupancy_n7, occupancy_n8};
+    return t[N];
+}
+
+int max_smem_optin()
+{
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return v > 0 ? v : 232448;
+}
+int num_sms()
+{
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
+}
+
+// One launch: all grids of one (N, precision, group kind).
+struct LaunchClass {
+    int N;
+    bool mixed, warp;
+    int item_begin, item_count;
+    int block, grid;
+    size_t smem;
+    int smem_group;
+    int64_t lu_stride;   // bytes of Thomas factors per block (CTA groups)
+    int64_t lu_offset;   // this class's part of the plan's scratch array
+};
+
+struct Plan {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int n_inst = 0, n_grids = 0, dim = 0;
+    std::vector<InstDev> insts;
+    std::vector<Item> items;          // grouped by launch class, largest grids first
+    std::vector<double> coefs;        // per grid, instance order
+    std::vector<int8_t> levels;       // per grid (dim = 8 each), instance order
+    std::vector<LaunchClass> classes;
+    // device
+    InstDev* d_insts = nullptr;
+    Item* d_items = nullptr;
+    double* d_coefs = nullptr;
+    double* d_u = nullptr;
+    double* d_prices = nullptr;
+    int32_t* d_queue = nullptr;
+    int32_t* d_flag = nullptr;
+    double* d_state = nullptr;
+    int64_t state_len = 0;
+    unsigned char* d_lu = nullptr;   // scratch: Thomas factors of CTA-group grids
+    int64_t lu_scratch_len = 0;
+
+    ~Plan() { release(); }
+    void release()
+    {
+        cudaFree(d_insts);
+        cudaFree(d_items);
+        cudaFree(d_coefs);
+        cudaFree(d_u);
+        cudaFree(d_prices);
+        cudaFree(d_queue);
+        cudaFree(d_flag);
+        cudaFree(d_state);
+        cudaFree(d_lu);
+        d_lu = nullptr;
+        d_insts = nullptr; d_items = nullptr; d_coefs = nullptr; d_u = nullptr;
+        d_prices = nullptr; d_queue = nullptr; d_flag = nullptr; d_state = nullptr;
+    }
+};
+
+int build_plan(const amfrw_params* ps, int n, void* stream, bool keep_state, Plan& P)
+{
+    if (n < 1) return fail(AMFRW_EINVAL, "need at least one instance");
+    if (!ps) return fail(AMFRW_EINVAL, "params is NULL");
+    // every instance is validated before any CUDA call
+    for (int i = 0; i < n; ++i) {
+        int st = validate(ps + i);
+        if (st != AMFRW_OK) {
+            g_last_error = "instance " + std::to_string(i) + ": " + g_last_error;
+            return st;
+        }
+        const amfrw_params* p = ps + i;
+        std::vector<GridSpec> grids = enumerate(p->n_rates + 1, p->level, p->psi, p->full_grid != 0);
+        for (const GridSpec& g : grids) {
+            int sumlv = 0;
+            for (int a = 0; a <= p->n_rates; ++a) sumlv += g.lv[a];
+            if (sumlv > 20)
+                return fail(AMFRW_ETOOBIG, "instance " + std::to_string(i) +
+                                               ": a component grid has more than 2^20 Inner nodes");
+        }
+    }
+    CUDA_TRY(cudaGetDevice(&P.device));
+    P.stream = (cudaStream_t)stream;
+    P.n_inst = n;
+    const int smem_cap = max_smem_optin();
+    struct Tmp { Item it; int L; int N; bool mixed; bool warp; int smem_group; int64_t lu_bytes; };
+    std::vector<Tmp> all;
+    int64_t state_off = 0;
+    for (int i = 0; i < n; ++i) {
+        const amfrw_params* p = ps + i;
+        InstDev I = to_device(p);
+        const int N = I.N;
+        const bool mixed = p->precision == AMFRW_MIXED;
+        std::vector<GridSpec> grids = enumerate(N, p->level, p->psi, p->full_grid != 0);
+        I.grid_begin = (int32_t)P.coefs.size();
+        I.grid_count = (int32_t)grids.size();
+        for (const GridSpec& g : grids) {
+            int Lg = 1;
+            for (int a = 0; a < N; ++a) Lg <<= g.lv[a];
+            const bool warp = Lg <= kWarpMaxL;
+            Layout lay = make_layout(N, g.lv, mixed, warp);
+            if (lay.total > smem_cap)
+                return fail(AMFRW_ETOOBIG, "component grid with " + std::to_string(lay.L) +
+                                               " Inner nodes needs " + std::to_string(lay.total) +
+                                               " bytes of shared memory (limit " +
+                                               std::to_string(smem_cap) + ")");
+            Tmp t{};
+            t.it.inst = i;
+            t.it.out_idx = (int32_t)P.coefs.size();
+            t.it.L = lay.L;
+            memcpy(t.it.lv, g.lv, sizeof(t.it.lv));
+            t.it.state_off = keep_state ? state_off : -1;
+            if (keep_state) state_off += lay.L;
+            t.L = lay.L;
+            t.N = N;
+            t.mixed = mixed;
+            t.warp = warp;
+            t.smem_group = lay.total;
+            t.lu_bytes = warp ? 0 : (int64_t)lay.nlu * (mixed ? 4 : 8);
+            all.push_back(t);
+            P.coefs.push_back(g.coef);
+            for (int a = 0; a < kMaxDim; ++a) P.levels.push_back(a < N ? g.lv[a] : 0);
+        }
+        P.insts.push_back(I);
+        P.dim = N;
+    }
+    P.n_grids = (int)P.coefs.size();
+    P.state_len = state_off;
+    // group by launch class, largest grids first within a class (LPT order)
+    std::stable_sort(all.begin(), all.end(), [](const Tmp& a, const Tmp& b) {
+        return std::make_tuple(a.N, a.mixed, a.warp, -a.L) < std::make_tuple(b.N, b.mixed, b.warp, -b.L);
+    });
+    const int sms = num_sms();
+    for (size_t k = 0; k < all.size();) {
+        size_t e = k;
+        int gmax = 0, lmax = 0;
+        int64_t lumax = 0;
+        while (e < all.size() && all[e].N == all[k].N && all[e].mixed == all[k].mixed &&
+               all[e].warp == all[k].warp) {
+            gmax = std::max(gmax, all[e].smem_group);
+            lmax = std::max(lmax, all[e].L);
+            lumax = std::max(lumax, all[e].lu_bytes);
+            ++e;
+        }
+        LaunchClass c{};
+        c.N = all[k].N;
+        c.mixed = all[k].mixed;
+        c.warp = all[k].warp;
+        c.item_begin = (int)P.items.size();
+        c.item_count = (int)(e - k);
+        c.smem_group = gmax;
+        if (c.warp) {
+            int wpb = std::min(kWarpsPerBlock, std::max(1, smem_cap / gmax));
+            c.block = 32 * wpb;
+            c.smem = (size_t)gmax * wpb;
+        } else {
+            int b = 64;
+            while (b < 512 && b * 8 < lmax) b *= 2;
+            c.block = b;
+            c.smem = (size_t)gmax;
+        }
+        const int per_sm = occ_for(c.N)(c.mixed, c.warp, c.block, c.smem);
+        if (per_sm < 1)
+            return fail(AMFRW_ETOOBIG, "no resident block possible for a launch class (shared memory " +
+                                           std::to_string(c.smem) + " bytes)");
+        const int groups_per_block = c.warp ? c.block / 32 : 1;
+        const int need = (c.item_count + groups_per_block - 1) / groups_per_block;
+        c.grid = std::max(1, std::min(need, per_sm * sms));
+        c.lu_stride = (lumax + 255) & ~(int64_t)255;
+        c.lu_offset = P.lu_scratch_len;
+        P.lu_scratch_len += c.lu_stride * c.grid;
+        for (size_t q = k; q < e; ++q) P.items.push_back(all[q].it);
+        P.classes.push_back(c);
+        k = e;
+    }
+    // device buffers
+    CUDA_TRY(cudaMalloc(&P.d_insts, sizeof(InstDev) * P.insts.size()));
+    CUDA_TRY(cudaMalloc(&P.d_items, sizeof(Item) * P.items.size()));
+    CUDA_TRY(cudaMalloc(&P.d_coefs, sizeof(double) * P.coefs.size()));
+    CUDA_TRY(cudaMalloc(&P.d_u, sizeof(double) * P.coefs.size()));
+    CUDA_TRY(cudaMalloc(&P.d_prices, sizeof(double) * P.n_inst));
+    CUDA_TRY(cudaMalloc(&P.d_queue, sizeof(int32_t) * std::max<size_t>(1, P.classes.size())));
+    CUDA_TRY(cudaMalloc(&P.d_flag, sizeof(int32_t)));
+    if (keep_state) CUDA_TRY(cudaMalloc(&P.d_state, sizeof(double) * std::max<int64_t>(1, P.state_len)));
+    if (P.lu_scratch_len > 0) CUDA_TRY(cudaMalloc(&P.d_lu, (size_t)P.lu_scratch_len));
+    CUDA_TRY(cudaMemcpyAsync(P.d_insts, P.insts.data(), sizeof(InstDev) * P.insts.size(),
+                             cudaMemcpyHostToDevice, P.stream));
+    CUDA_TRY(cudaMemcpyAsync(P.d_items, P.items.data(), sizeof(Item) * P.items.size(),
+                             cudaMemcpyHostToDevice, P.stream));
+    CUDA_TRY(cudaMemcpyAsync(P.d_coefs, P.coefs.data(), sizeof(double) * P.coefs.size(),
+                             cudaMemcpyHostToDevice, P.stream));
+    CUDA_TRY(cudaMemsetAsync(P.d_u, 0, sizeof(double) * P.coefs.size(), P.stream));
+    return AMFRW_OK;
+}
+
+__global__ void combine_kernel(const InstDev* __restrict__ insts, int n, const double* __restrict__ coefs,
+                               const double* __restrict__ u, double* __restrict__ prices,
+                               int32_t* __restrict__ nonfinite)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const InstDev& I = insts[i];
+    double s = 0.0;
+    for (int k = I.grid_begin; k < I.grid_begin + I.grid_count; ++k) s += coefs[k] * u[k];
+    const double p = I.discount * s;
+    prices[i] = p;
+    if (!isfinite(p)) atomicOr(nonfinite, 1);
+}
+
+// Solve launches for every class.  steps < 0: each instance's own n_steps.
+int run_solve(Plan& P, int steps, int flags, cudaEvent_t* ev = nullptr)
+{
+    CUDA_TRY(cudaMemsetAsync(P.d_queue, 0, sizeof(int32_t) * P.classes.size(), P.stream));
+    for (size_t c = 0; c < P.classes.size(); ++c) {
+        const LaunchClass& L = P.classes[c];
+        SolveArgs a{};
+        a.items = P.d_items + L.item_begin;
+        a.n_items = L.item_count;
+        a.steps = steps;
+        a.flags = flags;
+        a.smem_group = L.smem_group;
+        a.insts = P.d_insts;
+        a.u_out = P.d_u;
+        a.state = P.d_state;
+        a.queue = P.d_queue + c;
+        a.lu_scratch = P.d_lu ? P.d_lu + L.lu_offset : nullptr;
+        a.lu_stride = L.lu_stride;
+        if (ev) CUDA_TRY(cudaEventRecord(ev[2 * c], P.stream));
+        const int rc = launch_for(L.N)(a, L.mixed, L.warp, L.block, L.grid, L.smem, P.stream);
+        if (ev) CUDA_TRY(cudaEventRecord(ev[2 * c + 1], P.stream));
+        if (rc != 0) return fail(AMFRW_ECUDA, std::string("solver launch: ") + cudaGetErrorString((cudaError_t)rc));
+    }
+    return AMFRW_OK;
+}
+
+int run_combine(Plan& P, double* d_out)
+{
+    CUDA_TRY(cudaMemsetAsync(P.d_flag, 0, sizeof(int32_t), P.stream));
+    const int b = 128;
+    combine_kernel<<<(P.n_inst + b - 1) / b, b, 0, P.stream>>>(P.d_insts, P.n_inst, P.d_coefs, P.d_u,
+                                                               d_out, P.d_flag);
+    CUDA_TRY(cudaGetLastError());
+    return AMFRW_OK;
+}
+
+int all_same_steps(const Plan& P)
+{
+    int s = P.insts[0].n_steps;
+    for (const InstDev& I : P.insts)
+        if (I.n_steps != s) return -1;
+    return s;
+}
+
+}  // namespace
+
+struct amfrw_problem {
+    Plan plan;
+    int steps_done = 0;
+};
+
+struct amfrw_batch {
+    Plan plan;
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;   // two per solver launch
+    ~amfrw_batch()
+    {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+};
+
+extern "C" {
+
+const char* amfrw_status_string(int status)
+{
+    switch (status) {
+        case AMFRW_OK: return "AMFRW_OK";
+        case AMFRW_EINVAL: return "AMFRW_EINVAL";
+        case AMFRW_ENOTPSD: return "AMFRW_ENOTPSD";
+        case AMFRW_ENOMEM: return "AMFRW_ENOMEM";
+        case AMFRW_ECUDA: return "AMFRW_ECUDA";
+        case AMFRW_ETIMEOUT: return "AMFRW_ETIMEOUT";
+        case AMFRW_ENONFINITE: return "AMFRW_ENONFINITE";
+        case AMFRW_ETOOBIG: return "AMFRW_ETOOBIG";
+        default: return "AMFRW_UNKNOWN";
+    }
+}
+
+const char* amfrw_last_error(void) { return g_last_error.c_str(); }
+
+int amfrw_problem_create(const amfrw_params* p, void* cuda_stream, amfrw_problem** out)
+{
+    if (!out) return fail(AMFRW_EINVAL, "out is NULL");
+    *out = nullptr;
+    amfrw_problem* h = new (std::nothrow) amfrw_problem();
+    if (!h) return fail(AMFRW_ENOMEM, "host allocation failed");
+    int st = build_plan(p, 1, cuda_stream, true, h->plan);
+    if (st != AMFRW_OK) {
+        delete h;
+        return st;
+    }
+    // state = payoff: zero steps with a store writes Y = G on every grid
+    st = run_solve(h->plan, 0, kStoreState);
+    if (st != AMFRW_OK) {
+        delete h;
+        return st;
+    }
+    *out = h;
+    return AMFRW_OK;
+}
+
+int amfrw_step(amfrw_problem* h, int32_t n_steps)
+{
+    if (!h) return fail(AMFRW_EINVAL, "handle is NULL");
+    if (n_steps < 0) return fail(AMFRW_EINVAL, "n_steps must be >= 0");
+    int st = run_solve(h->plan, n_steps, kLoadState | kStoreState);
+    if (st == AMFRW_OK) h->steps_done += n_steps;
+    return st;
+}
+
+int amfrw_combine(amfrw_problem* h, double* price_out)
+{
+    if (!h || !price_out) return fail(AMFRW_EINVAL, "NULL argument");
+    Plan& P = h->plan;
+    int st = run_combine(P, P.d_prices);
+    if (st != AMFRW_OK) return st;
+    double v = 0.0;
+    int32_t flag = 0;
+    CUDA_TRY(cudaMemcpyAsync(&v, P.d_prices, sizeof(double), cudaMemcpyDeviceToHost, P.stream));
+    CUDA_TRY(cudaMemcpyAsync(&flag, P.d_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, P.stream));
+    CUDA_TRY(cudaStreamSynchronize(P.stream));
+    if (flag) return fail(AMFRW_ENONFINITE, "the combined price is not finite");
+    *price_out = v;
+    return AMFRW_OK;
+}
+
+int amfrw_problem_num_grids(const amfrw_problem* h, int32_t* n_grids, int32_t* dim)
+{
+    if (!h || !n_grids || !dim) return fail(AMFRW_EINVAL, "NULL argument");
+    *n_grids = h->plan.n_grids;
+    *dim = h->plan.dim;
+    return AMFRW_OK;
+}
+
+int amfrw_problem_grid_info(const amfrw_problem* h, int32_t* levels_out, double* coefs_out)
+{
+    if (!h) return fail(AMFRW_EINVAL, "handle is NULL");
+    const Plan& P = h->plan;
+    for (int g = 0; g < P.n_grids; ++g) {
+        if (levels_out)
+            for (int a = 0; a < P.dim; ++a) levels_out[g * P.dim + a] = P.levels[g * kMaxDim + a];
+        if (coefs_out) coefs_out[g] = P.coefs[g];
+    }
+    return AMFRW_OK;
+}
+
+int amfrw_problem_grid_values(amfrw_problem* h, double* u_out)
+{
+    if (!h || !u_out) return fail(AMFRW_EINVAL, "NULL argument");
+    Plan& P = h->plan;
+    CUDA_TRY(cudaMemcpyAsync(u_out, P.d_u, sizeof(double) * P.n_grids, cudaMemcpyDeviceToHost, P.stream));
+    CUDA_TRY(cudaStreamSynchronize(P.stream));
+    return AMFRW_OK;
+}
+
+int amfrw_problem_read_grid(amfrw_problem* h, int32_t grid, double* Y_out)
+{
+    if (!h || !Y_out) return fail(AMFRW_EINVAL, "NULL argument");
+    Plan& P = h->plan;
+    if (grid < 0 || grid >= P.n_grids) return fail(AMFRW_EINVAL, "grid index out of range");
+    int64_t off = -1, L = 0;
+    for (const Item& it : P.items)
+        if (it.out_idx == grid) {
+            off = it.state_off;
+            L = it.L;
+        }
+    if (off < 0) return fail(AMFRW_EINVAL, "grid has no stored state");
+    CUDA_TRY(cudaMemcpyAsync(Y_out, P.d_state + off, sizeof(double) * L, cudaMemcpyDeviceToHost, P.stream));
+    CUDA_TRY(cudaStreamSynchronize(P.stream));
+    return AMFRW_OK;
+}
+
+void amfrw_problem_destroy(amfrw_problem* h) { delete h; }
+
+int amfrw_batch_create(const amfrw_params* ps, int32_t n, void* cuda_stream, amfrw_batch** out)
+{
+    if (!out) return fail(AMFRW_EINVAL, "out is NULL");
+    *out = nullptr;
+    amfrw_batch* b = new (std::nothrow) amfrw_batch();
+    if (!b) return fail(AMFRW_ENOMEM, "host allocation failed");
+    int st = build_plan(ps, n, cuda_stream, false, b->plan);
+    if (st != AMFRW_OK) {
+        delete b;
+        return st;
+    }
+    if (all_same_steps(b->plan) < 0) {
+        delete b;
+        return fail(AMFRW_EINVAL, "all instances of a batch must use the same n_steps");
+    }
+    *out = b;
+    return AMFRW_OK;
+}
+
+int amfrw_batch_run(amfrw_batch* b, double* d_prices_out)
+{
+    if (!b || !d_prices_out) return fail(AMFRW_EINVAL, "NULL argument");
+    Plan& P = b->plan;
+    int st = run_solve(P, P.insts[0].n_steps, 0, b->timing ? b->ev.data() : nullptr);
+    if (st != AMFRW_OK) return st;
+    return run_combine(P, d_prices_out);
+}
+
+int amfrw_batch_enable_timing(amfrw_batch* b, int32_t on)
+{
+    if (!b) return fail(AMFRW_EINVAL, "NULL argument");
+    if (on && b->ev.empty()) {
+        b->ev.resize(2 * b->plan.classes.size());
+        for (cudaEvent_t& e : b->ev) CUDA_TRY(cudaEventCreate(&e));
+    }
+    b->timing = on != 0;
+    return AMFRW_OK;
+}
+
+int amfrw_batch_kernel_times(amfrw_batch* b, float* ms_out, double* node_steps_out, int32_t* dims_out,
+                             int32_t cap, int32_t* n_out)
+{
+    if (!b || !ms_out || !n_out) return fail(AMFRW_EINVAL, "NULL argument");
+    if (b->ev.empty()) return fail(AMFRW_EINVAL, "timing is not enabled");
+    const Plan& P = b->plan;
+    const int n = std::min<int>(cap, (int)P.classes.size());
+    for (int c = 0; c < n; ++c) {
+        CUDA_TRY(cudaEventSynchronize(b->ev[2 * c + 1]));
+        CUDA_TRY(cudaEventElapsedTime(&ms_out[c], b->ev[2 * c], b->ev[2 * c + 1]));
+        const LaunchClass& L = P.classes[c];
+        if (node_steps_out) {
+            double s = 0.0;
+            for (int k = L.item_begin; k < L.item_begin + L.item_count; ++k)
+                s += (double)P.items[k].L * (double)P.insts[P.items[k].inst].n_steps;
+            node_steps_out[c] = s;
+        }
+        if (dims_out) dims_out[c] = L.N;
+    }
+    *n_out = n;
+    return AMFRW_OK;
+}
+
+int amfrw_batch_io_bytes(const amfrw_batch* b, int64_t* h2d_bytes, int64_t* d2h_bytes)
+{
+    if (!b || !h2d_bytes || !d2h_bytes) return fail(AMFRW_EINVAL, "NULL argument");
+    const Plan& P = b->plan;
+    *h2d_bytes = (int64_t)(sizeof(InstDev) * P.insts.size() + sizeof(Item) * P.items.size() +
+                           sizeof(double) * P.coefs.size());
+    *d2h_bytes = (int64_t)(sizeof(double) * P.n_inst + sizeof(int32_t));
+    return AMFRW_OK;
+}
+
+int amfrw_batch_launches(const amfrw_batch* b, int32_t* n_launches)
+{
+    if (!b || !n_launches) return fail(AMFRW_EINVAL, "NULL argument");
+    *n_launches = (int32_t)b->plan.classes.size() + 1;
+    return AMFRW_OK;
+}
+
+void amfrw_batch_destroy(amfrw_batch* b) { delete b; }
+
+int amfrw_solve_batch(const amfrw_params* ps, int32_t n, double* prices_out, void* cuda_stream)
+{
+    if (!prices_out) return fail(AMFRW_EINVAL, "prices_out is NULL");
+    amfrw_batch* b = nullptr;
+    int st = amfrw_batch_create(ps, n, cuda_stream, &b);
+    if (st != AMFRW_OK) return st;
+    Plan& P = b->plan;
+    st = amfrw_batch_run(b, P.d_prices);
+    if (st == AMFRW_OK) {
+        int32_t flag = 0;
+        cudaError_t e1 = cudaMemcpyAsync(prices_out, P.d_prices, sizeof(double) * n, cudaMemcpyDeviceToHost, P.stream);
+        cudaError_t e2 = cudaMemcpyAsync(&flag, P.d_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, P.stream);
+        cudaError_t e3 = cudaStreamSynchronize(P.stream);
+        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess)
+            st = fail(AMFRW_ECUDA, std::string("download: ") + cudaGetErrorString(e3 != cudaSuccess ? e3 : (e1 != cudaSuccess ? e1 : e2)));
+        else if (flag)
+            st = fail(AMFRW_ENONFINITE, "a combined price is not finite");
+    }
+    amfrw_batch_destroy(b);
+    return st;
+}
+
+}  // extern "C"

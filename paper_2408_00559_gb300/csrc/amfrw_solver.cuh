@@ -1,0 +1,665 @@
+// AMFR-W2 solver for one sparse-grid component grid, resident in shared
+// memory for the whole time integration.
+//
+// A work group (one warp, or a whole CTA for large grids) takes a component
+// grid from a queue, builds its coefficient and line-solve tables, sets the
+// grid to the payoff, runs every AMFR-W2 step on chip and writes the value
+// interpolated at the spot.  HBM traffic per grid is the parameter record in
+// and one double out.
+//
+// Storage.  Only the Inner nodes (all j_i >= 1, Sec. 3) are stored, in the
+// paper's lexicographic order with axis 0 fastest, plus one padding slot per
+// axis-0 row so that lines along axis 0 handled by consecutive lanes fall in
+// different shared-memory banks.  The grid function is split as Y = G + Z,
+// where G is the payoff on every node (Inner and Outer) and Z vanishes on the
+// Outer nodes (they keep the Dirichlet data, Y' = 0 there).  Because F is
+// linear (end of Sec. 4.1), F(Y) = F(G) + F_0(Z), where F_0 is Sketch 1 with
+// zero Outer values, and F(G) is computed once per grid in FP64.  The payoff
+// does not depend on V and every coefficient carries the factor V^2, so
+// F(G) = V^2 H(F_1..F_{N-1}) and only H is stored.
+//
+// Time stepping follows eq. (amfrw) with the AMFR-W2 coefficients of eq.
+// (coef_W2):  per stage an F evaluation, N directional solves (Lemma ls),
+// the refinement Khat = 2K^(0) - K^(N) + theta dt F(K^(N)), and N solves.
+// The directional matrices (I - nu dt A_i) do not change in time, so their
+// Thomas factors are computed once per grid: for a rate axis they depend on
+// the V index only (d_i = 1/2 alpha_i^2 F_i^{2 beta} V^2), for the V axis on
+// nothing else.
+//
+// Precision.  FP64 mode: every operation in double.  Mixed mode: the stencil
+// and the line solves run in FP32 on the increments K; Z is accumulated in
+// FP64 (Y_{n+1} = Y_n + b1 K1 + b2 K2) and the stencil of F(Y_n) reads Z as
+// an unevaluated pair of floats (hi + lo), so its differences keep ~48 bits;
+// F(G) (through H), the interpolation and the combination sum are FP64.  The
+// stage-2 argument uses linearity, F(Y_n + a21 K1) = F(Y_n) + a21 F_0(K1), so
+// that F is applied to Y only once per step.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "amfrw_internal.h"
+
+namespace amfrw {
+
+constexpr double kA21 = 2.0 / 3.0;   // eq. (coef_W2)
+constexpr double kQ21 = -4.0 / 3.0;
+constexpr double kB1 = 5.0 / 4.0;
+constexpr double kB2 = 3.0 / 4.0;
+
+template <int N>
+struct Shape {
+    int lv[N], M[N], sh[N], Sp[N];
+    int toff[N];   // coefficient tables: rate axis a -> [dI | pw | ph] of M_a each; V -> v2
+    int poff[N];   // payoff tables: rate axis a -> M_a + 1 entries (Outer node included)
+    int luoff[N];  // Thomas factors: rate axis -> M_V classes x M_a rows x 3; V -> M_V x 3
+    int L, Lr, pad, phalf;
+    __device__ __forceinline__ int padded(int t) const { return t + pad * (t >> lv[0]); }
+};
+
+template <int N>
+__device__ __forceinline__ void make_shape(Shape<N>& s, const int8_t* lv)
+{
+    int sh = 0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        s.lv[i] = lv[i];
+        s.M[i] = 1 << lv[i];
+        s.sh[i] = sh;
+        sh += lv[i];
+    }
+    s.L = 1 << sh;
+    s.Lr = s.L >> s.lv[N - 1];
+    s.pad = s.M[0] > 1 ? 1 : 0;
+    int r = s.M[0] + s.pad;
+    s.Sp[0] = 1;
+#pragma unroll
+    for (int i = 1; i < N; ++i) {
+        s.Sp[i] = r;
+        r *= s.M[i];
+    }
+    int o = 0, po = 0, lo = 0;
+#pragma unroll
+    for (int i = 0; i < N - 1; ++i) {
+        s.toff[i] = o;
+        o += 3 * s.M[i];
+        s.poff[i] = po;
+        po += s.M[i] + 1;
+        s.luoff[i] = lo;
+        lo += 3 * s.M[N - 1] * s.M[i];
+    }
+    s.toff[N - 1] = o;
+    s.poff[N - 1] = po;
+    s.luoff[N - 1] = lo;
+    s.phalf = po;
+}
+
+template <int N>
+__device__ __forceinline__ void decode(const Shape<N>& s, int t, int (&j)[N])
+{
+#pragma unroll
+    for (int i = 0; i < N; ++i) j[i] = ((t >> s.sh[i]) & (s.M[i] - 1)) + 1;
+}
+
+// ------------------------------------------------------------------ sources
+// A source supplies the grid values the stencil reads.  nb() gets both the
+// shared-memory offset of the neighbour and its multi-index displacement;
+// each source uses what it needs.
+
+template <typename T>
+struct ArrSrc {  // stored increments or Z: zero on Outer nodes
+    using V = T;
+    const T* X;
+    __device__ __forceinline__ V ctr(int J) const { return X[J]; }
+    __device__ __forceinline__ V nb(int J, int off, bool valid, int, int, int, int) const
+    {
+        return valid ? X[J + off] : T(0);
+    }
+    __device__ static __forceinline__ T diff(V a, V b) { return a - b; }
+};
+
+struct DFSrc {  // Z as an unevaluated float pair hi + lo
+    using V = float2;
+    const float2* X;
+    __device__ __forceinline__ V ctr(int J) const { return X[J]; }
+    __device__ __forceinline__ V nb(int J, int off, bool valid, int, int, int, int) const
+    {
+        return valid ? X[J + off] : make_float2(0.f, 0.f);
+    }
+    // hi parts of nearby values are close, so hi_a - hi_b is (nearly) exact
+    __device__ static __forceinline__ float diff(V a, V b) { return (a.x - b.x) + (a.y - b.y); }
+};
+
+// Payoff g at rate multi-index jj (Sec. 2).  Caplet: (F_1 - K)^+.
+// Swaption: max{ sum_i tau_i (F_i - K) prod_{l<=i} 1/(1 + tau_l F_l), 0 }.
+template <int N>
+__device__ __forceinline__ double payoff_at(const Shape<N>& s, const double* pay, int payoff,
+                                            const int (&jj)[N])
+{
+    if (payoff == 0) return fmax(pay[s.poff[0] + jj[0]], 0.0);
+    double sum = 0.0, P = 1.0;
+#pragma unroll
+    for (int r = 0; r < N - 1; ++r) {
+        P *= pay[s.phalf + s.poff[r] + jj[r]];
+        sum += pay[s.poff[r] + jj[r]] * P;
+    }
+    return fmax(sum, 0.0);
+}
+
+template <int N>
+struct PaySrc {  // the payoff G on every node, Outer included
+    using V = double;
+    const Shape<N>* s;
+    const double* pay;
+    int payoff;
+    int j[N];
+    __device__ __forceinline__ double at(int i, int si, int k, int sk) const
+    {
+        int jj[N];
+#pragma unroll
+        for (int r = 0; r < N; ++r) jj[r] = j[r] + (r == i ? si : 0) + (r == k ? sk : 0);
+        return payoff_at<N>(*s, pay, payoff, jj);
+    }
+    __device__ __forceinline__ V ctr(int) const { return at(-1, 0, -1, 0); }
+    __device__ __forceinline__ V nb(int, int, bool, int i, int si, int k, int sk) const
+    {
+        return at(i, si, k, sk);
+    }
+    __device__ static __forceinline__ double diff(V a, V b) { return a - b; }
+};
+
+// -------------------------------------------------------------- the stencil
+// Sketch 1 at the Inner node with multi-index j, divided by V^2 (every
+// coefficient of eqs. coef_diff, coef_mix, coef_adv carries F_N^2 = V^2):
+//   sum_i d_i/V^2 Delta^(i) + sum_{i<k} m_ik/V^2 Delta^(ik) + sum_i a_i/V^2 nabla^(i)
+// with the Neumann rules of Sketch 1 on the upper faces (ghost node
+// Y_{J+E_i} = Y_{J-E_i}, zero first and mixed differences).  The 1/h factors
+// are folded into the tables.
+template <int N, typename TC, class Src>
+__device__ __forceinline__ TC stencil_acc(const Shape<N>& s, const int (&j)[N], int J,
+                                          const Src& src, const TC* __restrict__ tab,
+                                          const Consts<TC>& c)
+{
+    using V = typename Src::V;
+    const V x0 = src.ctr(J);
+    TC lap[N], grad[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const bool has_lo = j[i] > 1;
+        const bool top = j[i] == s.M[i];
+        const V m = src.nb(J, -s.Sp[i], has_lo, i, -1, -1, 0);
+        const V p = top ? m : src.nb(J, s.Sp[i], true, i, 1, -1, 0);
+        const TC dp = Src::diff(p, x0);
+        const TC dm = Src::diff(x0, m);
+        lap[i] = dp - dm;
+        grad[i] = top ? TC(0) : dp + dm;
+    }
+    TC acc = c.cV * lap[N - 1];
+#pragma unroll
+    for (int i = 0; i < N - 1; ++i) acc += tab[s.toff[i] + j[i] - 1] * lap[i];
+#pragma unroll
+    for (int i = 0; i < N - 1; ++i) {
+        TC inner = TC(0);
+        if (j[i] != s.M[i]) {
+            const bool li = j[i] > 1;
+#pragma unroll
+            for (int k = i + 1; k < N; ++k) {
+                if (j[k] != s.M[k]) {
+                    const bool lk = j[k] > 1;
+                    const V pp = src.nb(J, s.Sp[i] + s.Sp[k], true, i, 1, k, 1);
+                    const V pm = src.nb(J, s.Sp[i] - s.Sp[k], lk, i, 1, k, -1);
+                    const V mp = src.nb(J, -s.Sp[i] + s.Sp[k], li, i, -1, k, 1);
+                    const V mm = src.nb(J, -s.Sp[i] - s.Sp[k], li && lk, i, -1, k, -1);
+                    const TC mix = Src::diff(pp, pm) - Src::diff(mp, mm);
+                    const TC ck = (k < N - 1) ? c.rm[i][k] * tab[s.toff[k] + s.M[k] + j[k] - 1]
+                                              : c.sm[i];
+                    inner += ck * mix;
+                }
+            }
+        }
+        if (i >= 1) {  // drift of rates 2..N-1 (eq. coef_adv), sum over rates 2..i
+            TC S = TC(0);
+#pragma unroll
+            for (int r = 1; r <= i; ++r) S += c.rh[i][r] * tab[s.toff[r] + 2 * s.M[r] + j[r] - 1];
+            inner += S * c.g2[i] * grad[i];
+        }
+        acc += tab[s.toff[i] + s.M[i] + j[i] - 1] * inner;
+    }
+    return acc;
+}
+
+// ----------------------------------------------------------- line solves
+// (I - nu dt A_axis) X = G on every line along `axis` (Lemma ls, eq.
+// decomp1) by Thomas elimination with the precomputed factors
+// (lower_r, 1/beta_r, gamma_r) of the line's class; one thread per line.
+// src may equal dst.  epi(J, x) sees every solved value.
+template <int N, typename T, class Epi>
+__device__ __forceinline__ void sweep(const Shape<N>& s, int axis, const T* __restrict__ lu,
+                                      const T* src, T* dst, int rank, int gsize, Epi epi)
+{
+    const int M = s.M[axis];
+    const int lvA = s.lv[axis];
+    const int sh = s.sh[axis];
+    const int Spa = s.Sp[axis];
+    const int nl = s.L >> lvA;
+    const int lo_mask = (1 << sh) - 1;
+    const int MV1 = s.M[N - 1] - 1;
+    const int shV = s.sh[N - 1];
+    for (int line = rank; line < nl; line += gsize) {
+        const int t0 = (line & lo_mask) | ((line >> sh) << (sh + lvA));
+        const int J0 = s.padded(t0);
+        const int cls = (axis == N - 1) ? 0 : ((t0 >> shV) & MV1);
+        const T* tb = lu + s.luoff[axis] + cls * M * 3;
+        T y = T(0);
+        int J = J0;
+        for (int r = 0; r < M; ++r, J += Spa) {
+            y = (src[J] - tb[3 * r] * y) * tb[3 * r + 1];
+            dst[J] = y;
+        }
+        J -= Spa;
+        T x = y;
+        epi(J, x);
+        for (int r = M - 2; r >= 0; --r) {
+            J -= Spa;
+            x = dst[J] - tb[3 * r + 2] * x;
+            dst[J] = x;
+            epi(J, x);
+        }
+    }
+}
+
+struct NoEpi {
+    template <typename T>
+    __device__ __forceinline__ void operator()(int, T) const {}
+};
+
+template <bool WARP>
+__device__ __forceinline__ void gsync()
+{
+    if (WARP)
+        __syncwarp();
+    else
+        __syncthreads();
+}
+
+// --------------------------------------------------------- table building
+template <int N>
+__device__ void build_tables(const Shape<N>& s, const InstDev& P, double* tabd, double* pay,
+                             Consts<double>* cd, int rank, int gsize)
+{
+    const double beta = P.beta;
+    for (int a = 0; a < N - 1; ++a) {
+        const int M = s.M[a];
+        const double h = P.Fmax[a] / (double)M;
+        const double al = P.alpha[a], ta = P.tau[a];
+        const double raa = P.rho[a * kMaxDim + a];
+        for (int jj = 1 + rank; jj <= M; jj += gsize) {
+            const double F = (double)jj * h;
+            const double Fb = pow(F, beta);
+            tabd[s.toff[a] + jj - 1] = 0.5 * al * al * raa * pow(F, 2.0 * beta) / (h * h);
+            tabd[s.toff[a] + M + jj - 1] = al * Fb;
+            tabd[s.toff[a] + 2 * M + jj - 1] = al * ta * Fb / (1.0 + ta * F);
+        }
+        for (int jj = rank; jj <= M; jj += gsize) {
+            const double F = (double)jj * h;
+            pay[s.poff[a] + jj] = (P.payoff == 0) ? (F - P.K) : ta * (F - P.K);
+            pay[s.phalf + s.poff[a] + jj] = 1.0 / (1.0 + ta * F);
+        }
+    }
+    {
+        const int MV = s.M[N - 1];
+        const double hV = P.Fmax[N - 1] / (double)MV;
+        for (int jj = 1 + rank; jj <= MV; jj += gsize) {
+            const double V = (double)jj * hV;
+            tabd[s.toff[N - 1] + jj - 1] = V * V;
+        }
+    }
+    if (rank == 0) {
+        double h[kMaxDim];
+        for (int i = 0; i < N; ++i) h[i] = P.Fmax[i] / (double)s.M[i];
+        const double hV = h[N - 1];
+        cd->cV = 0.5 * P.sigma * P.sigma / (hV * hV);
+        cd->dt = P.dt;
+        cd->thdt = P.theta * P.dt;
+        cd->nudt = P.nu * P.dt;
+        for (int i = 0; i < kMaxDim; ++i) {
+            for (int k = 0; k < kMaxDim; ++k) {
+                const bool ok = i < N - 1 && k < N - 1;
+                cd->rm[i][k] = ok ? P.rho[i * kMaxDim + k] / (4.0 * h[i] * h[k]) : 0.0;
+                cd->rh[i][k] = ok ? P.rho[i * kMaxDim + k] : 0.0;
+            }
+            cd->sm[i] = (i < N - 1) ? P.sigma * P.phi[i] / (4.0 * h[i] * hV) : 0.0;
+            cd->g2[i] = (i < N) ? 1.0 / (2.0 * h[i]) : 0.0;
+        }
+    }
+}
+
+template <typename T>
+__device__ void convert_consts(const Consts<double>& a, Consts<T>* b)
+{
+    b->cV = (T)a.cV;
+    b->dt = (T)a.dt;
+    b->thdt = (T)a.thdt;
+    b->nudt = (T)a.nudt;
+    for (int i = 0; i < kMaxDim; ++i) {
+        for (int k = 0; k < kMaxDim; ++k) {
+            b->rm[i][k] = (T)a.rm[i][k];
+            b->rh[i][k] = (T)a.rh[i][k];
+        }
+        b->sm[i] = (T)a.sm[i];
+        b->g2[i] = (T)a.g2[i];
+    }
+}
+
+// Thomas factors of (I - nu dt A_axis) for every line class (Lemma ls).
+template <int N, typename T>
+__device__ void build_lu(const Shape<N>& s, const double* tabd, const Consts<double>& c, T* lu,
+                         int rank, int gsize)
+{
+    const int MV = s.M[N - 1];
+    const int ncls = (N - 1) * MV + 1;
+    for (int q = rank; q < ncls; q += gsize) {
+        const int axis = (q == ncls - 1) ? N - 1 : q / MV;
+        const int cls = (axis == N - 1) ? 0 : q % MV;
+        const int M = s.M[axis];
+        T* tb = lu + s.luoff[axis] + cls * M * 3;
+        double gam = 0.0;
+        for (int r = 0; r < M; ++r) {
+            const double delta = (axis < N - 1)
+                                     ? tabd[s.toff[axis] + r] * tabd[s.toff[N - 1] + cls]
+                                     : c.cV * tabd[s.toff[N - 1] + r];
+            const double nd = c.nudt * delta;
+            const double diag = 1.0 + 2.0 * nd;
+            const double up = (r < M - 1) ? -nd : 0.0;
+            const double lo = (r == 0) ? 0.0 : ((r < M - 1) ? -nd : -2.0 * nd);
+            const double inv = 1.0 / (diag - lo * gam);
+            gam = up * inv;
+            tb[3 * r] = (T)lo;
+            tb[3 * r + 1] = (T)inv;
+            tb[3 * r + 2] = (T)gam;
+        }
+    }
+}
+
+__device__ __forceinline__ float2 split_df(double z)
+{
+    const float hi = __double2float_rn(z);
+    const float lo = __double2float_rn(z - (double)hi);
+    return make_float2(hi, lo);
+}
+
+// ------------------------------------------------------------- one grid
+template <int N, bool MIXED, bool WARP>
+__device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* base, int rank,
+                           int gsize)
+{
+    using TK = typename std::conditional<MIXED, float, double>::type;
+    const InstDev& P = a.insts[it.inst];
+    Shape<N> s;
+    make_shape<N>(s, it.lv);
+    const Layout lay = make_layout(N, it.lv, MIXED, WARP);
+    Consts<double>* cd = reinterpret_cast<Consts<double>*>(base + lay.cd);
+    Consts<TK>* ck = MIXED ? reinterpret_cast<Consts<TK>*>(base + lay.cf)
+                           : reinterpret_cast<Consts<TK>*>(base + lay.cd);
+    double* tabd = reinterpret_cast<double*>(base + lay.tabd);
+    TK* tabk = MIXED ? reinterpret_cast<TK*>(base + lay.tabf) : reinterpret_cast<TK*>(tabd);
+    double* pay = reinterpret_cast<double*>(base + lay.pay);
+    // warp groups keep the Thomas factors on chip; a CTA group (grids of more
+    // than 256 Inner nodes) keeps them in its block's slice of global scratch,
+    // read through L1
+    TK* lu = WARP ? reinterpret_cast<TK*>(base + lay.lu)
+                  : reinterpret_cast<TK*>(a.lu_scratch + (size_t)blockIdx.x * (size_t)a.lu_stride);
+    double* Z = reinterpret_cast<double*>(base + lay.Z);
+    float2* ZZ = reinterpret_cast<float2*>(base + lay.ZZ);
+    TK* H = reinterpret_cast<TK*>(base + lay.H);
+    float* FY = reinterpret_cast<float*>(base + lay.FY);
+    TK* K1 = reinterpret_cast<TK*>(base + lay.K1);
+    TK* K0 = reinterpret_cast<TK*>(base + lay.K0);
+    TK* Kw = reinterpret_cast<TK*>(base + lay.Kw);
+
+    // 1. coefficient and payoff tables, constants
+    build_tables<N>(s, P, tabd, pay, cd, rank, gsize);
+    gsync<WARP>();
+    if constexpr (MIXED) {
+        for (int q = rank; q < lay.ntab; q += gsize) tabk[q] = (TK)tabd[q];
+        if (rank == 0) convert_consts<TK>(*cd, ck);
+    }
+    build_lu<N, TK>(s, tabd, *cd, lu, rank, gsize);
+
+    // 2. H = F(G)/V^2 on the rate grid (FP64), Z from the state or zero
+    for (int tr = rank; tr < s.Lr; tr += gsize) {
+        PaySrc<N> ps;
+        ps.s = &s;
+        ps.pay = pay;
+        ps.payoff = P.payoff;
+        decode<N>(s, tr, ps.j);
+        H[tr] = (TK)stencil_acc<N, double>(s, ps.j, 0, ps, tabd, *cd);
+    }
+    for (int t = rank; t < s.L; t += gsize) {
+        const int J = s.padded(t);
+        double z = 0.0;
+        if (a.flags & kLoadState) {
+            int j[N];
+            decode<N>(s, t, j);
+            z = a.state[it.state_off + t] - payoff_at<N>(s, pay, P.payoff, j);
+        }
+        Z[J] = z;
+        if constexpr (MIXED) ZZ[J] = split_df(z);
+    }
+    gsync<WARP>();
+
+    const int Lr1 = s.Lr - 1;
+    const TK* v2 = tabk + s.toff[N - 1] - 1;  // v2[j_V], 1-based
+    const TK* luc = lu;
+    auto sweeps_into = [&](TK* from, TK* to) {
+        sweep<N, TK>(s, 0, luc, from, to, rank, gsize, NoEpi());
+        gsync<WARP>();
+        for (int ax = 1; ax < N; ++ax) {
+            sweep<N, TK>(s, ax, luc, to, to, rank, gsize, NoEpi());
+            gsync<WARP>();
+        }
+    };
+
+    for (int n = 0; n < a.steps; ++n) {
+        // ---- stage 1: K^(0) = dt F(Y_n)
+        for (int t = rank; t < s.L; t += gsize) {
+            int j[N];
+            decode<N>(s, t, j);
+            const int J = s.padded(t);
+            TK k0;
+            if constexpr (MIXED) {
+                const float acc = stencil_acc<N, float>(s, j, J, DFSrc{ZZ}, (const float*)tabk,
+                                                        *(const Consts<float>*)ck);
+                k0 = (TK)(ck->dt * v2[j[N - 1]] * ((float)H[t & Lr1] + acc));
+                FY[J] = (float)k0;
+            } else {
+                const double acc = stencil_acc<N, double>(s, j, J, ArrSrc<double>{Z},
+                                                          (const double*)tabk,
+                                                          *(const Consts<double>*)ck);
+                k0 = (TK)(cd->dt * (double)v2[j[N - 1]] * ((double)H[t & Lr1] + acc));
+            }
+            K0[J] = k0;
+        }
+        gsync<WARP>();
+        sweeps_into(K0, Kw);
+        // refinement: Khat = 2 K^(0) - K^(N) + theta dt F(K^(N))
+        for (int t = rank; t < s.L; t += gsize) {
+            int j[N];
+            decode<N>(s, t, j);
+            const int J = s.padded(t);
+            const TK acc = stencil_acc<N, TK>(s, j, J, ArrSrc<TK>{Kw}, tabk, *ck);
+            K0[J] = TK(2) * K0[J] - Kw[J] + ck->thdt * v2[j[N - 1]] * acc;
+        }
+        gsync<WARP>();
+        // N solves into K1; the last one also forms the stage-2 argument
+        sweep<N, TK>(s, 0, luc, K0, K1, rank, gsize, NoEpi());
+        gsync<WARP>();
+        for (int ax = 1; ax < N; ++ax) {
+            if (!MIXED && ax == N - 1) {  // FP64: Kw = Z + a21 K1
+                sweep<N, TK>(s, ax, luc, K1, K1, rank, gsize, [&](int J, TK x) {
+                    Kw[J] = (TK)(Z[J] + kA21 * (double)x);
+                });
+            } else {
+                sweep<N, TK>(s, ax, luc, K1, K1, rank, gsize, NoEpi());
+            }
+            gsync<WARP>();
+        }
+        // ---- stage 2: K^(0) = dt F(Y_n + a21 K1) + q21 K1
+        for (int t = rank; t < s.L; t += gsize) {
+            int j[N];
+            decode<N>(s, t, j);
+            const int J = s.padded(t);
+            if constexpr (MIXED) {
+                const float acc = stencil_acc<N, float>(s, j, J, ArrSrc<float>{(const float*)K1},
+                                                        (const float*)tabk,
+                                                        *(const Consts<float>*)ck);
+                const float a21dt = (float)kA21 * (float)ck->dt;
+                K0[J] = (TK)(FY[J] + a21dt * (float)v2[j[N - 1]] * acc +
+                             (float)kQ21 * (float)K1[J]);
+            } else {
+                const double acc = stencil_acc<N, double>(s, j, J, ArrSrc<double>{(const double*)Kw},
+                                                          (const double*)tabk,
+                                                          *(const Consts<double>*)ck);
+                K0[J] = (TK)(cd->dt * (double)v2[j[N - 1]] * ((double)H[t & Lr1] + acc) +
+                             kQ21 * (double)K1[J]);
+            }
+        }
+        gsync<WARP>();
+        sweeps_into(K0, Kw);
+        for (int t = rank; t < s.L; t += gsize) {
+            int j[N];
+            decode<N>(s, t, j);
+            const int J = s.padded(t);
+            const TK acc = stencil_acc<N, TK>(s, j, J, ArrSrc<TK>{Kw}, tabk, *ck);
+            K0[J] = TK(2) * K0[J] - Kw[J] + ck->thdt * v2[j[N - 1]] * acc;
+        }
+        gsync<WARP>();
+        // N solves in place; the last one accumulates Y_{n+1} = Y_n + b1 K1 + b2 K2
+        for (int ax = 0; ax < N; ++ax) {
+            if (ax == N - 1) {
+                sweep<N, TK>(s, ax, luc, K0, K0, rank, gsize, [&](int J, TK x) {
+                    const double z = fma(kB2, (double)x, fma(kB1, (double)K1[J], Z[J]));
+                    Z[J] = z;
+                    if constexpr (MIXED) ZZ[J] = split_df(z);
+                });
+            } else {
+                sweep<N, TK>(s, ax, luc, K0, K0, rank, gsize, NoEpi());
+            }
+            gsync<WARP>();
+        }
+    }
+
+    // 3. keep the state (Y on Inner nodes) if asked
+    if (a.flags & kStoreState) {
+        for (int t = rank; t < s.L; t += gsize) {
+            int j[N];
+            decode<N>(s, t, j);
+            a.state[it.state_off + t] = payoff_at<N>(s, pay, P.payoff, j) + Z[s.padded(t)];
+        }
+    }
+    // 4. multilinear interpolation at the spot x* = (F_1(0), ..., V0)
+    if (rank == 0) {
+        int c[N];
+        double w[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            const double x = (i < N - 1) ? P.F0[i] : P.V0;
+            const double h = P.Fmax[i] / (double)s.M[i];
+            const double sx = x / h;
+            int ci = (int)floor(sx);
+            ci = ci > s.M[i] - 1 ? s.M[i] - 1 : ci;
+            ci = ci < 0 ? 0 : ci;
+            c[i] = ci;
+            w[i] = sx - (double)ci;
+        }
+        double u = 0.0;
+        for (int corner = 0; corner < (1 << N); ++corner) {
+            double wt = 1.0;
+            int jj[N];
+            bool outer = false;
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                const int bit = (corner >> i) & 1;
+                wt *= bit ? w[i] : 1.0 - w[i];
+                jj[i] = c[i] + bit;
+                outer |= jj[i] == 0;
+            }
+            double zv = 0.0;
+            if (!outer) {
+                int t = 0;
+#pragma unroll
+                for (int i = 0; i < N; ++i) t += (jj[i] - 1) << s.sh[i];
+                zv = Z[s.padded(t)];
+            }
+            u += wt * (payoff_at<N>(s, pay, P.payoff, jj) + zv);
+        }
+        a.u_out[it.out_idx] = u;
+    }
+    gsync<WARP>();  // the group's shared memory is reused by its next grid
+}
+
+template <int N, bool MIXED, bool WARP>
+__global__ void __launch_bounds__(WARP ? 256 : 512) solve_kernel(SolveArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_item;
+    const int gid = WARP ? (int)(threadIdx.x >> 5) : 0;
+    const int rank = WARP ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
+    const int gsize = WARP ? 32 : (int)blockDim.x;
+    unsigned char* base = smem + (size_t)gid * (size_t)a.smem_group;
+    for (;;) {
+        int item;
+        if (WARP) {
+            item = 0;
+            if (rank == 0) item = atomicAdd(a.queue, 1);
+            item = __shfl_sync(0xffffffffu, item, 0);
+        } else {
+            if (threadIdx.x == 0) s_item = atomicAdd(a.queue, 1);
+            __syncthreads();
+            item = s_item;
+            __syncthreads();
+        }
+        if (item >= a.n_items) break;
+        const Item it = a.items[item];
+        solve_item<N, MIXED, WARP>(a, it, base, rank, gsize);
+    }
+}
+
+// Host launch / occupancy helpers, instantiated once per N.
+template <int N>
+int launch_impl(const SolveArgs& a, bool mixed, bool warp, int block, int grid, size_t smem,
+                void* stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    if (mixed && warp) solve_kernel<N, true, true><<<grid, block, smem, st>>>(a);
+    else if (mixed) solve_kernel<N, true, false><<<grid, block, smem, st>>>(a);
+    else if (warp) solve_kernel<N, false, true><<<grid, block, smem, st>>>(a);
+    else solve_kernel<N, false, false><<<grid, block, smem, st>>>(a);
+    return (int)cudaGetLastError();
+}
+
+template <int N>
+int occupancy_impl(bool mixed, bool warp, int block, size_t smem)
+{
+    int nb = 0;
+    const void* f = mixed ? (warp ? (const void*)solve_kernel<N, true, true>
+                                  : (const void*)solve_kernel<N, true, false>)
+                          : (warp ? (const void*)solve_kernel<N, false, true>
+                                  : (const void*)solve_kernel<N, false, false>);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, block, smem) != cudaSuccess) return 0;
+    return nb;
+}
+
+}  // namespace amfrw
+
+#define AMFRW_INSTANTIATE(NN)                                                               \
+    namespace amfrw {                                                                       \
+    int launch_n##NN(const SolveArgs& a, bool m, bool w, int b, int g, size_t s, void* st)  \
+    {                                                                                       \
+        return launch_impl<NN>(a, m, w, b, g, s, st);                                       \
+    }                                                                                       \
+    int occupancy_n##NN(bool m, bool w, int b, size_t s) { return occupancy_impl<NN>(m, w, b, s); } \
+    }
