@@ -193,6 +193,39 @@ int amfrw_batch_kernel_times(amfrw_batch *b, float *ms_out, double *node_steps_o
 int amfrw_batch_io_bytes(const amfrw_batch *b, int64_t *h2d_bytes, int64_t *d2h_bytes);
 void amfrw_batch_destroy(amfrw_batch *b);
 
+/* ------------------------------------------------------------------------
+ * Pricing without device allocation.  The paper has no counterpart: this is
+ * an integration entry point of the library.
+ *
+ * Every other entry point obtains its device buffers with cudaMalloc.  Some
+ * callers cannot: programs whose device memory belongs to another allocator
+ * (a framework's caching pool, or a fixed budget reserved at start-up), and
+ * latency-sensitive loops that must not pay for cudaMalloc/cudaFree, since a
+ * free synchronises the whole device and stalls every other stream.
+ * amfrw_solve_noalloc prices the n instances of ps like amfrw_solve_batch,
+ * but its device working memory is one fixed array compiled into the library
+ * (AMFRW_NOALLOC_SCRATCH_BYTES); it calls no cudaMalloc, cudaFree or other
+ * allocating routine.  Host side it only uses small temporary host buffers
+ * for validation and the grid list.
+ *   - d_prices_out: DEVICE array [n] owned by the caller; written
+ *     asynchronously on cuda_stream (like amfrw_batch_run).
+ *   - Limit: the instance records, grid list, per-grid values, counters and
+ *     line-solve factors must fit in AMFRW_NOALLOC_SCRATCH_BYTES (about 2000
+ *     instances of the d=4 level-5 problem, or one d=6 modified level-6
+ *     problem); larger problems are rejected with AMFRW_ETOOBIG and a message
+ *     giving the bytes needed.  All instances must share n_steps (EINVAL).
+ *   - The array is reserved on every GPU that loads the library, for the life
+ *     of the process, and is shared by all calls: calls whose work overlaps
+ *     on the GPU (different streams, or host threads) race and give wrong
+ *     prices; serialise them.  The array keeps the previous call's contents;
+ *     each call rewrites everything it reads and zeroes its counters.
+ *   - The first call on a device looks up the array's device address (once
+ *     per device, with that device current); make that first call before any
+ *     stream capture begins.
+ * Errors: EINVAL, ENOTPSD, ETOOBIG, ECUDA. */
+#define AMFRW_NOALLOC_SCRATCH_BYTES (16u << 20)
+int amfrw_solve_noalloc(const amfrw_params *ps, int32_t n, double *d_prices_out, void *cuda_stream);
+
 const char *amfrw_status_string(int status);
 const char *amfrw_last_error(void);
 

@@ -27,6 +27,7 @@ EXPORTS = [
     "amfrw_problem_destroy", "amfrw_solve_batch", "amfrw_batch_create", "amfrw_batch_run",
     "amfrw_batch_launches", "amfrw_batch_destroy", "amfrw_status_string", "amfrw_last_error",
     "amfrw_batch_enable_timing", "amfrw_batch_kernel_times", "amfrw_batch_io_bytes",
+    "amfrw_solve_noalloc",
 ]
 
 
@@ -82,6 +83,7 @@ def lib():
         L.amfrw_batch_kernel_times.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(C.c_double),
                                                C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_int32)]
         L.amfrw_batch_io_bytes.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+        L.amfrw_solve_noalloc.argtypes = [pp, C.c_int32, vp, vp]
         L.amfrw_status_string.restype = C.c_char_p
         L.amfrw_status_string.argtypes = [C.c_int]
         L.amfrw_last_error.restype = C.c_char_p
@@ -257,3 +259,13 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def solve_noalloc(insts: list[dict], d_prices_ptr: int, stream=None):
+    """amfrw_solve_noalloc: prices into the device array at d_prices_ptr
+    without any device allocation by the library (its working memory is a
+    fixed array inside the library, shared by all calls; see include/amfrw.h
+    for the size limit and why overlapping calls must be serialised)."""
+    m = _Marshal(insts)
+    _check(lib().amfrw_solve_noalloc(m.arr, len(insts), C.c_void_p(int(d_prices_ptr)),
+                                     _stream_ptr(stream)), "amfrw_solve_noalloc")

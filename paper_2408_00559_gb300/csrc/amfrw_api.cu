@@ -11,6 +11,8 @@
 #include <map>
 #include <string>
 #include <tuple>
+#include <mutex>
+#include <new>
 #include <vector>
 
 #include "../../include/amfrw.h"
@@ -698,3 +700,217 @@ int amfrw_solve_batch(const amfrw_params* ps, int32_t n, double* prices_out, voi
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------
+// Entry point that allocates no device memory (amfrw_solve_noalloc).
+//
+// Every other entry point gets its device buffers from cudaMalloc.  Some
+// callers cannot do that: a host program whose device memory is owned by
+// another allocator (a framework's caching pool or a fixed budget reserved
+// at start-up), or a latency-sensitive loop that must not pay for
+// cudaMalloc/cudaFree, whose frees synchronise the whole device and stall
+// every other stream.  This entry point takes its working memory from one
+// fixed device array declared below, so it never allocates.  That array is
+// reserved by every GPU that loads the library, for the life of the
+// process.
+namespace {
+
+// Scratch of amfrw_solve_noalloc: instance records, grid list, combination
+// coefficients, per-grid values, work counters and the Thomas factors of
+// the grids solved by whole blocks.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[AMFRW_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+unsigned char* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device.  In host code
+// the array's name only stands in for the symbol, so the address is asked
+// from the runtime once per device, with that device current, and cached.
+int noalloc_scratch(unsigned char** out)
+{
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(AMFRW_EINVAL, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_ptr[dev] = static_cast<unsigned char*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return AMFRW_OK;
+}
+
+int64_t align256(int64_t x) { return (x + 255) & ~(int64_t)255; }
+
+// The same grid list and launch classes as the allocating path, built on the
+// host only; lu offsets are relative to the Thomas-factor region.
+int noalloc_plan(const amfrw_params* ps, int n, Plan& P)
+{
+    if (n < 1) return fail(AMFRW_EINVAL, "need at least one instance");
+    if (!ps) return fail(AMFRW_EINVAL, "params is NULL");
+    for (int i = 0; i < n; ++i) {
+        int st = validate(ps + i);
+        if (st != AMFRW_OK) {
+            g_last_error = "instance " + std::to_string(i) + ": " + g_last_error;
+            return st;
+        }
+    }
+    P.n_inst = n;
+    const int smem_cap = max_smem_optin();
+    struct Tmp { Item it; int L; int N; bool mixed; bool warp; int smem_group; int64_t lu_bytes; };
+    std::vector<Tmp> all;
+    for (int i = 0; i < n; ++i) {
+        const amfrw_params* p = ps + i;
+        InstDev I = to_device(p);
+        const int N = I.N;
+        const bool mixed = p->precision == AMFRW_MIXED;
+        std::vector<GridSpec> grids = enumerate(N, p->level, p->psi, p->full_grid != 0);
+        I.grid_begin = (int32_t)P.coefs.size();
+        I.grid_count = (int32_t)grids.size();
+        for (const GridSpec& g : grids) {
+            int sumlv = 0;
+            for (int a = 0; a < N; ++a) sumlv += g.lv[a];
+            if (sumlv > 20) return fail(AMFRW_ETOOBIG, "a component grid has more than 2^20 Inner nodes");
+            const bool warp = (1 << sumlv) <= kWarpMaxL;
+            Layout lay = make_layout(N, g.lv, mixed, warp);
+            if (lay.total > smem_cap) return fail(AMFRW_ETOOBIG, "a component grid does not fit in shared memory");
+            Tmp t{};
+            t.it.inst = i;
+            t.it.out_idx = (int32_t)P.coefs.size();
+            t.it.L = lay.L;
+            memcpy(t.it.lv, g.lv, sizeof(t.it.lv));
+            t.it.state_off = -1;
+            t.L = lay.L;
+            t.N = N;
+            t.mixed = mixed;
+            t.warp = warp;
+            t.smem_group = lay.total;
+            t.lu_bytes = warp ? 0 : (int64_t)lay.nlu * (mixed ? 4 : 8);
+            all.push_back(t);
+            P.coefs.push_back(g.coef);
+        }
+        P.insts.push_back(I);
+        P.dim = N;
+    }
+    P.n_grids = (int)P.coefs.size();
+    std::stable_sort(all.begin(), all.end(), [](const Tmp& a, const Tmp& b) {
+        return std::make_tuple(a.N, a.mixed, a.warp, -a.L) < std::make_tuple(b.N, b.mixed, b.warp, -b.L);
+    });
+    const int sms = num_sms();
+    for (size_t k = 0; k < all.size();) {
+        size_t e = k;
+        int gmax = 0, lmax = 0;
+        int64_t lumax = 0;
+        while (e < all.size() && all[e].N == all[k].N && all[e].mixed == all[k].mixed &&
+               all[e].warp == all[k].warp) {
+            gmax = std::max(gmax, all[e].smem_group);
+            lmax = std::max(lmax, all[e].L);
+            lumax = std::max(lumax, all[e].lu_bytes);
+            ++e;
+        }
+        LaunchClass c{};
+        c.N = all[k].N;
+        c.mixed = all[k].mixed;
+        c.warp = all[k].warp;
+        c.item_begin = (int)P.items.size();
+        c.item_count = (int)(e - k);
+        c.smem_group = gmax;
+        if (c.warp) {
+            int wpb = std::min(kWarpsPerBlock, std::max(1, smem_cap / gmax));
+            c.block = 32 * wpb;
+            c.smem = (size_t)gmax * wpb;
+        } else {
+            int b = 64;
+            while (b < 512 && b * 8 < lmax) b *= 2;
+            c.block = b;
+            c.smem = (size_t)gmax;
+        }
+        const int per_sm = occ_for(c.N)(c.mixed, c.warp, c.block, c.smem);
+        if (per_sm < 1) return fail(AMFRW_ETOOBIG, "no resident block possible for a launch class");
+        const int groups_per_block = c.warp ? c.block / 32 : 1;
+        const int need = (c.item_count + groups_per_block - 1) / groups_per_block;
+        c.grid = std::max(1, std::min(need, per_sm * sms));
+        c.lu_stride = align256(lumax);
+        c.lu_offset = P.lu_scratch_len;
+        P.lu_scratch_len += c.lu_stride * c.grid;
+        for (size_t q = k; q < e; ++q) P.items.push_back(all[q].it);
+        P.classes.push_back(c);
+        k = e;
+    }
+    return AMFRW_OK;
+}
+
+// Releases the host vectors of a plan built in place for amfrw_solve_noalloc.
+// The plan's destructor is never run on that path because it would call
+// cudaFree (on null pointers).
+void noalloc_release_host(Plan& P)
+{
+    std::vector<InstDev>().swap(P.insts);
+    std::vector<Item>().swap(P.items);
+    std::vector<double>().swap(P.coefs);
+    std::vector<int8_t>().swap(P.levels);
+    std::vector<LaunchClass>().swap(P.classes);
+    P.d_insts = nullptr; P.d_items = nullptr; P.d_coefs = nullptr; P.d_u = nullptr;
+    P.d_prices = nullptr; P.d_queue = nullptr; P.d_flag = nullptr; P.d_state = nullptr;
+    P.d_lu = nullptr;
+}
+
+int noalloc_run(const amfrw_params* ps, int n, double* d_prices_out, cudaStream_t stream, Plan& P)
+{
+    int st = noalloc_plan(ps, n, P);
+    if (st != AMFRW_OK) return st;
+    const int s0 = P.insts[0].n_steps;
+    for (const InstDev& I : P.insts)
+        if (I.n_steps != s0) return fail(AMFRW_EINVAL, "all instances must use the same n_steps");
+    // carve the fixed array: records, grid list, coefficients, values, counters, factors
+    const int64_t o_inst = 0;
+    const int64_t o_item = align256(o_inst + (int64_t)(sizeof(InstDev) * P.insts.size()));
+    const int64_t o_coef = align256(o_item + (int64_t)(sizeof(Item) * P.items.size()));
+    const int64_t o_u = align256(o_coef + (int64_t)(sizeof(double) * P.coefs.size()));
+    const int64_t o_queue = align256(o_u + (int64_t)(sizeof(double) * P.coefs.size()));
+    const int64_t o_flag = align256(o_queue + (int64_t)(sizeof(int32_t) * P.classes.size()));
+    const int64_t o_lu = align256(o_flag + (int64_t)sizeof(int32_t));
+    const int64_t total = o_lu + P.lu_scratch_len;
+    if (total > (int64_t)AMFRW_NOALLOC_SCRATCH_BYTES)
+        return fail(AMFRW_ETOOBIG, "problem needs " + std::to_string(total) +
+                                       " bytes of scratch; amfrw_solve_noalloc is limited to " +
+                                       std::to_string((long long)AMFRW_NOALLOC_SCRATCH_BYTES));
+    unsigned char* base = nullptr;
+    st = noalloc_scratch(&base);
+    if (st != AMFRW_OK) return st;
+    P.stream = stream;
+    P.d_insts = reinterpret_cast<InstDev*>(base + o_inst);
+    P.d_items = reinterpret_cast<Item*>(base + o_item);
+    P.d_coefs = reinterpret_cast<double*>(base + o_coef);
+    P.d_u = reinterpret_cast<double*>(base + o_u);
+    P.d_queue = reinterpret_cast<int32_t*>(base + o_queue);
+    P.d_flag = reinterpret_cast<int32_t*>(base + o_flag);
+    P.d_lu = P.lu_scratch_len > 0 ? base + o_lu : nullptr;
+    // the array keeps the previous call's contents: the records are rewritten,
+    // the per-grid values cleared, and run_solve / run_combine zero the counters
+    CUDA_TRY(cudaMemcpyAsync(P.d_insts, P.insts.data(), sizeof(InstDev) * P.insts.size(),
+                             cudaMemcpyHostToDevice, stream));
+    CUDA_TRY(cudaMemcpyAsync(P.d_items, P.items.data(), sizeof(Item) * P.items.size(),
+                             cudaMemcpyHostToDevice, stream));
+    CUDA_TRY(cudaMemcpyAsync(P.d_coefs, P.coefs.data(), sizeof(double) * P.coefs.size(),
+                             cudaMemcpyHostToDevice, stream));
+    CUDA_TRY(cudaMemsetAsync(P.d_u, 0, sizeof(double) * P.coefs.size(), stream));
+    st = run_solve(P, s0, 0);
+    if (st != AMFRW_OK) return st;
+    return run_combine(P, d_prices_out);
+}
+
+}  // namespace
+
+extern "C" int amfrw_solve_noalloc(const amfrw_params* ps, int32_t n, double* d_prices_out,
+                                   void* cuda_stream)
+{
+    if (!d_prices_out) return fail(AMFRW_EINVAL, "d_prices_out is NULL");
+    alignas(Plan) unsigned char buf[sizeof(Plan)];
+    Plan* P = new (buf) Plan();
+    const int st = noalloc_run(ps, n, d_prices_out, (cudaStream_t)cuda_stream, *P);
+    noalloc_release_host(*P);
+    return st;
+}

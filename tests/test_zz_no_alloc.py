@@ -1,0 +1,56 @@
+"""amfrw_solve_noalloc, the entry point for callers that cannot allocate
+device memory (their memory belongs to another allocator, or they cannot
+afford cudaMalloc/cudaFree and the device-wide synchronisation of a free).
+
+It must price exactly like amfrw_solve_batch, the allocating entry point, and
+keep doing so on a second call in a row, because every call reuses the same
+fixed device array and inherits the previous call's contents.  Two problem
+sets are used: d=4 level-5 swaptions (grids solved one per warp) and the
+65x65 full grid in FP64 (solved by a whole block, whose line-solve factors
+live in the fixed array).  This file is collected last on purpose.
+"""
+import numpy as np
+import pytest
+
+from paper_2408_00559_gb300 import _lib as B
+from paper_2408_00559_gb300 import build as BLD
+from paper_2408_00559_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    BLD.build()
+    B.lib()
+
+
+@pytest.mark.parametrize("which", ["c2_batch", "c1_full_grid", "mixed_d6"])
+def test_noalloc_matches_allocating_entry_point_twice(which):
+    import torch
+    if which == "c2_batch":
+        insts = W.batch("c2", 48, start=321)
+    elif which == "c1_full_grid":
+        insts = [W.c1_instance()]
+    else:
+        insts = [W.small_instance(6, 3, psi=1, steps=5, seed=9, precision="mixed")]
+    ref = B.solve_batch(insts)
+    out = torch.full((len(insts),), float("nan"), dtype=torch.float64, device="cuda")
+    for call in range(2):
+        out.fill_(float("nan"))
+        B.solve_noalloc(insts, out.data_ptr())
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        assert np.all(np.isfinite(got)), call
+        assert np.all(np.abs(got - ref) <= TOL64 * np.abs(ref)), (call, got - ref)
+
+
+def test_noalloc_rejects_problems_beyond_its_array():
+    import torch
+    insts = W.batch("c2", 4000)  # needs more than AMFRW_NOALLOC_SCRATCH_BYTES
+    out = torch.zeros(len(insts), dtype=torch.float64, device="cuda")
+    with pytest.raises(B.AmfrwError) as e:
+        B.solve_noalloc(insts, out.data_ptr())
+    assert e.value.status == 7 and "limited to" in str(e.value)
