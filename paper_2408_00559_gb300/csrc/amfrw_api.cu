@@ -37,7 +37,7 @@ int fail(int status, const std::string& msg)
             return fail(AMFRW_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
-constexpr int kWarpMaxL = 256;         // grids up to this many Inner nodes: one warp each
+constexpr int kWarpMaxL = 64;          // grids up to this many Inner nodes: one warp each
 constexpr int kWarpsPerBlock = 4;
 
 bool finite(double x) { return std::isfinite(x); }
@@ -273,7 +273,17 @@ struct Plan {
     }
 };
 
-int build_plan(const amfrw_params* ps, int n, void* stream, bool keep_state, Plan& P)
+int log2i(int v)
+{
+    int r = 0;
+    while ((1 << (r + 1)) <= v) ++r;
+    return r;
+}
+
+// Host-side plan: validated instances, grid list grouped into launch classes
+// (largest grids first), launch shapes and the size of the line-solve scratch.
+// No device memory is touched.
+int plan_host(const amfrw_params* ps, int n, bool keep_state, Plan& P)
 {
     if (n < 1) return fail(AMFRW_EINVAL, "need at least one instance");
     if (!ps) return fail(AMFRW_EINVAL, "params is NULL");
@@ -287,18 +297,22 @@ int build_plan(const amfrw_params* ps, int n, void* stream, bool keep_state, Pla
         const amfrw_params* p = ps + i;
         std::vector<GridSpec> grids = enumerate(p->n_rates + 1, p->level, p->psi, p->full_grid != 0);
         for (const GridSpec& g : grids) {
-            int sumlv = 0;
-            for (int a = 0; a <= p->n_rates; ++a) sumlv += g.lv[a];
+            int sumlv = 0, maxlv = 0;
+            for (int a = 0; a <= p->n_rates; ++a) {
+                sumlv += g.lv[a];
+                maxlv = std::max(maxlv, (int)g.lv[a]);
+            }
             if (sumlv > 20)
                 return fail(AMFRW_ETOOBIG, "instance " + std::to_string(i) +
                                                ": a component grid has more than 2^20 Inner nodes");
+            if (maxlv > 5 + kRowsLogCta)
+                return fail(AMFRW_ETOOBIG, "instance " + std::to_string(i) +
+                                               ": an axis has more than 256 Inner nodes");
         }
     }
-    CUDA_TRY(cudaGetDevice(&P.device));
-    P.stream = (cudaStream_t)stream;
     P.n_inst = n;
     const int smem_cap = max_smem_optin();
-    struct Tmp { Item it; int L; int N; bool mixed; bool warp; int smem_group; int64_t lu_bytes; };
+    struct Tmp { Item it; int L; int N; bool mixed; bool warp; int smem_group; };
     std::vector<Tmp> all;
     int64_t state_off = 0;
     for (int i = 0; i < n; ++i) {
@@ -313,7 +327,7 @@ int build_plan(const amfrw_params* ps, int n, void* stream, bool keep_state, Pla
             int Lg = 1;
             for (int a = 0; a < N; ++a) Lg <<= g.lv[a];
             const bool warp = Lg <= kWarpMaxL;
-            Layout lay = make_layout(N, g.lv, mixed, warp);
+            Layout lay = make_layout(N, g.lv, mixed, warp, 5);
             if (lay.total > smem_cap)
                 return fail(AMFRW_ETOOBIG, "component grid with " + std::to_string(lay.L) +
                                                " Inner nodes needs " + std::to_string(lay.total) +
@@ -331,7 +345,6 @@ int build_plan(const amfrw_params* ps, int n, void* stream, bool keep_state, Pla
             t.mixed = mixed;
             t.warp = warp;
             t.smem_group = lay.total;
-            t.lu_bytes = warp ? 0 : (int64_t)lay.nlu * (mixed ? 4 : 8);
             all.push_back(t);
             P.coefs.push_back(g.coef);
             for (int a = 0; a < kMaxDim; ++a) P.levels.push_back(a < N ? g.lv[a] : 0);
@@ -341,7 +354,6 @@ int build_plan(const amfrw_params* ps, int n, void* stream, bool keep_state, Pla
     }
     P.n_grids = (int)P.coefs.size();
     P.state_len = state_off;
-    // group by launch class, largest grids first within a class (LPT order)
     std::stable_sort(all.begin(), all.end(), [](const Tmp& a, const Tmp& b) {
         return std::make_tuple(a.N, a.mixed, a.warp, -a.L) < std::make_tuple(b.N, b.mixed, b.warp, -b.L);
     });
@@ -349,12 +361,10 @@ int build_plan(const amfrw_params* ps, int n, void* stream, bool keep_state, Pla
     for (size_t k = 0; k < all.size();) {
         size_t e = k;
         int gmax = 0, lmax = 0;
-        int64_t lumax = 0;
         while (e < all.size() && all[e].N == all[k].N && all[e].mixed == all[k].mixed &&
                all[e].warp == all[k].warp) {
             gmax = std::max(gmax, all[e].smem_group);
             lmax = std::max(lmax, all[e].L);
-            lumax = std::max(lumax, all[e].lu_bytes);
             ++e;
         }
         LaunchClass c{};
@@ -364,6 +374,7 @@ int build_plan(const amfrw_params* ps, int n, void* stream, bool keep_state, Pla
         c.item_begin = (int)P.items.size();
         c.item_count = (int)(e - k);
         c.smem_group = gmax;
+        int64_t lumax = 0;
         if (c.warp) {
             int wpb = std::min(kWarpsPerBlock, std::max(1, smem_cap / gmax));
             c.block = 32 * wpb;
@@ -373,6 +384,10 @@ int build_plan(const amfrw_params* ps, int n, void* stream, bool keep_state, Pla
             while (b < 512 && b * 8 < lmax) b *= 2;
             c.block = b;
             c.smem = (size_t)gmax;
+            for (size_t q = k; q < e; ++q) {
+                Layout lay = make_layout(c.N, all[q].it.lv, c.mixed, false, log2i(b));
+                lumax = std::max<int64_t>(lumax, (int64_t)lay.nlu * (c.mixed ? 4 : 8));
+            }
         }
         const int per_sm = occ_for(c.N)(c.mixed, c.warp, c.block, c.smem);
         if (per_sm < 1)
@@ -388,6 +403,15 @@ int build_plan(const amfrw_params* ps, int n, void* stream, bool keep_state, Pla
         P.classes.push_back(c);
         k = e;
     }
+    return AMFRW_OK;
+}
+
+int build_plan(const amfrw_params* ps, int n, void* stream, bool keep_state, Plan& P)
+{
+    int st = plan_host(ps, n, keep_state, P);
+    if (st != AMFRW_OK) return st;
+    CUDA_TRY(cudaGetDevice(&P.device));
+    P.stream = (cudaStream_t)stream;
     // device buffers
     CUDA_TRY(cudaMalloc(&P.d_insts, sizeof(InstDev) * P.insts.size()));
     CUDA_TRY(cudaMalloc(&P.d_items, sizeof(Item) * P.items.size()));
@@ -744,104 +768,6 @@ int noalloc_scratch(unsigned char** out)
 
 int64_t align256(int64_t x) { return (x + 255) & ~(int64_t)255; }
 
-// The same grid list and launch classes as the allocating path, built on the
-// host only; lu offsets are relative to the Thomas-factor region.
-int noalloc_plan(const amfrw_params* ps, int n, Plan& P)
-{
-    if (n < 1) return fail(AMFRW_EINVAL, "need at least one instance");
-    if (!ps) return fail(AMFRW_EINVAL, "params is NULL");
-    for (int i = 0; i < n; ++i) {
-        int st = validate(ps + i);
-        if (st != AMFRW_OK) {
-            g_last_error = "instance " + std::to_string(i) + ": " + g_last_error;
-            return st;
-        }
-    }
-    P.n_inst = n;
-    const int smem_cap = max_smem_optin();
-    struct Tmp { Item it; int L; int N; bool mixed; bool warp; int smem_group; int64_t lu_bytes; };
-    std::vector<Tmp> all;
-    for (int i = 0; i < n; ++i) {
-        const amfrw_params* p = ps + i;
-        InstDev I = to_device(p);
-        const int N = I.N;
-        const bool mixed = p->precision == AMFRW_MIXED;
-        std::vector<GridSpec> grids = enumerate(N, p->level, p->psi, p->full_grid != 0);
-        I.grid_begin = (int32_t)P.coefs.size();
-        I.grid_count = (int32_t)grids.size();
-        for (const GridSpec& g : grids) {
-            int sumlv = 0;
-            for (int a = 0; a < N; ++a) sumlv += g.lv[a];
-            if (sumlv > 20) return fail(AMFRW_ETOOBIG, "a component grid has more than 2^20 Inner nodes");
-            const bool warp = (1 << sumlv) <= kWarpMaxL;
-            Layout lay = make_layout(N, g.lv, mixed, warp);
-            if (lay.total > smem_cap) return fail(AMFRW_ETOOBIG, "a component grid does not fit in shared memory");
-            Tmp t{};
-            t.it.inst = i;
-            t.it.out_idx = (int32_t)P.coefs.size();
-            t.it.L = lay.L;
-            memcpy(t.it.lv, g.lv, sizeof(t.it.lv));
-            t.it.state_off = -1;
-            t.L = lay.L;
-            t.N = N;
-            t.mixed = mixed;
-            t.warp = warp;
-            t.smem_group = lay.total;
-            t.lu_bytes = warp ? 0 : (int64_t)lay.nlu * (mixed ? 4 : 8);
-            all.push_back(t);
-            P.coefs.push_back(g.coef);
-        }
-        P.insts.push_back(I);
-        P.dim = N;
-    }
-    P.n_grids = (int)P.coefs.size();
-    std::stable_sort(all.begin(), all.end(), [](const Tmp& a, const Tmp& b) {
-        return std::make_tuple(a.N, a.mixed, a.warp, -a.L) < std::make_tuple(b.N, b.mixed, b.warp, -b.L);
-    });
-    const int sms = num_sms();
-    for (size_t k = 0; k < all.size();) {
-        size_t e = k;
-        int gmax = 0, lmax = 0;
-        int64_t lumax = 0;
-        while (e < all.size() && all[e].N == all[k].N && all[e].mixed == all[k].mixed &&
-               all[e].warp == all[k].warp) {
-            gmax = std::max(gmax, all[e].smem_group);
-            lmax = std::max(lmax, all[e].L);
-            lumax = std::max(lumax, all[e].lu_bytes);
-            ++e;
-        }
-        LaunchClass c{};
-        c.N = all[k].N;
-        c.mixed = all[k].mixed;
-        c.warp = all[k].warp;
-        c.item_begin = (int)P.items.size();
-        c.item_count = (int)(e - k);
-        c.smem_group = gmax;
-        if (c.warp) {
-            int wpb = std::min(kWarpsPerBlock, std::max(1, smem_cap / gmax));
-            c.block = 32 * wpb;
-            c.smem = (size_t)gmax * wpb;
-        } else {
-            int b = 64;
-            while (b < 512 && b * 8 < lmax) b *= 2;
-            c.block = b;
-            c.smem = (size_t)gmax;
-        }
-        const int per_sm = occ_for(c.N)(c.mixed, c.warp, c.block, c.smem);
-        if (per_sm < 1) return fail(AMFRW_ETOOBIG, "no resident block possible for a launch class");
-        const int groups_per_block = c.warp ? c.block / 32 : 1;
-        const int need = (c.item_count + groups_per_block - 1) / groups_per_block;
-        c.grid = std::max(1, std::min(need, per_sm * sms));
-        c.lu_stride = align256(lumax);
-        c.lu_offset = P.lu_scratch_len;
-        P.lu_scratch_len += c.lu_stride * c.grid;
-        for (size_t q = k; q < e; ++q) P.items.push_back(all[q].it);
-        P.classes.push_back(c);
-        k = e;
-    }
-    return AMFRW_OK;
-}
-
 // Releases the host vectors of a plan built in place for amfrw_solve_noalloc.
 // The plan's destructor is never run on that path because it would call
 // cudaFree (on null pointers).
@@ -859,7 +785,7 @@ void noalloc_release_host(Plan& P)
 
 int noalloc_run(const amfrw_params* ps, int n, double* d_prices_out, cudaStream_t stream, Plan& P)
 {
-    int st = noalloc_plan(ps, n, P);
+    int st = plan_host(ps, n, false, P);
     if (st != AMFRW_OK) return st;
     const int s0 = P.insts[0].n_steps;
     for (const InstDev& I : P.insts)

@@ -38,9 +38,13 @@ struct Item {
 // to size dynamic shared memory, the device to place the arrays; both call
 // this one function so they cannot disagree.
 struct Layout {
-    int32_t cd, cf, tabd, tabf, pay, lu, Z, ZZ, H, FY, K1, K0, Kw, total;
-    int32_t L, Lp, Lr, ntab, npay, nlu;
+    int32_t cd, cf, tabd, tabf, pay, lu, Z, ZZ, H, FY, K1, K0, Kw, D, C, total;
+    int32_t L, Lp, Lr, ntab, npay, nlu, ncoef;
 };
+
+// Per-node coefficients of the difference-array stencil (FP64 warp groups):
+// N diagonal, 1 centre, N(N-1)/2 cross, N-2 drift, 1 for dt F(payoff).
+AMFRW_HD int node_coefs(int N) { return N + 1 + N * (N - 1) / 2 + (N - 2) + 1; }
 
 template <typename T>
 struct Consts {
@@ -54,9 +58,35 @@ struct Consts {
 
 AMFRW_HD int32_t align16(int32_t x) { return (x + 15) & ~15; }
 
-// lu_smem: whether the Thomas factors live in shared memory (warp groups) or
-// in the group's slice of a global scratch array (CTA groups, large grids).
-AMFRW_HD Layout make_layout(int N, const int8_t* lv, bool mixed, bool lu_smem)
+// Rows of a line per lane in a line solve: at most 2 for warp groups (grids of
+// at most 64 Inner nodes), at most 8 for CTA groups.
+constexpr int kRowsLogWarp = 1;
+constexpr int kRowsLogCta = 3;
+AMFRW_HD int rows_log(bool warp) { return warp ? kRowsLogWarp : kRowsLogCta; }
+
+// Lanes per line (as log2) for the directional solves along an axis with
+// 2^mlog rows, on a grid of 2^llog Inner nodes solved by a group of 2^tlog
+// threads: enough lanes that the whole group is busy, at most 2^rlog rows per
+// lane, at most 32 lanes (one warp) and at most one row per lane.
+AMFRW_HD int lanes_log(int mlog, int llog, int tlog, int rlog)
+{
+    int p = tlog + mlog - llog;
+    if (p < mlog - rlog) p = mlog - rlog;
+    if (p < 0) p = 0;
+    if (p > mlog) p = mlog;
+    if (p > 5) p = 5;
+    return p;
+}
+
+// Values stored per matrix row for an axis solved with 2^plog lanes per line:
+// PCR multipliers (alpha, gamma) of each level, then the Thomas factors
+// (lower, 1/pivot, upper/pivot) of the reduced interleaved systems.
+AMFRW_HD int lu_row_values(int plog) { return 2 * plog + 3; }
+
+// lu_smem: true for warp groups (line-solve factors in shared memory), false
+// for CTA groups (factors in the group's slice of a global scratch array);
+// tlog: log2 of the group's thread count.
+AMFRW_HD Layout make_layout(int N, const int8_t* lv, bool mixed, bool lu_smem, int tlog)
 {
     Layout y{};
     int L = 1, sumM = 0, npay = 0;
@@ -73,7 +103,14 @@ AMFRW_HD Layout make_layout(int N, const int8_t* lv, bool mixed, bool lu_smem)
     y.Lr = L >> lv[N - 1];
     y.ntab = 3 * sumM + MV;
     y.npay = 2 * npay;
-    y.nlu = 3 * (MV * sumM + MV);
+    int llog = 0;
+    for (int i = 0; i < N; ++i) llog += lv[i];
+    int nlu = 0;
+    for (int i = 0; i < N; ++i) {
+        const int rows = (i < N - 1 ? MV : 1) << lv[i];  // classes x rows
+        nlu += rows * lu_row_values(lanes_log(lv[i], llog, tlog, rows_log(lu_smem)));
+    }
+    y.nlu = nlu;
     const int sk = mixed ? 4 : 8;  // bytes of an increment / table value
     int o = 0;
     y.cd = o;   o = align16(o + (int)sizeof(Consts<double>));
@@ -89,6 +126,11 @@ AMFRW_HD Layout make_layout(int N, const int8_t* lv, bool mixed, bool lu_smem)
     y.K1 = o;   o = align16(o + sk * y.Lp);
     y.K0 = o;   o = align16(o + sk * y.Lp);
     y.Kw = o;   o = align16(o + sk * y.Lp);
+    // FP64 warp groups: central differences per axis and per-node coefficients
+    const bool diff = !mixed && lu_smem;
+    y.ncoef = diff ? node_coefs(N) : 0;
+    y.D = o;    o = align16(o + (diff ? 8 * N * y.Lp : 0));
+    y.C = o;    o = align16(o + 8 * y.ncoef * y.Lp);
     y.total = o;
     return y;
 }

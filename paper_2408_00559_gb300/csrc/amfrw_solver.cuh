@@ -53,13 +53,15 @@ struct Shape {
     int lv[N], M[N], sh[N], Sp[N];
     int toff[N];   // coefficient tables: rate axis a -> [dI | pw | ph] of M_a each; V -> v2
     int poff[N];   // payoff tables: rate axis a -> M_a + 1 entries (Outer node included)
-    int luoff[N];  // Thomas factors: rate axis -> M_V classes x M_a rows x 3; V -> M_V x 3
+    int luoff[N];  // line-solve factors: rate axis -> M_V classes x M_a rows; V -> M_V rows
+    int plog[N];   // log2 lanes per line in the directional solves
+    int luS[N];    // factor values per matrix row (2 plog + 3)
     int L, Lr, pad, phalf;
     __device__ __forceinline__ int padded(int t) const { return t + pad * (t >> lv[0]); }
 };
 
 template <int N>
-__device__ __forceinline__ void make_shape(Shape<N>& s, const int8_t* lv)
+__device__ __forceinline__ void make_shape(Shape<N>& s, const int8_t* lv, int tlog, int rlog)
 {
     int sh = 0;
 #pragma unroll
@@ -86,13 +88,17 @@ __device__ __forceinline__ void make_shape(Shape<N>& s, const int8_t* lv)
         o += 3 * s.M[i];
         s.poff[i] = po;
         po += s.M[i] + 1;
-        s.luoff[i] = lo;
-        lo += 3 * s.M[N - 1] * s.M[i];
     }
     s.toff[N - 1] = o;
     s.poff[N - 1] = po;
-    s.luoff[N - 1] = lo;
     s.phalf = po;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        s.plog[i] = lanes_log(s.lv[i], sh, tlog, rlog);
+        s.luS[i] = lu_row_values(s.plog[i]);
+        s.luoff[i] = lo;
+        lo += ((i < N - 1 ? s.M[N - 1] : 1) << s.lv[i]) * s.luS[i];
+    }
 }
 
 template <int N>
@@ -229,16 +235,241 @@ __device__ __forceinline__ TC stencil_acc(const Shape<N>& s, const int (&j)[N], 
     return acc;
 }
 
+// ------------------------------------------- difference-array stencil
+// FP64 warp groups evaluate Sketch 1 in two passes.  Pass 1 stores, per
+// axis k, the central difference D_k = X(J+E_k) - X(J-E_k) (zero on Outer
+// nodes and, by the ghost node Y_{J+E_k} = Y_{J-E_k}, zero on the upper face
+// of axis k).  Pass 2 combines, with per-node coefficients computed once per
+// grid (every coefficient of eqs. coef_diff/mix/adv carries V^2, folded in):
+//   F_0(X)_J = sum_i d_i/h_i^2 (X+_i + X-_i) - 2 sum_i d_i/h_i^2 X_J
+//            + sum_{i<k} m_ik/(4 h_i h_k) (D_k(J+E_i) - D_k(J-E_i))
+//            + sum_i a_i/(2 h_i) D_i(J)
+// with the same ghost reflection on X and D.  This reproduces every rule of
+// Sketch 1 (zero cross and first differences on upper faces, the doubled
+// Neumann second difference, Outer values) with about half the FP64
+// operations of the direct form.
+template <int N>
+struct CIdx {
+    static constexpr int diag = 0;                           // N
+    static constexpr int ctr = N;                            // 1
+    static constexpr int cross = N + 1;                      // N(N-1)/2, (i,k) i<k row by row
+    static constexpr int drift = N + 1 + N * (N - 1) / 2;    // N-2, axes 1..N-2
+    static constexpr int fg = drift + N - 2;                 // dt * F(payoff)
+    __device__ static constexpr int pair(int i, int k) { return cross + i * (2 * N - i - 1) / 2 + (k - i - 1); }
+};
+
+template <int N>
+__device__ void build_node_coefs(const Shape<N>& s, const double* tabd, const Consts<double>& c,
+                                 const double* H, double* C, int Lp, int rank, int gsize)
+{
+    using I = CIdx<N>;
+    for (int t = rank; t < s.L; t += gsize) {
+        int j[N];
+        decode<N>(s, t, j);
+        const int J = s.padded(t);
+        const double v2 = tabd[s.toff[N - 1] + j[N - 1] - 1];
+        double sum = 0.0;
+#pragma unroll
+        for (int i = 0; i < N - 1; ++i) {
+            const double cdi = tabd[s.toff[i] + j[i] - 1] * v2;
+            C[(I::diag + i) * Lp + J] = cdi;
+            sum += cdi;
+        }
+        const double cdv = c.cV * v2;
+        C[(I::diag + N - 1) * Lp + J] = cdv;
+        sum += cdv;
+        C[I::ctr * Lp + J] = -2.0 * sum;
+#pragma unroll
+        for (int i = 0; i < N - 1; ++i) {
+            const double pwi = tabd[s.toff[i] + s.M[i] + j[i] - 1];
+#pragma unroll
+            for (int k = i + 1; k < N; ++k) {
+                const double m = (k < N - 1) ? c.rm[i][k] * pwi * tabd[s.toff[k] + s.M[k] + j[k] - 1] * v2
+                                             : c.sm[i] * pwi * v2;
+                C[I::pair(i, k) * Lp + J] = m;
+            }
+            if (i >= 1) {
+                double S = 0.0;
+#pragma unroll
+                for (int r = 1; r <= i; ++r) S += c.rh[i][r] * tabd[s.toff[r] + 2 * s.M[r] + j[r] - 1];
+                C[(I::drift + i - 1) * Lp + J] = pwi * S * c.g2[i] * v2;
+            }
+        }
+        C[I::fg * Lp + J] = c.dt * v2 * H[t & (s.Lr - 1)];
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void diff_pass(const Shape<N>& s, const double* X, double* D, int Lp,
+                                          int rank, int gsize)
+{
+    for (int t = rank; t < s.L; t += gsize) {
+        int j[N];
+        decode<N>(s, t, j);
+        const int J = s.padded(t);
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            const bool top = j[k] == s.M[k];
+            const double xm = (j[k] > 1) ? X[J - s.Sp[k]] : 0.0;
+            D[k * Lp + J] = top ? 0.0 : X[J + s.Sp[k]] - xm;
+        }
+    }
+}
+
+template <int N>
+__device__ __forceinline__ double diff_F(const Shape<N>& s, const int (&j)[N], int J,
+                                         const double* X, const double* D, const double* C, int Lp)
+{
+    using I = CIdx<N>;
+    double f = C[I::ctr * Lp + J] * X[J];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const double xm = (j[i] > 1) ? X[J - s.Sp[i]] : 0.0;
+        const double xp = (j[i] == s.M[i]) ? xm : X[J + s.Sp[i]];
+        f += C[(I::diag + i) * Lp + J] * (xp + xm);
+    }
+#pragma unroll
+    for (int i = 0; i < N - 1; ++i) {
+        if (j[i] != s.M[i]) {
+            const bool li = j[i] > 1;
+#pragma unroll
+            for (int k = i + 1; k < N; ++k) {
+                const double dp = D[k * Lp + J + s.Sp[i]];
+                const double dm = li ? D[k * Lp + J - s.Sp[i]] : 0.0;
+                f += C[I::pair(i, k) * Lp + J] * (dp - dm);
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 1; i < N - 1; ++i) f += C[(I::drift + i - 1) * Lp + J] * D[i * Lp + J];
+    return f;
+}
+
 // ----------------------------------------------------------- line solves
 // (I - nu dt A_axis) X = G on every line along `axis` (Lemma ls, eq.
-// decomp1) by Thomas elimination with the precomputed factors
-// (lower_r, 1/beta_r, gamma_r) of the line's class; one thread per line.
-// src may equal dst.  epi(J, x) sees every solved value.
-template <int N, typename T, class Epi>
+// decomp1).  A line of M rows is shared by P = 2^plog lanes of one warp; lane
+// p holds rows p, p+P, p+2P, ... (R = M/P <= kMaxRows of them).  plog levels
+// of parallel cyclic reduction over warp shuffles decouple the line into P
+// interleaved tridiagonal systems, which each lane then solves by Thomas
+// elimination.  The matrices do not change in time, so every multiplier and
+// Thomas factor comes from tables built once per grid (pcr_setup).  At a
+// wrap-around (row p+Pq's neighbour at distance d lives in the previous or
+// next row slot of another lane) the sending lane picks the slot, so each
+// level costs one shuffle per direction.
+
+template <typename T>
+__device__ __forceinline__ T shfl(T v, int src, int width)
+{
+    return __shfl_sync(0xffffffffu, v, src, width);
+}
+
+// Row r of (I - nu dt A_axis) for line class cls: lower a, diagonal b, upper c.
+template <int N>
+__device__ __forceinline__ void matrix_row(const Shape<N>& s, const double* tabd,
+                                           const Consts<double>& c, int axis, int cls, int r,
+                                           double& a, double& b, double& u)
+{
+    const int M = s.M[axis];
+    const double delta = (axis < N - 1) ? tabd[s.toff[axis] + r] * tabd[s.toff[N - 1] + cls]
+                                        : c.cV * tabd[s.toff[N - 1] + r];
+    const double nd = c.nudt * delta;
+    b = 1.0 + 2.0 * nd;
+    u = (r < M - 1) ? -nd : 0.0;
+    a = (r == 0) ? 0.0 : ((r < M - 1) ? -nd : -2.0 * nd);
+}
+
+// The PCR multipliers and Thomas factors of every line class: the same
+// reduction as the solve, applied to the matrix coefficients (FP64).  Rows
+// are updated in ascending order; each lane keeps the pre-update values of
+// its previous row, which is the wrap-around neighbour the next row needs.
+template <int N, typename T, int RMAX>
+__device__ void pcr_setup(const Shape<N>& s, const double* tabd, const Consts<double>& c, T* lu,
+                          int rank, int gsize)
+{
+    for (int axis = 0; axis < N; ++axis) {
+        const int M = s.M[axis];
+        const int plog = s.plog[axis];
+        const int P = 1 << plog;
+        const int R = M >> plog;
+        const int S = s.luS[axis];
+        const int ncls = (axis < N - 1) ? s.M[N - 1] : 1;
+        const int lpr = gsize >> plog;
+        const int p = rank & (P - 1);
+        const int slot = rank >> plog;
+        for (int base = 0; base < ncls; base += lpr) {  // uniform across the group
+            const int cls = base + slot;
+            const bool act = cls < ncls;
+            const int cl = act ? cls : 0;
+            T* tb = lu + s.luoff[axis] + (cl * M + p) * S;
+            double a[RMAX], b[RMAX], u[RMAX];
+#pragma unroll
+            for (int q = 0; q < RMAX; ++q)
+                if (q < R) matrix_row<N>(s, tabd, c, axis, cl, p + P * q, a[q], b[q], u[q]);
+            for (int k = 0; k < plog; ++k) {
+                const int d = 1 << k;
+                const int sm = (p - d) & (P - 1), sp = (p + d) & (P - 1);
+                const bool wm = p < d, wp = p + d >= P;      // this lane receives across a wrap
+                const bool send_prev = p >= P - d;          // my receiver (p + d) wraps
+                const bool send_next = p < d;               // my receiver (p - d) wraps
+                double pa = 0.0, pb = 1.0, pu = 0.0;         // pre-update values of row q-1
+#pragma unroll
+                for (int q = 0; q < RMAX; ++q) {
+                    if (q < R) {
+                        const int qn = (q + 1 < RMAX) ? q + 1 : q;  // static after unrolling
+                        const bool nx = q + 1 < R;
+                        // to the lane above (p + d): my row q, or my row q-1 across the wrap
+                        const double a_m = shfl(send_prev ? pa : a[q], sm, P);
+                        const double b_m = shfl(send_prev ? pb : b[q], sm, P);
+                        const double u_m = shfl(send_prev ? pu : u[q], sm, P);
+                        // to the lane below (p - d): my row q, or my row q+1 across the wrap
+                        const double a_p = shfl(send_next ? (nx ? a[qn] : 0.0) : a[q], sp, P);
+                        const double b_p = shfl(send_next ? (nx ? b[qn] : 1.0) : b[q], sp, P);
+                        const double u_p = shfl(send_next ? (nx ? u[qn] : 0.0) : u[q], sp, P);
+                        const bool hm = !wm || q >= 1;
+                        const double al = hm ? a[q] / b_m : 0.0;
+                        const double ga = u[q] / b_p;  // identity row sent past the end
+                        if (act) {
+                            tb[q * P * S + 2 * k] = (T)al;
+                            tb[q * P * S + 2 * k + 1] = (T)(wp && !nx ? 0.0 : ga);
+                        }
+                        pa = a[q];
+                        pb = b[q];
+                        pu = u[q];
+                        const double gg = (wp && !nx) ? 0.0 : ga;
+                        b[q] = b[q] - al * u_m - gg * a_p;
+                        a[q] = -al * a_m;
+                        u[q] = -gg * u_p;
+                    }
+                }
+            }
+            // Thomas factors of the lane's interleaved system (rows coupled at distance P)
+            double gam = 0.0;
+#pragma unroll
+            for (int q = 0; q < RMAX; ++q) {
+                if (q < R) {
+                    const double inv = 1.0 / (b[q] - a[q] * gam);
+                    gam = u[q] * inv;
+                    if (act) {
+                        T* row = tb + q * P * S + 2 * plog;
+                        row[0] = (T)a[q];
+                        row[1] = (T)inv;
+                        row[2] = (T)gam;
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <int N, typename T, int RMAX, class Epi>
 __device__ __forceinline__ void sweep(const Shape<N>& s, int axis, const T* __restrict__ lu,
                                       const T* src, T* dst, int rank, int gsize, Epi epi)
 {
     const int M = s.M[axis];
+    const int plog = s.plog[axis];
+    const int P = 1 << plog;
+    const int R = M >> plog;
+    const int S = s.luS[axis];
     const int lvA = s.lv[axis];
     const int sh = s.sh[axis];
     const int Spa = s.Sp[axis];
@@ -246,25 +477,62 @@ __device__ __forceinline__ void sweep(const Shape<N>& s, int axis, const T* __re
     const int lo_mask = (1 << sh) - 1;
     const int MV1 = s.M[N - 1] - 1;
     const int shV = s.sh[N - 1];
-    for (int line = rank; line < nl; line += gsize) {
-        const int t0 = (line & lo_mask) | ((line >> sh) << (sh + lvA));
-        const int J0 = s.padded(t0);
+    const int lpr = gsize >> plog;
+    const int p = rank & (P - 1);
+    const int slot = rank >> plog;
+    for (int base = 0; base < nl; base += lpr) {  // uniform across the group
+        const int line = base + slot;
+        const bool act = line < nl;
+        const int ln = act ? line : 0;
+        const int t0 = (ln & lo_mask) | ((ln >> sh) << (sh + lvA));
+        const int J0 = s.padded(t0) + p * Spa;
         const int cls = (axis == N - 1) ? 0 : ((t0 >> shV) & MV1);
-        const T* tb = lu + s.luoff[axis] + cls * M * 3;
-        T y = T(0);
-        int J = J0;
-        for (int r = 0; r < M; ++r, J += Spa) {
-            y = (src[J] - tb[3 * r] * y) * tb[3 * r + 1];
-            dst[J] = y;
+        const T* tb = lu + s.luoff[axis] + (cls * M + p) * S;  // row p of the line
+        const int PS = P * S, PSp = P * Spa;
+        T x[RMAX];
+#pragma unroll
+        for (int q = 0; q < RMAX; ++q)
+            if (q < R) x[q] = act ? src[J0 + q * PSp] : T(0);
+        for (int k = 0; k < plog; ++k) {
+            const int d = 1 << k;
+            const int sm = (p - d) & (P - 1), sp = (p + d) & (P - 1);
+            const bool send_prev = p >= P - d;
+            const bool send_next = p < d;
+            T prev = T(0);  // pre-update value of this lane's row q-1
+#pragma unroll
+            for (int q = 0; q < RMAX; ++q) {
+                if (q < R) {
+                    const int qn = (q + 1 < RMAX) ? q + 1 : q;  // static after unrolling
+                    const T vm = shfl(send_prev ? prev : x[q], sm, P);
+                    const T vp = shfl(send_next ? ((q + 1 < R) ? x[qn] : T(0)) : x[q], sp, P);
+                    const T* row = tb + q * PS;
+                    prev = x[q];
+                    // multipliers are zero where the neighbour lies outside the line
+                    x[q] = x[q] - row[2 * k] * vm - row[2 * k + 1] * vp;
+                }
+            }
         }
-        J -= Spa;
-        T x = y;
-        epi(J, x);
-        for (int r = M - 2; r >= 0; --r) {
-            J -= Spa;
-            x = dst[J] - tb[3 * r + 2] * x;
-            dst[J] = x;
-            epi(J, x);
+        T y = T(0);
+#pragma unroll
+        for (int q = 0; q < RMAX; ++q) {
+            if (q < R) {
+                const T* row = tb + q * PS + 2 * plog;
+                y = (x[q] - row[0] * y) * row[1];
+                x[q] = y;
+            }
+        }
+#pragma unroll
+        for (int q = RMAX - 2; q >= 0; --q)
+            if (q < R - 1) x[q] = x[q] - tb[q * PS + 2 * plog + 2] * x[q + 1];
+        if (act) {
+#pragma unroll
+            for (int q = 0; q < RMAX; ++q) {
+                if (q < R) {
+                    const int J = J0 + q * PSp;
+                    dst[J] = x[q];
+                    epi(J, x[q]);
+                }
+            }
         }
     }
 }
@@ -352,36 +620,6 @@ __device__ void convert_consts(const Consts<double>& a, Consts<T>* b)
     }
 }
 
-// Thomas factors of (I - nu dt A_axis) for every line class (Lemma ls).
-template <int N, typename T>
-__device__ void build_lu(const Shape<N>& s, const double* tabd, const Consts<double>& c, T* lu,
-                         int rank, int gsize)
-{
-    const int MV = s.M[N - 1];
-    const int ncls = (N - 1) * MV + 1;
-    for (int q = rank; q < ncls; q += gsize) {
-        const int axis = (q == ncls - 1) ? N - 1 : q / MV;
-        const int cls = (axis == N - 1) ? 0 : q % MV;
-        const int M = s.M[axis];
-        T* tb = lu + s.luoff[axis] + cls * M * 3;
-        double gam = 0.0;
-        for (int r = 0; r < M; ++r) {
-            const double delta = (axis < N - 1)
-                                     ? tabd[s.toff[axis] + r] * tabd[s.toff[N - 1] + cls]
-                                     : c.cV * tabd[s.toff[N - 1] + r];
-            const double nd = c.nudt * delta;
-            const double diag = 1.0 + 2.0 * nd;
-            const double up = (r < M - 1) ? -nd : 0.0;
-            const double lo = (r == 0) ? 0.0 : ((r < M - 1) ? -nd : -2.0 * nd);
-            const double inv = 1.0 / (diag - lo * gam);
-            gam = up * inv;
-            tb[3 * r] = (T)lo;
-            tb[3 * r + 1] = (T)inv;
-            tb[3 * r + 2] = (T)gam;
-        }
-    }
-}
-
 __device__ __forceinline__ float2 split_df(double z)
 {
     const float hi = __double2float_rn(z);
@@ -396,9 +634,11 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
 {
     using TK = typename std::conditional<MIXED, float, double>::type;
     const InstDev& P = a.insts[it.inst];
+    constexpr int RMAX = 1 << (WARP ? kRowsLogWarp : kRowsLogCta);
+    const int tlog = WARP ? 5 : 31 - __clz(gsize);
     Shape<N> s;
-    make_shape<N>(s, it.lv);
-    const Layout lay = make_layout(N, it.lv, MIXED, WARP);
+    make_shape<N>(s, it.lv, tlog, rows_log(WARP));
+    const Layout lay = make_layout(N, it.lv, MIXED, WARP, tlog);
     Consts<double>* cd = reinterpret_cast<Consts<double>*>(base + lay.cd);
     Consts<TK>* ck = MIXED ? reinterpret_cast<Consts<TK>*>(base + lay.cf)
                            : reinterpret_cast<Consts<TK>*>(base + lay.cd);
@@ -417,6 +657,11 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
     TK* K1 = reinterpret_cast<TK*>(base + lay.K1);
     TK* K0 = reinterpret_cast<TK*>(base + lay.K0);
     TK* Kw = reinterpret_cast<TK*>(base + lay.Kw);
+    // FP64 warp groups use the difference-array stencil
+    constexpr bool DIFF = !MIXED && WARP;
+    double* Dd = reinterpret_cast<double*>(base + lay.D);
+    double* Cc = reinterpret_cast<double*>(base + lay.C);
+    const int Lp = lay.Lp;
 
     // 1. coefficient and payoff tables, constants
     build_tables<N>(s, P, tabd, pay, cd, rank, gsize);
@@ -425,7 +670,7 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
         for (int q = rank; q < lay.ntab; q += gsize) tabk[q] = (TK)tabd[q];
         if (rank == 0) convert_consts<TK>(*cd, ck);
     }
-    build_lu<N, TK>(s, tabd, *cd, lu, rank, gsize);
+    pcr_setup<N, TK, RMAX>(s, tabd, *cd, lu, rank, gsize);
 
     // 2. H = F(G)/V^2 on the rate grid (FP64), Z from the state or zero
     for (int tr = rank; tr < s.Lr; tr += gsize) {
@@ -448,22 +693,36 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
         if constexpr (MIXED) ZZ[J] = split_df(z);
     }
     gsync<WARP>();
+    if constexpr (DIFF) {
+        build_node_coefs<N>(s, tabd, *cd, (const double*)H, Cc, Lp, rank, gsize);
+        gsync<WARP>();
+    }
 
     const int Lr1 = s.Lr - 1;
     const TK* v2 = tabk + s.toff[N - 1] - 1;  // v2[j_V], 1-based
     const TK* luc = lu;
     auto sweeps_into = [&](TK* from, TK* to) {
-        sweep<N, TK>(s, 0, luc, from, to, rank, gsize, NoEpi());
+        sweep<N, TK, RMAX>(s, 0, luc, from, to, rank, gsize, NoEpi());
         gsync<WARP>();
         for (int ax = 1; ax < N; ++ax) {
-            sweep<N, TK>(s, ax, luc, to, to, rank, gsize, NoEpi());
+            sweep<N, TK, RMAX>(s, ax, luc, to, to, rank, gsize, NoEpi());
             gsync<WARP>();
         }
     };
 
+    using CI = CIdx<N>;
     for (int n = 0; n < a.steps; ++n) {
         // ---- stage 1: K^(0) = dt F(Y_n)
-        for (int t = rank; t < s.L; t += gsize) {
+        if constexpr (DIFF) {
+            diff_pass<N>(s, Z, Dd, Lp, rank, gsize);
+            gsync<WARP>();
+            for (int t = rank; t < s.L; t += gsize) {
+                int j[N];
+                decode<N>(s, t, j);
+                const int J = s.padded(t);
+                K0[J] = (TK)(Cc[CI::fg * Lp + J] + cd->dt * diff_F<N>(s, j, J, Z, Dd, Cc, Lp));
+            }
+        } else for (int t = rank; t < s.L; t += gsize) {
             int j[N];
             decode<N>(s, t, j);
             const int J = s.padded(t);
@@ -484,7 +743,17 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
         gsync<WARP>();
         sweeps_into(K0, Kw);
         // refinement: Khat = 2 K^(0) - K^(N) + theta dt F(K^(N))
-        for (int t = rank; t < s.L; t += gsize) {
+        if constexpr (DIFF) {
+            diff_pass<N>(s, (const double*)Kw, Dd, Lp, rank, gsize);
+            gsync<WARP>();
+            for (int t = rank; t < s.L; t += gsize) {
+                int j[N];
+                decode<N>(s, t, j);
+                const int J = s.padded(t);
+                const double f = diff_F<N>(s, j, J, (const double*)Kw, Dd, Cc, Lp);
+                K0[J] = (TK)(2.0 * (double)K0[J] - (double)Kw[J] + cd->thdt * f);
+            }
+        } else for (int t = rank; t < s.L; t += gsize) {
             int j[N];
             decode<N>(s, t, j);
             const int J = s.padded(t);
@@ -493,20 +762,30 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
         }
         gsync<WARP>();
         // N solves into K1; the last one also forms the stage-2 argument
-        sweep<N, TK>(s, 0, luc, K0, K1, rank, gsize, NoEpi());
+        sweep<N, TK, RMAX>(s, 0, luc, K0, K1, rank, gsize, NoEpi());
         gsync<WARP>();
         for (int ax = 1; ax < N; ++ax) {
             if (!MIXED && ax == N - 1) {  // FP64: Kw = Z + a21 K1
-                sweep<N, TK>(s, ax, luc, K1, K1, rank, gsize, [&](int J, TK x) {
+                sweep<N, TK, RMAX>(s, ax, luc, K1, K1, rank, gsize, [&](int J, TK x) {
                     Kw[J] = (TK)(Z[J] + kA21 * (double)x);
                 });
             } else {
-                sweep<N, TK>(s, ax, luc, K1, K1, rank, gsize, NoEpi());
+                sweep<N, TK, RMAX>(s, ax, luc, K1, K1, rank, gsize, NoEpi());
             }
             gsync<WARP>();
         }
         // ---- stage 2: K^(0) = dt F(Y_n + a21 K1) + q21 K1
-        for (int t = rank; t < s.L; t += gsize) {
+        if constexpr (DIFF) {
+            diff_pass<N>(s, (const double*)Kw, Dd, Lp, rank, gsize);
+            gsync<WARP>();
+            for (int t = rank; t < s.L; t += gsize) {
+                int j[N];
+                decode<N>(s, t, j);
+                const int J = s.padded(t);
+                const double f = diff_F<N>(s, j, J, (const double*)Kw, Dd, Cc, Lp);
+                K0[J] = (TK)(Cc[CI::fg * Lp + J] + cd->dt * f + kQ21 * (double)K1[J]);
+            }
+        } else for (int t = rank; t < s.L; t += gsize) {
             int j[N];
             decode<N>(s, t, j);
             const int J = s.padded(t);
@@ -527,7 +806,17 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
         }
         gsync<WARP>();
         sweeps_into(K0, Kw);
-        for (int t = rank; t < s.L; t += gsize) {
+        if constexpr (DIFF) {
+            diff_pass<N>(s, (const double*)Kw, Dd, Lp, rank, gsize);
+            gsync<WARP>();
+            for (int t = rank; t < s.L; t += gsize) {
+                int j[N];
+                decode<N>(s, t, j);
+                const int J = s.padded(t);
+                const double f = diff_F<N>(s, j, J, (const double*)Kw, Dd, Cc, Lp);
+                K0[J] = (TK)(2.0 * (double)K0[J] - (double)Kw[J] + cd->thdt * f);
+            }
+        } else for (int t = rank; t < s.L; t += gsize) {
             int j[N];
             decode<N>(s, t, j);
             const int J = s.padded(t);
@@ -538,13 +827,13 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
         // N solves in place; the last one accumulates Y_{n+1} = Y_n + b1 K1 + b2 K2
         for (int ax = 0; ax < N; ++ax) {
             if (ax == N - 1) {
-                sweep<N, TK>(s, ax, luc, K0, K0, rank, gsize, [&](int J, TK x) {
+                sweep<N, TK, RMAX>(s, ax, luc, K0, K0, rank, gsize, [&](int J, TK x) {
                     const double z = fma(kB2, (double)x, fma(kB1, (double)K1[J], Z[J]));
                     Z[J] = z;
                     if constexpr (MIXED) ZZ[J] = split_df(z);
                 });
             } else {
-                sweep<N, TK>(s, ax, luc, K0, K0, rank, gsize, NoEpi());
+                sweep<N, TK, RMAX>(s, ax, luc, K0, K0, rank, gsize, NoEpi());
             }
             gsync<WARP>();
         }
