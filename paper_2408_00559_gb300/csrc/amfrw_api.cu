@@ -229,6 +229,7 @@ struct LaunchClass {
     int block, grid;
     size_t smem;
     int smem_group;
+    int glog;            // warp groups: log2 lanes per group
     int64_t lu_stride;   // bytes of Thomas factors per block (CTA groups)
     int64_t lu_offset;   // this class's part of the plan's scratch array
 };
@@ -324,10 +325,14 @@ int plan_host(const amfrw_params* ps, int n, bool keep_state, Plan& P)
         I.grid_begin = (int32_t)P.coefs.size();
         I.grid_count = (int32_t)grids.size();
         for (const GridSpec& g : grids) {
-            int Lg = 1;
-            for (int a = 0; a < N; ++a) Lg <<= g.lv[a];
+            int Lg = 1, llog = 0;
+            for (int a = 0; a < N; ++a) {
+                Lg <<= g.lv[a];
+                llog += g.lv[a];
+            }
             const bool warp = Lg <= kWarpMaxL;
-            Layout lay = make_layout(N, g.lv, mixed, warp, 5);
+            // warp groups: one lane per node up to 32 nodes, so small grids share a warp
+            Layout lay = make_layout(N, g.lv, mixed, warp, warp ? std::min(llog, 5) : 5);
             if (lay.total > smem_cap)
                 return fail(AMFRW_ETOOBIG, "component grid with " + std::to_string(lay.L) +
                                                " Inner nodes needs " + std::to_string(lay.total) +
@@ -354,15 +359,20 @@ int plan_host(const amfrw_params* ps, int n, bool keep_state, Plan& P)
     }
     P.n_grids = (int)P.coefs.size();
     P.state_len = state_off;
+    // classes: (N, precision, group kind) and, for warp groups, the grid size;
+    // inside a class the largest grids first and equal shapes adjacent
     std::stable_sort(all.begin(), all.end(), [](const Tmp& a, const Tmp& b) {
-        return std::make_tuple(a.N, a.mixed, a.warp, -a.L) < std::make_tuple(b.N, b.mixed, b.warp, -b.L);
+        const int wa = a.warp ? a.L : 0, wb = b.warp ? b.L : 0;
+        if (std::make_tuple(a.N, a.mixed, a.warp, -wa, -a.L) != std::make_tuple(b.N, b.mixed, b.warp, -wb, -b.L))
+            return std::make_tuple(a.N, a.mixed, a.warp, -wa, -a.L) < std::make_tuple(b.N, b.mixed, b.warp, -wb, -b.L);
+        return memcmp(a.it.lv, b.it.lv, sizeof(a.it.lv)) < 0;
     });
     const int sms = num_sms();
     for (size_t k = 0; k < all.size();) {
         size_t e = k;
         int gmax = 0, lmax = 0;
         while (e < all.size() && all[e].N == all[k].N && all[e].mixed == all[k].mixed &&
-               all[e].warp == all[k].warp) {
+               all[e].warp == all[k].warp && (!all[k].warp || all[e].L == all[k].L)) {
             gmax = std::max(gmax, all[e].smem_group);
             lmax = std::max(lmax, all[e].L);
             ++e;
@@ -376,9 +386,13 @@ int plan_host(const amfrw_params* ps, int n, bool keep_state, Plan& P)
         c.smem_group = gmax;
         int64_t lumax = 0;
         if (c.warp) {
-            int wpb = std::min(kWarpsPerBlock, std::max(1, smem_cap / gmax));
+            c.glog = log2i(std::min(lmax, 32));
+            const int gpw = 32 >> c.glog;  // groups per warp
+            int wpb = std::min(kWarpsPerBlock, std::max(1, smem_cap / (gmax * gpw)));
+            if ((size_t)gmax * gpw > (size_t)smem_cap)
+                return fail(AMFRW_ETOOBIG, "warp groups of a launch class do not fit in shared memory");
             c.block = 32 * wpb;
-            c.smem = (size_t)gmax * wpb;
+            c.smem = (size_t)gmax * gpw * wpb;
         } else {
             int b = 64;
             while (b < 512 && b * 8 < lmax) b *= 2;
@@ -393,7 +407,7 @@ int plan_host(const amfrw_params* ps, int n, bool keep_state, Plan& P)
         if (per_sm < 1)
             return fail(AMFRW_ETOOBIG, "no resident block possible for a launch class (shared memory " +
                                            std::to_string(c.smem) + " bytes)");
-        const int groups_per_block = c.warp ? c.block / 32 : 1;
+        const int groups_per_block = c.warp ? (c.block >> c.glog) : 1;
         const int need = (c.item_count + groups_per_block - 1) / groups_per_block;
         c.grid = std::max(1, std::min(need, per_sm * sms));
         c.lu_stride = (lumax + 255) & ~(int64_t)255;
@@ -462,6 +476,7 @@ int run_solve(Plan& P, int steps, int flags, cudaEvent_t* ev = nullptr)
         a.u_out = P.d_u;
         a.state = P.d_state;
         a.queue = P.d_queue + c;
+        a.glog = L.glog;
         a.lu_scratch = P.d_lu ? P.d_lu + L.lu_offset : nullptr;
         a.lu_stride = L.lu_stride;
         if (ev) CUDA_TRY(cudaEventRecord(ev[2 * c], P.stream));

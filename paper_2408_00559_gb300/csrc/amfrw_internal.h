@@ -46,14 +46,18 @@ struct Layout {
 // N diagonal, 1 centre, N(N-1)/2 cross, N-2 drift, 1 for dt F(payoff).
 AMFRW_HD int node_coefs(int N) { return N + 1 + N * (N - 1) / 2 + (N - 2) + 1; }
 
+// Packed index of the pair (i, k), i < k < 8, and of (i, r), r <= i < 8.
+AMFRW_HD int upair(int i, int k) { return i * (2 * kMaxDim - i - 1) / 2 + (k - i - 1); }
+AMFRW_HD int ltri(int i, int r) { return i * (i + 1) / 2 + r; }
+
 template <typename T>
 struct Consts {
     T cV;                 // sigma^2 / (2 h_V^2)
     T dt, thdt, nudt;     // dt, theta*dt, nu*dt
-    T rm[kMaxDim][kMaxDim];   // rho_ik / (4 h_i h_k), rate pairs i < k
-    T rh[kMaxDim][kMaxDim];   // rho_ij for the drift sums (j <= i)
-    T sm[kMaxDim];            // sigma phi_i / (4 h_i h_V)
-    T g2[kMaxDim];            // 1 / (2 h_i)
+    T rm[kMaxDim * (kMaxDim - 1) / 2];  // rho_ik / (4 h_i h_k), rate pairs i < k (upair)
+    T rh[kMaxDim * (kMaxDim + 1) / 2];  // rho_ir for the drift sums, r <= i (ltri)
+    T sm[kMaxDim];                      // sigma phi_i / (4 h_i h_V)
+    T g2[kMaxDim];                      // 1 / (2 h_i)
 };
 
 AMFRW_HD int32_t align16(int32_t x) { return (x + 15) & ~15; }
@@ -146,6 +150,7 @@ struct SolveArgs {
     double* u_out;        // [n grids] u_l(x*)
     double* state;        // state pool (Inner values of Y), may be null
     int32_t* queue;       // work counter, zero before the launch
+    int32_t glog;         // warp groups: log2 lanes per group (grids of 2^glog <= 32 nodes share a warp)
     unsigned char* lu_scratch;  // CTA groups: Thomas factors, lu_stride bytes per block
     int64_t lu_stride;
 };

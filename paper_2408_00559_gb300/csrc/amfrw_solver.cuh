@@ -218,7 +218,7 @@ __device__ __forceinline__ TC stencil_acc(const Shape<N>& s, const int (&j)[N], 
                     const V mp = src.nb(J, -s.Sp[i] + s.Sp[k], li, i, -1, k, 1);
                     const V mm = src.nb(J, -s.Sp[i] - s.Sp[k], li && lk, i, -1, k, -1);
                     const TC mix = Src::diff(pp, pm) - Src::diff(mp, mm);
-                    const TC ck = (k < N - 1) ? c.rm[i][k] * tab[s.toff[k] + s.M[k] + j[k] - 1]
+                    const TC ck = (k < N - 1) ? c.rm[upair(i, k)] * tab[s.toff[k] + s.M[k] + j[k] - 1]
                                               : c.sm[i];
                     inner += ck * mix;
                 }
@@ -227,7 +227,7 @@ __device__ __forceinline__ TC stencil_acc(const Shape<N>& s, const int (&j)[N], 
         if (i >= 1) {  // drift of rates 2..N-1 (eq. coef_adv), sum over rates 2..i
             TC S = TC(0);
 #pragma unroll
-            for (int r = 1; r <= i; ++r) S += c.rh[i][r] * tab[s.toff[r] + 2 * s.M[r] + j[r] - 1];
+            for (int r = 1; r <= i; ++r) S += c.rh[ltri(i, r)] * tab[s.toff[r] + 2 * s.M[r] + j[r] - 1];
             inner += S * c.g2[i] * grad[i];
         }
         acc += tab[s.toff[i] + s.M[i] + j[i] - 1] * inner;
@@ -284,14 +284,14 @@ __device__ void build_node_coefs(const Shape<N>& s, const double* tabd, const Co
             const double pwi = tabd[s.toff[i] + s.M[i] + j[i] - 1];
 #pragma unroll
             for (int k = i + 1; k < N; ++k) {
-                const double m = (k < N - 1) ? c.rm[i][k] * pwi * tabd[s.toff[k] + s.M[k] + j[k] - 1] * v2
+                const double m = (k < N - 1) ? c.rm[upair(i, k)] * pwi * tabd[s.toff[k] + s.M[k] + j[k] - 1] * v2
                                              : c.sm[i] * pwi * v2;
                 C[I::pair(i, k) * Lp + J] = m;
             }
             if (i >= 1) {
                 double S = 0.0;
 #pragma unroll
-                for (int r = 1; r <= i; ++r) S += c.rh[i][r] * tabd[s.toff[r] + 2 * s.M[r] + j[r] - 1];
+                for (int r = 1; r <= i; ++r) S += c.rh[ltri(i, r)] * tabd[s.toff[r] + 2 * s.M[r] + j[r] - 1];
                 C[(I::drift + i - 1) * Lp + J] = pwi * S * c.g2[i] * v2;
             }
         }
@@ -357,10 +357,19 @@ __device__ __forceinline__ double diff_F(const Shape<N>& s, const int (&j)[N], i
 // next row slot of another lane) the sending lane picks the slot, so each
 // level costs one shuffle per direction.
 
-template <typename T>
-__device__ __forceinline__ T shfl(T v, int src, int width)
+// Lanes of the calling thread's work group inside its warp: the whole warp
+// for CTA groups and 32-lane warp groups, 2^glog lanes for smaller groups.
+__device__ __forceinline__ unsigned group_mask(int glog)
 {
-    return __shfl_sync(0xffffffffu, v, src, width);
+    if (glog >= 5) return 0xffffffffu;
+    const unsigned lanes = (1u << (1 << glog)) - 1u;
+    return lanes << ((threadIdx.x & 31) & ~((1 << glog) - 1));
+}
+
+template <typename T>
+__device__ __forceinline__ T shfl(T v, int src, int width, unsigned mask)
+{
+    return __shfl_sync(mask, v, src, width);
 }
 
 // Row r of (I - nu dt A_axis) for line class cls: lower a, diagonal b, upper c.
@@ -384,7 +393,7 @@ __device__ __forceinline__ void matrix_row(const Shape<N>& s, const double* tabd
 // its previous row, which is the wrap-around neighbour the next row needs.
 template <int N, typename T, int RMAX>
 __device__ void pcr_setup(const Shape<N>& s, const double* tabd, const Consts<double>& c, T* lu,
-                          int rank, int gsize)
+                          int rank, int gsize, unsigned gm)
 {
     for (int axis = 0; axis < N; ++axis) {
         const int M = s.M[axis];
@@ -418,13 +427,13 @@ __device__ void pcr_setup(const Shape<N>& s, const double* tabd, const Consts<do
                         const int qn = (q + 1 < RMAX) ? q + 1 : q;  // static after unrolling
                         const bool nx = q + 1 < R;
                         // to the lane above (p + d): my row q, or my row q-1 across the wrap
-                        const double a_m = shfl(send_prev ? pa : a[q], sm, P);
-                        const double b_m = shfl(send_prev ? pb : b[q], sm, P);
-                        const double u_m = shfl(send_prev ? pu : u[q], sm, P);
+                        const double a_m = shfl(send_prev ? pa : a[q], sm, P, gm);
+                        const double b_m = shfl(send_prev ? pb : b[q], sm, P, gm);
+                        const double u_m = shfl(send_prev ? pu : u[q], sm, P, gm);
                         // to the lane below (p - d): my row q, or my row q+1 across the wrap
-                        const double a_p = shfl(send_next ? (nx ? a[qn] : 0.0) : a[q], sp, P);
-                        const double b_p = shfl(send_next ? (nx ? b[qn] : 1.0) : b[q], sp, P);
-                        const double u_p = shfl(send_next ? (nx ? u[qn] : 0.0) : u[q], sp, P);
+                        const double a_p = shfl(send_next ? (nx ? a[qn] : 0.0) : a[q], sp, P, gm);
+                        const double b_p = shfl(send_next ? (nx ? b[qn] : 1.0) : b[q], sp, P, gm);
+                        const double u_p = shfl(send_next ? (nx ? u[qn] : 0.0) : u[q], sp, P, gm);
                         const bool hm = !wm || q >= 1;
                         const double al = hm ? a[q] / b_m : 0.0;
                         const double ga = u[q] / b_p;  // identity row sent past the end
@@ -463,7 +472,8 @@ __device__ void pcr_setup(const Shape<N>& s, const double* tabd, const Consts<do
 
 template <int N, typename T, int RMAX, class Epi>
 __device__ __forceinline__ void sweep(const Shape<N>& s, int axis, const T* __restrict__ lu,
-                                      const T* src, T* dst, int rank, int gsize, Epi epi)
+                                      const T* src, T* dst, int rank, int gsize, unsigned gm,
+                                      Epi epi)
 {
     const int M = s.M[axis];
     const int plog = s.plog[axis];
@@ -503,8 +513,8 @@ __device__ __forceinline__ void sweep(const Shape<N>& s, int axis, const T* __re
             for (int q = 0; q < RMAX; ++q) {
                 if (q < R) {
                     const int qn = (q + 1 < RMAX) ? q + 1 : q;  // static after unrolling
-                    const T vm = shfl(send_prev ? prev : x[q], sm, P);
-                    const T vp = shfl(send_next ? ((q + 1 < R) ? x[qn] : T(0)) : x[q], sp, P);
+                    const T vm = shfl(send_prev ? prev : x[q], sm, P, gm);
+                    const T vp = shfl(send_next ? ((q + 1 < R) ? x[qn] : T(0)) : x[q], sp, P, gm);
                     const T* row = tb + q * PS;
                     prev = x[q];
                     // multipliers are zero where the neighbour lies outside the line
@@ -543,10 +553,10 @@ struct NoEpi {
 };
 
 template <bool WARP>
-__device__ __forceinline__ void gsync()
+__device__ __forceinline__ void gsync(unsigned gm)
 {
     if (WARP)
-        __syncwarp();
+        __syncwarp(gm);
     else
         __syncthreads();
 }
@@ -592,10 +602,13 @@ __device__ void build_tables(const Shape<N>& s, const InstDev& P, double* tabd, 
         cd->thdt = P.theta * P.dt;
         cd->nudt = P.nu * P.dt;
         for (int i = 0; i < kMaxDim; ++i) {
-            for (int k = 0; k < kMaxDim; ++k) {
+            for (int k = i + 1; k < kMaxDim; ++k) {
                 const bool ok = i < N - 1 && k < N - 1;
-                cd->rm[i][k] = ok ? P.rho[i * kMaxDim + k] / (4.0 * h[i] * h[k]) : 0.0;
-                cd->rh[i][k] = ok ? P.rho[i * kMaxDim + k] : 0.0;
+                cd->rm[upair(i, k)] = ok ? P.rho[i * kMaxDim + k] / (4.0 * h[i] * h[k]) : 0.0;
+            }
+            for (int r = 0; r <= i; ++r) {
+                const bool ok = i < N - 1;
+                cd->rh[ltri(i, r)] = ok ? P.rho[i * kMaxDim + r] : 0.0;
             }
             cd->sm[i] = (i < N - 1) ? P.sigma * P.phi[i] / (4.0 * h[i] * hV) : 0.0;
             cd->g2[i] = (i < N) ? 1.0 / (2.0 * h[i]) : 0.0;
@@ -610,11 +623,9 @@ __device__ void convert_consts(const Consts<double>& a, Consts<T>* b)
     b->dt = (T)a.dt;
     b->thdt = (T)a.thdt;
     b->nudt = (T)a.nudt;
+    for (int q = 0; q < kMaxDim * (kMaxDim - 1) / 2; ++q) b->rm[q] = (T)a.rm[q];
+    for (int q = 0; q < kMaxDim * (kMaxDim + 1) / 2; ++q) b->rh[q] = (T)a.rh[q];
     for (int i = 0; i < kMaxDim; ++i) {
-        for (int k = 0; k < kMaxDim; ++k) {
-            b->rm[i][k] = (T)a.rm[i][k];
-            b->rh[i][k] = (T)a.rh[i][k];
-        }
         b->sm[i] = (T)a.sm[i];
         b->g2[i] = (T)a.g2[i];
     }
@@ -635,7 +646,8 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
     using TK = typename std::conditional<MIXED, float, double>::type;
     const InstDev& P = a.insts[it.inst];
     constexpr int RMAX = 1 << (WARP ? kRowsLogWarp : kRowsLogCta);
-    const int tlog = WARP ? 5 : 31 - __clz(gsize);
+    const int tlog = 31 - __clz(gsize);
+    const unsigned gm = WARP ? group_mask(tlog) : 0xffffffffu;
     Shape<N> s;
     make_shape<N>(s, it.lv, tlog, rows_log(WARP));
     const Layout lay = make_layout(N, it.lv, MIXED, WARP, tlog);
@@ -665,12 +677,12 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
 
     // 1. coefficient and payoff tables, constants
     build_tables<N>(s, P, tabd, pay, cd, rank, gsize);
-    gsync<WARP>();
+    gsync<WARP>(gm);
     if constexpr (MIXED) {
         for (int q = rank; q < lay.ntab; q += gsize) tabk[q] = (TK)tabd[q];
         if (rank == 0) convert_consts<TK>(*cd, ck);
     }
-    pcr_setup<N, TK, RMAX>(s, tabd, *cd, lu, rank, gsize);
+    pcr_setup<N, TK, RMAX>(s, tabd, *cd, lu, rank, gsize, gm);
 
     // 2. H = F(G)/V^2 on the rate grid (FP64), Z from the state or zero
     for (int tr = rank; tr < s.Lr; tr += gsize) {
@@ -692,21 +704,21 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
         Z[J] = z;
         if constexpr (MIXED) ZZ[J] = split_df(z);
     }
-    gsync<WARP>();
+    gsync<WARP>(gm);
     if constexpr (DIFF) {
         build_node_coefs<N>(s, tabd, *cd, (const double*)H, Cc, Lp, rank, gsize);
-        gsync<WARP>();
+        gsync<WARP>(gm);
     }
 
     const int Lr1 = s.Lr - 1;
     const TK* v2 = tabk + s.toff[N - 1] - 1;  // v2[j_V], 1-based
     const TK* luc = lu;
     auto sweeps_into = [&](TK* from, TK* to) {
-        sweep<N, TK, RMAX>(s, 0, luc, from, to, rank, gsize, NoEpi());
-        gsync<WARP>();
+        sweep<N, TK, RMAX>(s, 0, luc, from, to, rank, gsize, gm, NoEpi());
+        gsync<WARP>(gm);
         for (int ax = 1; ax < N; ++ax) {
-            sweep<N, TK, RMAX>(s, ax, luc, to, to, rank, gsize, NoEpi());
-            gsync<WARP>();
+            sweep<N, TK, RMAX>(s, ax, luc, to, to, rank, gsize, gm, NoEpi());
+            gsync<WARP>(gm);
         }
     };
 
@@ -715,7 +727,7 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
         // ---- stage 1: K^(0) = dt F(Y_n)
         if constexpr (DIFF) {
             diff_pass<N>(s, Z, Dd, Lp, rank, gsize);
-            gsync<WARP>();
+            gsync<WARP>(gm);
             for (int t = rank; t < s.L; t += gsize) {
                 int j[N];
                 decode<N>(s, t, j);
@@ -740,12 +752,12 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
             }
             K0[J] = k0;
         }
-        gsync<WARP>();
+        gsync<WARP>(gm);
         sweeps_into(K0, Kw);
         // refinement: Khat = 2 K^(0) - K^(N) + theta dt F(K^(N))
         if constexpr (DIFF) {
             diff_pass<N>(s, (const double*)Kw, Dd, Lp, rank, gsize);
-            gsync<WARP>();
+            gsync<WARP>(gm);
             for (int t = rank; t < s.L; t += gsize) {
                 int j[N];
                 decode<N>(s, t, j);
@@ -760,24 +772,24 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
             const TK acc = stencil_acc<N, TK>(s, j, J, ArrSrc<TK>{Kw}, tabk, *ck);
             K0[J] = TK(2) * K0[J] - Kw[J] + ck->thdt * v2[j[N - 1]] * acc;
         }
-        gsync<WARP>();
+        gsync<WARP>(gm);
         // N solves into K1; the last one also forms the stage-2 argument
-        sweep<N, TK, RMAX>(s, 0, luc, K0, K1, rank, gsize, NoEpi());
-        gsync<WARP>();
+        sweep<N, TK, RMAX>(s, 0, luc, K0, K1, rank, gsize, gm, NoEpi());
+        gsync<WARP>(gm);
         for (int ax = 1; ax < N; ++ax) {
             if (!MIXED && ax == N - 1) {  // FP64: Kw = Z + a21 K1
-                sweep<N, TK, RMAX>(s, ax, luc, K1, K1, rank, gsize, [&](int J, TK x) {
+                sweep<N, TK, RMAX>(s, ax, luc, K1, K1, rank, gsize, gm, [&](int J, TK x) {
                     Kw[J] = (TK)(Z[J] + kA21 * (double)x);
                 });
             } else {
-                sweep<N, TK, RMAX>(s, ax, luc, K1, K1, rank, gsize, NoEpi());
+                sweep<N, TK, RMAX>(s, ax, luc, K1, K1, rank, gsize, gm, NoEpi());
             }
-            gsync<WARP>();
+            gsync<WARP>(gm);
         }
         // ---- stage 2: K^(0) = dt F(Y_n + a21 K1) + q21 K1
         if constexpr (DIFF) {
             diff_pass<N>(s, (const double*)Kw, Dd, Lp, rank, gsize);
-            gsync<WARP>();
+            gsync<WARP>(gm);
             for (int t = rank; t < s.L; t += gsize) {
                 int j[N];
                 decode<N>(s, t, j);
@@ -804,11 +816,11 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
                              kQ21 * (double)K1[J]);
             }
         }
-        gsync<WARP>();
+        gsync<WARP>(gm);
         sweeps_into(K0, Kw);
         if constexpr (DIFF) {
             diff_pass<N>(s, (const double*)Kw, Dd, Lp, rank, gsize);
-            gsync<WARP>();
+            gsync<WARP>(gm);
             for (int t = rank; t < s.L; t += gsize) {
                 int j[N];
                 decode<N>(s, t, j);
@@ -823,19 +835,19 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
             const TK acc = stencil_acc<N, TK>(s, j, J, ArrSrc<TK>{Kw}, tabk, *ck);
             K0[J] = TK(2) * K0[J] - Kw[J] + ck->thdt * v2[j[N - 1]] * acc;
         }
-        gsync<WARP>();
+        gsync<WARP>(gm);
         // N solves in place; the last one accumulates Y_{n+1} = Y_n + b1 K1 + b2 K2
         for (int ax = 0; ax < N; ++ax) {
             if (ax == N - 1) {
-                sweep<N, TK, RMAX>(s, ax, luc, K0, K0, rank, gsize, [&](int J, TK x) {
+                sweep<N, TK, RMAX>(s, ax, luc, K0, K0, rank, gsize, gm, [&](int J, TK x) {
                     const double z = fma(kB2, (double)x, fma(kB1, (double)K1[J], Z[J]));
                     Z[J] = z;
                     if constexpr (MIXED) ZZ[J] = split_df(z);
                 });
             } else {
-                sweep<N, TK, RMAX>(s, ax, luc, K0, K0, rank, gsize, NoEpi());
+                sweep<N, TK, RMAX>(s, ax, luc, K0, K0, rank, gsize, gm, NoEpi());
             }
-            gsync<WARP>();
+            gsync<WARP>(gm);
         }
     }
 
@@ -885,7 +897,7 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
         }
         a.u_out[it.out_idx] = u;
     }
-    gsync<WARP>();  // the group's shared memory is reused by its next grid
+    gsync<WARP>(gm);  // the group's shared memory is reused by its next grid
 }
 
 template <int N, bool MIXED, bool WARP>
@@ -893,25 +905,32 @@ __global__ void __launch_bounds__(WARP ? 256 : 512) solve_kernel(SolveArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_item;
-    const int gid = WARP ? (int)(threadIdx.x >> 5) : 0;
-    const int rank = WARP ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
-    const int gsize = WARP ? 32 : (int)blockDim.x;
+    // warp groups: 2^glog lanes per grid, 32 >> glog grids per warp
+    const int glog = WARP ? a.glog : 0;
+    const int gid = WARP ? (int)(threadIdx.x >> glog) : 0;
+    const int rank = WARP ? (int)(threadIdx.x & ((1 << glog) - 1)) : (int)threadIdx.x;
+    const int gsize = WARP ? (1 << glog) : (int)blockDim.x;
+    const int lane = threadIdx.x & 31;
     unsigned char* base = smem + (size_t)gid * (size_t)a.smem_group;
     for (;;) {
         int item;
         if (WARP) {
-            item = 0;
-            if (rank == 0) item = atomicAdd(a.queue, 1);
-            item = __shfl_sync(0xffffffffu, item, 0);
+            int chunk = 0;
+            if (lane == 0) chunk = atomicAdd(a.queue, 32 >> glog);
+            chunk = __shfl_sync(0xffffffffu, chunk, 0);
+            if (chunk >= a.n_items) break;
+            item = chunk + (lane >> glog);
         } else {
             if (threadIdx.x == 0) s_item = atomicAdd(a.queue, 1);
             __syncthreads();
             item = s_item;
             __syncthreads();
+            if (item >= a.n_items) break;
         }
-        if (item >= a.n_items) break;
-        const Item it = a.items[item];
-        solve_item<N, MIXED, WARP>(a, it, base, rank, gsize);
+        if (item < a.n_items) {
+            const Item it = a.items[item];
+            solve_item<N, MIXED, WARP>(a, it, base, rank, gsize);
+        }
     }
 }
 
