@@ -140,23 +140,31 @@ struct DFSrc {  // Z as an unevaluated float pair hi + lo
 // Payoff g at rate multi-index jj (Sec. 2).  Caplet: (F_1 - K)^+.
 // Swaption: max{ sum_i tau_i (F_i - K) prod_{l<=i} 1/(1 + tau_l F_l), 0 }.
 template <int N>
-__device__ __forceinline__ double payoff_at(const Shape<N>& s, const double* pay, int payoff,
-                                            const int (&jj)[N])
+__device__ __forceinline__ double payoff_at(const int (&poff)[N], int phalf, const double* pay,
+                                            int payoff, const int (&jj)[N])
 {
-    if (payoff == 0) return fmax(pay[s.poff[0] + jj[0]], 0.0);
+    if (payoff == 0) return fmax(pay[poff[0] + jj[0]], 0.0);
     double sum = 0.0, P = 1.0;
 #pragma unroll
     for (int r = 0; r < N - 1; ++r) {
-        P *= pay[s.phalf + s.poff[r] + jj[r]];
-        sum += pay[s.poff[r] + jj[r]] * P;
+        P *= pay[phalf + poff[r] + jj[r]];
+        sum += pay[poff[r] + jj[r]] * P;
     }
     return fmax(sum, 0.0);
 }
 
 template <int N>
+__device__ __forceinline__ double payoff_at(const Shape<N>& s, const double* pay, int payoff,
+                                            const int (&jj)[N])
+{
+    return payoff_at<N>(s.poff, s.phalf, pay, payoff, jj);
+}
+
+template <int N>
 struct PaySrc {  // the payoff G on every node, Outer included
     using V = double;
-    const Shape<N>* s;
+    int poff[N];  // copies, so that the grid's shape never has its address taken
+    int phalf;
     const double* pay;
     int payoff;
     int j[N];
@@ -165,7 +173,7 @@ struct PaySrc {  // the payoff G on every node, Outer included
         int jj[N];
 #pragma unroll
         for (int r = 0; r < N; ++r) jj[r] = j[r] + (r == i ? si : 0) + (r == k ? sk : 0);
-        return payoff_at<N>(*s, pay, payoff, jj);
+        return payoff_at<N>(poff, phalf, pay, payoff, jj);
     }
     __device__ __forceinline__ V ctr(int) const { return at(-1, 0, -1, 0); }
     __device__ __forceinline__ V nb(int, int, bool, int i, int si, int k, int sk) const
@@ -595,17 +603,21 @@ __device__ void build_tables(const Shape<N>& s, const InstDev& P, double* tabd, 
     }
     if (rank == 0) {
         double h[kMaxDim];
-        for (int i = 0; i < N; ++i) h[i] = P.Fmax[i] / (double)s.M[i];
+#pragma unroll
+        for (int i = 0; i < kMaxDim; ++i) h[i] = (i < N) ? P.Fmax[i] / (double)s.M[i < N ? i : 0] : 1.0;
         const double hV = h[N - 1];
         cd->cV = 0.5 * P.sigma * P.sigma / (hV * hV);
         cd->dt = P.dt;
         cd->thdt = P.theta * P.dt;
         cd->nudt = P.nu * P.dt;
+#pragma unroll
         for (int i = 0; i < kMaxDim; ++i) {
+#pragma unroll
             for (int k = i + 1; k < kMaxDim; ++k) {
                 const bool ok = i < N - 1 && k < N - 1;
                 cd->rm[upair(i, k)] = ok ? P.rho[i * kMaxDim + k] / (4.0 * h[i] * h[k]) : 0.0;
             }
+#pragma unroll
             for (int r = 0; r <= i; ++r) {
                 const bool ok = i < N - 1;
                 cd->rh[ltri(i, r)] = ok ? P.rho[i * kMaxDim + r] : 0.0;
@@ -636,6 +648,19 @@ __device__ __forceinline__ float2 split_df(double z)
     const float hi = __double2float_rn(z);
     const float lo = __double2float_rn(z - (double)hi);
     return make_float2(hi, lo);
+}
+
+// N directional solves: the first from `from` into `to`, the rest in place.
+template <int N, typename TK, int RMAX, bool WARP>
+__device__ __forceinline__ void sweeps_into(const Shape<N>& s, const TK* lu, const TK* from, TK* to,
+                                            int rank, int gsize, unsigned gm)
+{
+    sweep<N, TK, RMAX>(s, 0, lu, from, to, rank, gsize, gm, NoEpi());
+    gsync<WARP>(gm);
+    for (int ax = 1; ax < N; ++ax) {
+        sweep<N, TK, RMAX>(s, ax, lu, to, to, rank, gsize, gm, NoEpi());
+        gsync<WARP>(gm);
+    }
 }
 
 // ------------------------------------------------------------- one grid
@@ -687,7 +712,9 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
     // 2. H = F(G)/V^2 on the rate grid (FP64), Z from the state or zero
     for (int tr = rank; tr < s.Lr; tr += gsize) {
         PaySrc<N> ps;
-        ps.s = &s;
+#pragma unroll
+        for (int i = 0; i < N; ++i) ps.poff[i] = s.poff[i];
+        ps.phalf = s.phalf;
         ps.pay = pay;
         ps.payoff = P.payoff;
         decode<N>(s, tr, ps.j);
@@ -713,14 +740,6 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
     const int Lr1 = s.Lr - 1;
     const TK* v2 = tabk + s.toff[N - 1] - 1;  // v2[j_V], 1-based
     const TK* luc = lu;
-    auto sweeps_into = [&](TK* from, TK* to) {
-        sweep<N, TK, RMAX>(s, 0, luc, from, to, rank, gsize, gm, NoEpi());
-        gsync<WARP>(gm);
-        for (int ax = 1; ax < N; ++ax) {
-            sweep<N, TK, RMAX>(s, ax, luc, to, to, rank, gsize, gm, NoEpi());
-            gsync<WARP>(gm);
-        }
-    };
 
     using CI = CIdx<N>;
     for (int n = 0; n < a.steps; ++n) {
@@ -753,7 +772,7 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
             K0[J] = k0;
         }
         gsync<WARP>(gm);
-        sweeps_into(K0, Kw);
+        sweeps_into<N, TK, RMAX, WARP>(s, luc, K0, Kw, rank, gsize, gm);
         // refinement: Khat = 2 K^(0) - K^(N) + theta dt F(K^(N))
         if constexpr (DIFF) {
             diff_pass<N>(s, (const double*)Kw, Dd, Lp, rank, gsize);
@@ -778,7 +797,7 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
         gsync<WARP>(gm);
         for (int ax = 1; ax < N; ++ax) {
             if (!MIXED && ax == N - 1) {  // FP64: Kw = Z + a21 K1
-                sweep<N, TK, RMAX>(s, ax, luc, K1, K1, rank, gsize, gm, [&](int J, TK x) {
+                sweep<N, TK, RMAX>(s, ax, luc, K1, K1, rank, gsize, gm, [=](int J, TK x) {
                     Kw[J] = (TK)(Z[J] + kA21 * (double)x);
                 });
             } else {
@@ -817,7 +836,7 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
             }
         }
         gsync<WARP>(gm);
-        sweeps_into(K0, Kw);
+        sweeps_into<N, TK, RMAX, WARP>(s, luc, K0, Kw, rank, gsize, gm);
         if constexpr (DIFF) {
             diff_pass<N>(s, (const double*)Kw, Dd, Lp, rank, gsize);
             gsync<WARP>(gm);
@@ -839,7 +858,7 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
         // N solves in place; the last one accumulates Y_{n+1} = Y_n + b1 K1 + b2 K2
         for (int ax = 0; ax < N; ++ax) {
             if (ax == N - 1) {
-                sweep<N, TK, RMAX>(s, ax, luc, K0, K0, rank, gsize, gm, [&](int J, TK x) {
+                sweep<N, TK, RMAX>(s, ax, luc, K0, K0, rank, gsize, gm, [=](int J, TK x) {
                     const double z = fma(kB2, (double)x, fma(kB1, (double)K1[J], Z[J]));
                     Z[J] = z;
                     if constexpr (MIXED) ZZ[J] = split_df(z);
@@ -901,7 +920,7 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
 }
 
 template <int N, bool MIXED, bool WARP>
-__global__ void __launch_bounds__(WARP ? 256 : 512) solve_kernel(SolveArgs a)
+__global__ void __launch_bounds__(WARP ? 128 : 512) solve_kernel(SolveArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_item;
