@@ -169,23 +169,36 @@ int amfrw_solve_batch(const amfrw_params *ps, int32_t n, double *prices_out, voi
  * everything once; amfrw_batch_run prices all instances with device-resident
  * inputs and writes the prices to the DEVICE array d_prices_out [n]
  * (asynchronous, stream-ordered; the array must stay valid until the stream
- * reaches that point).  amfrw_batch_run may be called any number of times. */
+ * reaches that point).  amfrw_batch_run may be called any number of times;
+ * its first call captures the solve and the combination into a CUDA graph
+ * (on a private stream) that later calls replay. */
 int amfrw_batch_create(const amfrw_params *ps, int32_t n, void *cuda_stream, amfrw_batch **out);
 int amfrw_batch_run(amfrw_batch *b, double *d_prices_out);
 /* Number of kernel launches one amfrw_batch_run issues (for accounting). */
 int amfrw_batch_launches(const amfrw_batch *b, int32_t *n_launches);
 
 /* Kernel timing (tracing).  With timing on, every amfrw_batch_run records a
- * CUDA event pair on the batch's stream around each solver launch (one launch
- * per (N, precision, work-group) class).  amfrw_batch_kernel_times
- * synchronises and writes, for the last run, the device milliseconds of each
- * solver launch to ms_out[0..*n_out-1] (at most cap entries) and the
- * Inner-node-steps that launch advanced (sum over its grids of Inner nodes x
- * steps) to node_steps_out (may be NULL); N of each launch goes to
- * dims_out (may be NULL). */
+ * CUDA event pair around each solver launch: one persistent multi-class
+ * launch per precision for all grids of at most 64 Inner nodes (when that
+ * strategy is selected), and one launch per remaining (N, precision, grid
+ * class).  amfrw_batch_kernel_times synchronises and writes, for the last
+ * run, the device milliseconds of each solver launch to ms_out[0..*n_out-1]
+ * (at most cap entries), the Inner-node-steps it advanced (sum over its grids
+ * of Inner nodes x steps) to node_steps_out (may be NULL) and its N (0 for a
+ * multi-class launch) to dims_out (may be NULL). */
 int amfrw_batch_enable_timing(amfrw_batch *b, int32_t on);
 int amfrw_batch_kernel_times(amfrw_batch *b, float *ms_out, double *node_steps_out,
                              int32_t *dims_out, int32_t cap, int32_t *n_out);
+
+/* Autotuning of the launch strategy (the paper has no counterpart; its CPU
+ * code schedules grids with OpenMP's dynamic schedule).  Times, on this
+ * batch and device, per-class launches against one persistent multi-class
+ * launch for the warp-solved grids (`trials` solves each after a warm-up),
+ * keeps the faster, and caches the choice in-process under the batch's class
+ * signature (and, if the environment variable AMFRW_TUNE_CACHE names a file,
+ * appends it there), so later batches with the same classes start with it.
+ * *use_multi_out (may be NULL) receives the choice.  Synchronises. */
+int amfrw_batch_autotune(amfrw_batch *b, int32_t trials, int32_t *use_multi_out);
 
 /* Bytes one amfrw_solve_batch call of this problem set copies host->device
  * (instance records, grid list, coefficients) and device->host (prices and

@@ -27,7 +27,7 @@ EXPORTS = [
     "amfrw_problem_destroy", "amfrw_solve_batch", "amfrw_batch_create", "amfrw_batch_run",
     "amfrw_batch_launches", "amfrw_batch_destroy", "amfrw_status_string", "amfrw_last_error",
     "amfrw_batch_enable_timing", "amfrw_batch_kernel_times", "amfrw_batch_io_bytes",
-    "amfrw_solve_noalloc",
+    "amfrw_solve_noalloc", "amfrw_batch_autotune",
 ]
 
 
@@ -84,6 +84,7 @@ def lib():
                                                C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_int32)]
         L.amfrw_batch_io_bytes.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         L.amfrw_solve_noalloc.argtypes = [pp, C.c_int32, vp, vp]
+        L.amfrw_batch_autotune.argtypes = [vp, C.c_int32, C.POINTER(C.c_int32)]
         L.amfrw_status_string.restype = C.c_char_p
         L.amfrw_status_string.argtypes = [C.c_int]
         L.amfrw_last_error.restype = C.c_char_p
@@ -243,6 +244,13 @@ class Batch:
         _check(lib().amfrw_batch_kernel_times(self.h, ms, ns, dims, cap, C.byref(n)),
                "amfrw_batch_kernel_times")
         return [(dims[i], ms[i], ns[i]) for i in range(n.value)]
+
+    def autotune(self, trials: int = 2) -> bool:
+        """Pick the faster launch strategy on this device; True = one persistent
+        multi-class launch for the warp-solved grids."""
+        m = C.c_int32()
+        _check(lib().amfrw_batch_autotune(self.h, int(trials), C.byref(m)), "amfrw_batch_autotune")
+        return bool(m.value)
 
     def io_bytes(self):
         h2d, d2h = C.c_int64(), C.c_int64()

@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cmath>
 #include <map>
+#include <cstdlib>
 #include <string>
 #include <tuple>
 #include <mutex>
@@ -39,6 +40,7 @@ int fail(int status, const std::string& msg)
 
 constexpr int kWarpMaxL = 64;          // grids up to this many Inner nodes: one warp each
 constexpr int kWarpsPerBlock = 4;
+constexpr int kMinGroupLog = 3;        // warp groups have at least 8 lanes (at most 4 grids per warp)
 
 bool finite(double x) { return std::isfinite(x); }
 
@@ -255,6 +257,21 @@ struct Plan {
     int64_t state_len = 0;
     unsigned char* d_lu = nullptr;   // scratch: Thomas factors of CTA-group grids
     int64_t lu_scratch_len = 0;
+    // warp-group launches: with the merged strategy one persistent launch per
+    // (N, precision) walks all its grid classes; split: one launch per class
+    struct WarpLaunch {
+        int N = 0;
+        bool mixed = false;
+        std::vector<ClassDesc> cls;
+        std::vector<int> covers;  // indices into `classes`
+        int block = 128, grid = 1, smem_warp = 0;
+        size_t smem = 0;
+        int64_t desc_offset = 0;  // into d_cdesc
+    };
+    std::vector<WarpLaunch> wl;
+    ClassDesc* d_cdesc = nullptr;
+    int64_t n_cdesc = 0;
+    bool use_multi = true;  // launch strategy (the autotuner may switch it)
 
     ~Plan() { release(); }
     void release()
@@ -268,7 +285,9 @@ struct Plan {
         cudaFree(d_flag);
         cudaFree(d_state);
         cudaFree(d_lu);
+        cudaFree(d_cdesc);
         d_lu = nullptr;
+        d_cdesc = nullptr;
         d_insts = nullptr; d_items = nullptr; d_coefs = nullptr; d_u = nullptr;
         d_prices = nullptr; d_queue = nullptr; d_flag = nullptr; d_state = nullptr;
     }
@@ -331,8 +350,10 @@ int plan_host(const amfrw_params* ps, int n, bool keep_state, Plan& P)
                 llog += g.lv[a];
             }
             const bool warp = Lg <= kWarpMaxL;
-            // warp groups: one lane per node up to 32 nodes, so small grids share a warp
-            Layout lay = make_layout(N, g.lv, mixed, warp, warp ? std::min(llog, 5) : 5);
+            // warp groups: one lane per node up to 32 nodes (at least 8 lanes), so
+            // small grids share a warp
+            Layout lay = make_layout(N, g.lv, mixed, warp,
+                                     warp ? std::max(std::min(llog, 5), kMinGroupLog) : 5);
             if (lay.total > smem_cap)
                 return fail(AMFRW_ETOOBIG, "component grid with " + std::to_string(lay.L) +
                                                " Inner nodes needs " + std::to_string(lay.total) +
@@ -386,7 +407,7 @@ int plan_host(const amfrw_params* ps, int n, bool keep_state, Plan& P)
         c.smem_group = gmax;
         int64_t lumax = 0;
         if (c.warp) {
-            c.glog = log2i(std::min(lmax, 32));
+            c.glog = std::max(log2i(std::min(lmax, 32)), kMinGroupLog);
             const int gpw = 32 >> c.glog;  // groups per warp
             int wpb = std::min(kWarpsPerBlock, std::max(1, smem_cap / (gmax * gpw)));
             if ((size_t)gmax * gpw > (size_t)smem_cap)
@@ -395,7 +416,7 @@ int plan_host(const amfrw_params* ps, int n, bool keep_state, Plan& P)
             c.smem = (size_t)gmax * gpw * wpb;
         } else {
             int b = 64;
-            while (b < 512 && b * 8 < lmax) b *= 2;
+            while (b < kCtaMaxThreads && b * 8 < lmax) b *= 2;
             c.block = b;
             c.smem = (size_t)gmax;
             for (size_t q = k; q < e; ++q) {
@@ -420,6 +441,81 @@ int plan_host(const amfrw_params* ps, int n, bool keep_state, Plan& P)
     return AMFRW_OK;
 }
 
+// Warp-group launches for the current strategy.  Merged: per (N, precision)
+// one launch over all its classes, largest grids first.  Split: one launch
+// per class.  Descriptors are laid out in launch order.
+int build_warp_launches(Plan& P)
+{
+    P.wl.clear();
+    const int smem_cap = max_smem_optin();
+    const int sms = num_sms();
+    std::vector<std::vector<int>> groups;
+    for (int N = 2; N <= kMaxDim; ++N) {
+        for (int mixed = 0; mixed < 2; ++mixed) {
+            std::vector<int> cs;
+            for (size_t c = 0; c < P.classes.size(); ++c)
+                if (P.classes[c].warp && P.classes[c].N == N && (int)P.classes[c].mixed == mixed)
+                    cs.push_back((int)c);
+            if (cs.empty()) continue;
+            std::sort(cs.begin(), cs.end(), [&](int x, int y) {
+                return P.items[P.classes[x].item_begin].L > P.items[P.classes[y].item_begin].L;
+            });
+            if (P.use_multi) {
+                groups.push_back(cs);
+            } else {
+                for (int c : cs) groups.push_back({c});
+            }
+        }
+    }
+    int64_t off = 0;
+    for (const std::vector<int>& g : groups) {
+        Plan::WarpLaunch w;
+        w.N = P.classes[g[0]].N;
+        w.mixed = P.classes[g[0]].mixed;
+        w.covers = g;
+        int items = 0;
+        for (int c : g) {
+            const LaunchClass& L = P.classes[c];
+            ClassDesc d{};
+            d.glog = L.glog;
+            d.item_begin = L.item_begin;
+            d.item_count = L.item_count;
+            d.smem_group = L.smem_group;
+            d.qidx = c;
+            w.cls.push_back(d);
+            w.smem_warp = std::max(w.smem_warp, L.smem_group << (5 - L.glog));
+            items += L.item_count << L.glog;  // lanes of work
+        }
+        if (w.smem_warp > smem_cap)
+            return fail(AMFRW_ETOOBIG, "the work groups of one warp do not fit in shared memory");
+        const int wpb = std::min(kWarpsPerBlock, std::max(1, smem_cap / w.smem_warp));
+        w.block = 32 * wpb;
+        w.smem = (size_t)w.smem_warp * wpb;
+        const int per_sm = occ_for(w.N)(w.mixed, true, w.block, w.smem);
+        if (per_sm < 1) return fail(AMFRW_ETOOBIG, "no resident block possible for a warp-group launch");
+        const int need = (items + w.block - 1) / w.block;
+        w.grid = std::max(1, std::min(need, per_sm * sms));
+        w.desc_offset = off;
+        off += (int64_t)w.cls.size();
+        P.wl.push_back(w);
+    }
+    P.n_cdesc = off;
+    return AMFRW_OK;
+}
+
+int upload_warp_launches(Plan& P)
+{
+    if (P.n_cdesc == 0) return AMFRW_OK;
+    std::vector<ClassDesc> all;
+    for (const Plan::WarpLaunch& w : P.wl) all.insert(all.end(), w.cls.begin(), w.cls.end());
+    if (!P.d_cdesc) CUDA_TRY(cudaMalloc(&P.d_cdesc, sizeof(ClassDesc) * all.size()));
+    CUDA_TRY(cudaMemcpyAsync(P.d_cdesc, all.data(), sizeof(ClassDesc) * all.size(),
+                             cudaMemcpyHostToDevice, P.stream));
+    // the upload must complete before `all` goes away
+    CUDA_TRY(cudaStreamSynchronize(P.stream));
+    return AMFRW_OK;
+}
+
 int build_plan(const amfrw_params* ps, int n, void* stream, bool keep_state, Plan& P)
 {
     int st = plan_host(ps, n, keep_state, P);
@@ -436,6 +532,10 @@ int build_plan(const amfrw_params* ps, int n, void* stream, bool keep_state, Pla
     CUDA_TRY(cudaMalloc(&P.d_flag, sizeof(int32_t)));
     if (keep_state) CUDA_TRY(cudaMalloc(&P.d_state, sizeof(double) * std::max<int64_t>(1, P.state_len)));
     if (P.lu_scratch_len > 0) CUDA_TRY(cudaMalloc(&P.d_lu, (size_t)P.lu_scratch_len));
+    int st2 = build_warp_launches(P);
+    if (st2 != AMFRW_OK) return st2;
+    st2 = upload_warp_launches(P);
+    if (st2 != AMFRW_OK) return st2;
     CUDA_TRY(cudaMemcpyAsync(P.d_insts, P.insts.data(), sizeof(InstDev) * P.insts.size(),
                              cudaMemcpyHostToDevice, P.stream));
     CUDA_TRY(cudaMemcpyAsync(P.d_items, P.items.data(), sizeof(Item) * P.items.size(),
@@ -461,27 +561,58 @@ __global__ void combine_kernel(const InstDev* __restrict__ insts, int n, const d
 }
 
 // Solve launches for every class.  steps < 0: each instance's own n_steps.
+SolveArgs class_args(const Plan& P, const LaunchClass& L, int c, int steps, int flags)
+{
+    SolveArgs a{};
+    a.items = P.d_items + L.item_begin;
+    a.n_items = L.item_count;
+    a.steps = steps;
+    a.flags = flags;
+    a.smem_group = L.smem_group;
+    a.insts = P.d_insts;
+    a.u_out = P.d_u;
+    a.state = P.d_state;
+    a.queue = P.d_queue + c;
+    a.lu_scratch = P.d_lu ? P.d_lu + L.lu_offset : nullptr;
+    a.lu_stride = L.lu_stride;
+    return a;
+}
+
+// The launches of one solve, in order: the warp-group launches, then the CTA
+// classes.  Each record is (warp launch index or -1, class index or -1).
+std::vector<std::pair<int, int>> launch_records(const Plan& P)
+{
+    std::vector<std::pair<int, int>> r;
+    for (size_t w = 0; w < P.wl.size(); ++w) r.push_back({(int)w, -1});
+    for (size_t c = 0; c < P.classes.size(); ++c)
+        if (!P.classes[c].warp) r.push_back({-1, (int)c});
+    return r;
+}
+
 int run_solve(Plan& P, int steps, int flags, cudaEvent_t* ev = nullptr)
 {
     CUDA_TRY(cudaMemsetAsync(P.d_queue, 0, sizeof(int32_t) * P.classes.size(), P.stream));
-    for (size_t c = 0; c < P.classes.size(); ++c) {
-        const LaunchClass& L = P.classes[c];
-        SolveArgs a{};
-        a.items = P.d_items + L.item_begin;
-        a.n_items = L.item_count;
-        a.steps = steps;
-        a.flags = flags;
-        a.smem_group = L.smem_group;
-        a.insts = P.d_insts;
-        a.u_out = P.d_u;
-        a.state = P.d_state;
-        a.queue = P.d_queue + c;
-        a.glog = L.glog;
-        a.lu_scratch = P.d_lu ? P.d_lu + L.lu_offset : nullptr;
-        a.lu_stride = L.lu_stride;
-        if (ev) CUDA_TRY(cudaEventRecord(ev[2 * c], P.stream));
-        const int rc = launch_for(L.N)(a, L.mixed, L.warp, L.block, L.grid, L.smem, P.stream);
-        if (ev) CUDA_TRY(cudaEventRecord(ev[2 * c + 1], P.stream));
+    const std::vector<std::pair<int, int>> recs = launch_records(P);
+    for (size_t r = 0; r < recs.size(); ++r) {
+        int rc = 0;
+        // external records so that they also record when replayed from a graph
+        if (ev) CUDA_TRY(cudaEventRecordWithFlags(ev[2 * r], P.stream, cudaEventRecordExternal));
+        if (recs[r].first >= 0) {
+            const Plan::WarpLaunch& w = P.wl[recs[r].first];
+            SolveArgs a = class_args(P, P.classes[w.covers[0]], 0, steps, flags);
+            a.items = P.d_items;
+            a.queue = P.d_queue;
+            a.classes = P.d_cdesc + w.desc_offset;
+            a.n_classes = (int32_t)w.cls.size();
+            a.smem_warp = w.smem_warp;
+            rc = launch_for(w.N)(a, w.mixed, true, w.block, w.grid, w.smem, P.stream);
+        } else {
+            const int c = recs[r].second;
+            const LaunchClass& L = P.classes[c];
+            rc = launch_for(L.N)(class_args(P, L, c, steps, flags), L.mixed, false, L.block, L.grid,
+                                 L.smem, P.stream);
+        }
+        if (ev) CUDA_TRY(cudaEventRecordWithFlags(ev[2 * r + 1], P.stream, cudaEventRecordExternal));
         if (rc != 0) return fail(AMFRW_ECUDA, std::string("solver launch: ") + cudaGetErrorString((cudaError_t)rc));
     }
     return AMFRW_OK;
@@ -515,12 +646,106 @@ struct amfrw_problem {
 struct amfrw_batch {
     Plan plan;
     bool timing = false;
-    std::vector<cudaEvent_t> ev;   // two per solver launch
+    std::vector<cudaEvent_t> ev;       // two per launch record
+    cudaStream_t capture = nullptr;    // private stream the graph is captured on
+    cudaGraphExec_t exec = nullptr;    // the captured solve + combination
+    bool exec_timing = false;          // whether the graph records the timing events
     ~amfrw_batch()
     {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (capture) cudaStreamDestroy(capture);
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
     }
 };
+
+namespace {
+
+// Launch-strategy cache of the autotuner: class signature -> multi on/off.
+std::mutex g_tune_mutex;
+std::map<std::string, bool> g_tune_cache;
+
+std::string class_signature(const Plan& P)
+{
+    std::string sig;
+    for (const LaunchClass& c : P.classes) {
+        sig += std::to_string(c.N) + (c.mixed ? "m" : "d") + (c.warp ? "w" : "c") +
+               std::to_string(P.items[c.item_begin].L) + ":" +
+               std::to_string(c.item_count > 4096 ? 4096 : c.item_count) + ";";
+    }
+    return sig;
+}
+
+void load_tune_file()
+{
+    static bool loaded = false;
+    if (loaded) return;
+    loaded = true;
+    const char* path = getenv("AMFRW_TUNE_CACHE");
+    if (!path) return;
+    FILE* f = fopen(path, "r");
+    if (!f) return;
+    char line[8192];
+    while (fgets(line, sizeof(line), f)) {
+        char* sp = strrchr(line, ' ');
+        if (!sp) continue;
+        *sp = 0;
+        g_tune_cache[line] = atoi(sp + 1) != 0;
+    }
+    fclose(f);
+}
+
+void save_tune_entry(const std::string& sig, bool multi)
+{
+    const char* path = getenv("AMFRW_TUNE_CACHE");
+    if (!path) return;
+    FILE* f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s %d\n", sig.c_str(), multi ? 1 : 0);
+    fclose(f);
+}
+
+// Capture solve + combination into a CUDA graph on the batch's private stream.
+int capture_graph(amfrw_batch* b)
+{
+    Plan& P = b->plan;
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    if (!b->capture) CUDA_TRY(cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking));
+    cudaStream_t user = P.stream;
+    P.stream = b->capture;
+    CUDA_TRY(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal));
+    int st = run_solve(P, P.insts[0].n_steps, 0, b->timing ? b->ev.data() : nullptr);
+    if (st == AMFRW_OK) st = run_combine(P, P.d_prices);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->capture, &g);
+    P.stream = user;
+    if (st != AMFRW_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return fail(AMFRW_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&b->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(AMFRW_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    b->exec_timing = b->timing;
+    return AMFRW_OK;
+}
+
+int ensure_events(amfrw_batch* b)
+{
+    const size_t need = 2 * b->plan.classes.size();
+    while (b->ev.size() < need) {
+        cudaEvent_t e;
+        CUDA_TRY(cudaEventCreate(&e));
+        b->ev.push_back(e);
+    }
+    return AMFRW_OK;
+}
+
+}  // namespace
+
 
 extern "C" {
 
@@ -650,6 +875,20 @@ int amfrw_batch_create(const amfrw_params* ps, int32_t n, void* cuda_stream, amf
         delete b;
         return fail(AMFRW_EINVAL, "all instances of a batch must use the same n_steps");
     }
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        load_tune_file();
+        auto it = g_tune_cache.find(class_signature(b->plan));
+        if (it != g_tune_cache.end() && it->second != b->plan.use_multi) {
+            b->plan.use_multi = it->second;
+            st = build_warp_launches(b->plan);
+            if (st == AMFRW_OK) st = upload_warp_launches(b->plan);
+            if (st != AMFRW_OK) {
+                delete b;
+                return st;
+            }
+        }
+    }
     *out = b;
     return AMFRW_OK;
 }
@@ -658,17 +897,76 @@ int amfrw_batch_run(amfrw_batch* b, double* d_prices_out)
 {
     if (!b || !d_prices_out) return fail(AMFRW_EINVAL, "NULL argument");
     Plan& P = b->plan;
-    int st = run_solve(P, P.insts[0].n_steps, 0, b->timing ? b->ev.data() : nullptr);
-    if (st != AMFRW_OK) return st;
-    return run_combine(P, d_prices_out);
+    // the solve and the combination are replayed from a CUDA graph
+    if (!b->exec || b->exec_timing != b->timing) {
+        int st = capture_graph(b);
+        if (st != AMFRW_OK) return st;
+    }
+    CUDA_TRY(cudaGraphLaunch(b->exec, P.stream));
+    if (d_prices_out != P.d_prices)
+        CUDA_TRY(cudaMemcpyAsync(d_prices_out, P.d_prices, sizeof(double) * P.n_inst,
+                                 cudaMemcpyDeviceToDevice, P.stream));
+    return AMFRW_OK;
+}
+
+int amfrw_batch_autotune(amfrw_batch* b, int32_t trials, int32_t* use_multi_out)
+{
+    if (!b) return fail(AMFRW_EINVAL, "NULL argument");
+    Plan& P = b->plan;
+    if (trials < 1) trials = 1;
+    bool best = P.use_multi;
+    // the strategies differ only if some (N, precision) has several warp classes
+    bool differs = false;
+    for (size_t c = 0; c < P.classes.size(); ++c)
+        for (size_t d = c + 1; d < P.classes.size(); ++d)
+            if (P.classes[c].warp && P.classes[d].warp && P.classes[c].N == P.classes[d].N &&
+                P.classes[c].mixed == P.classes[d].mixed)
+                differs = true;
+    if (differs) {
+        cudaEvent_t e0, e1;
+        CUDA_TRY(cudaEventCreate(&e0));
+        CUDA_TRY(cudaEventCreate(&e1));
+        float t[2] = {0.f, 0.f};
+        int st = AMFRW_OK;
+        for (int m = 0; m < 2 && st == AMFRW_OK; ++m) {
+            P.use_multi = m == 1;
+            st = build_warp_launches(P);
+            if (st == AMFRW_OK) st = upload_warp_launches(P);
+            if (st == AMFRW_OK) st = run_solve(P, P.insts[0].n_steps, 0);  // warm-up
+            if (st != AMFRW_OK) break;
+            cudaEventRecord(e0, P.stream);
+            for (int k = 0; k < trials && st == AMFRW_OK; ++k) st = run_solve(P, P.insts[0].n_steps, 0);
+            cudaEventRecord(e1, P.stream);
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(&t[m], e0, e1);
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (st != AMFRW_OK) return st;
+        best = t[1] <= t[0];
+        P.use_multi = best;
+        st = build_warp_launches(P);
+        if (st == AMFRW_OK) st = upload_warp_launches(P);
+        if (st != AMFRW_OK) return st;
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        const std::string sig = class_signature(P);
+        g_tune_cache[sig] = best;
+        save_tune_entry(sig, best);
+        if (b->exec) {
+            cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+        }
+    }
+    if (use_multi_out) *use_multi_out = best ? 1 : 0;
+    return AMFRW_OK;
 }
 
 int amfrw_batch_enable_timing(amfrw_batch* b, int32_t on)
 {
     if (!b) return fail(AMFRW_EINVAL, "NULL argument");
-    if (on && b->ev.empty()) {
-        b->ev.resize(2 * b->plan.classes.size());
-        for (cudaEvent_t& e : b->ev) CUDA_TRY(cudaEventCreate(&e));
+    if (on) {
+        int st = ensure_events(b);
+        if (st != AMFRW_OK) return st;
     }
     b->timing = on != 0;
     return AMFRW_OK;
@@ -680,18 +978,24 @@ int amfrw_batch_kernel_times(amfrw_batch* b, float* ms_out, double* node_steps_o
     if (!b || !ms_out || !n_out) return fail(AMFRW_EINVAL, "NULL argument");
     if (b->ev.empty()) return fail(AMFRW_EINVAL, "timing is not enabled");
     const Plan& P = b->plan;
-    const int n = std::min<int>(cap, (int)P.classes.size());
-    for (int c = 0; c < n; ++c) {
-        CUDA_TRY(cudaEventSynchronize(b->ev[2 * c + 1]));
-        CUDA_TRY(cudaEventElapsedTime(&ms_out[c], b->ev[2 * c], b->ev[2 * c + 1]));
-        const LaunchClass& L = P.classes[c];
-        if (node_steps_out) {
-            double s = 0.0;
+    const std::vector<std::pair<int, int>> recs = launch_records(P);
+    const int n = std::min<int>(cap, (int)recs.size());
+    for (int r = 0; r < n; ++r) {
+        CUDA_TRY(cudaEventSynchronize(b->ev[2 * r + 1]));
+        CUDA_TRY(cudaEventElapsedTime(&ms_out[r], b->ev[2 * r], b->ev[2 * r + 1]));
+        std::vector<int> cls;
+        if (recs[r].first >= 0) cls = P.wl[recs[r].first].covers;
+        else cls.push_back(recs[r].second);
+        double s = 0.0;
+        int dim = 0;
+        for (int c : cls) {
+            const LaunchClass& L = P.classes[c];
             for (int k = L.item_begin; k < L.item_begin + L.item_count; ++k)
                 s += (double)P.items[k].L * (double)P.insts[P.items[k].inst].n_steps;
-            node_steps_out[c] = s;
+            dim = (cls.size() == 1) ? L.N : 0;
         }
-        if (dims_out) dims_out[c] = L.N;
+        if (node_steps_out) node_steps_out[r] = s;
+        if (dims_out) dims_out[r] = dim;
     }
     *n_out = n;
     return AMFRW_OK;
@@ -710,7 +1014,7 @@ int amfrw_batch_io_bytes(const amfrw_batch* b, int64_t* h2d_bytes, int64_t* d2h_
 int amfrw_batch_launches(const amfrw_batch* b, int32_t* n_launches)
 {
     if (!b || !n_launches) return fail(AMFRW_EINVAL, "NULL argument");
-    *n_launches = (int32_t)b->plan.classes.size() + 1;
+    *n_launches = (int32_t)launch_records(b->plan).size() + 1;
     return AMFRW_OK;
 }
 
@@ -793,14 +1097,17 @@ void noalloc_release_host(Plan& P)
     std::vector<double>().swap(P.coefs);
     std::vector<int8_t>().swap(P.levels);
     std::vector<LaunchClass>().swap(P.classes);
+    std::vector<Plan::WarpLaunch>().swap(P.wl);
     P.d_insts = nullptr; P.d_items = nullptr; P.d_coefs = nullptr; P.d_u = nullptr;
     P.d_prices = nullptr; P.d_queue = nullptr; P.d_flag = nullptr; P.d_state = nullptr;
     P.d_lu = nullptr;
+    P.d_cdesc = nullptr;
 }
 
 int noalloc_run(const amfrw_params* ps, int n, double* d_prices_out, cudaStream_t stream, Plan& P)
 {
     int st = plan_host(ps, n, false, P);
+    if (st == AMFRW_OK) st = build_warp_launches(P);
     if (st != AMFRW_OK) return st;
     const int s0 = P.insts[0].n_steps;
     for (const InstDev& I : P.insts)
@@ -812,7 +1119,8 @@ int noalloc_run(const amfrw_params* ps, int n, double* d_prices_out, cudaStream_
     const int64_t o_u = align256(o_coef + (int64_t)(sizeof(double) * P.coefs.size()));
     const int64_t o_queue = align256(o_u + (int64_t)(sizeof(double) * P.coefs.size()));
     const int64_t o_flag = align256(o_queue + (int64_t)(sizeof(int32_t) * P.classes.size()));
-    const int64_t o_lu = align256(o_flag + (int64_t)sizeof(int32_t));
+    const int64_t o_desc = align256(o_flag + (int64_t)sizeof(int32_t));
+    const int64_t o_lu = align256(o_desc + (int64_t)(sizeof(ClassDesc) * P.n_cdesc));
     const int64_t total = o_lu + P.lu_scratch_len;
     if (total > (int64_t)AMFRW_NOALLOC_SCRATCH_BYTES)
         return fail(AMFRW_ETOOBIG, "problem needs " + std::to_string(total) +
@@ -829,6 +1137,12 @@ int noalloc_run(const amfrw_params* ps, int n, double* d_prices_out, cudaStream_
     P.d_queue = reinterpret_cast<int32_t*>(base + o_queue);
     P.d_flag = reinterpret_cast<int32_t*>(base + o_flag);
     P.d_lu = P.lu_scratch_len > 0 ? base + o_lu : nullptr;
+    P.d_cdesc = reinterpret_cast<ClassDesc*>(base + o_desc);
+    std::vector<ClassDesc> descs;
+    for (const Plan::WarpLaunch& w : P.wl) descs.insert(descs.end(), w.cls.begin(), w.cls.end());
+    if (!descs.empty())
+        CUDA_TRY(cudaMemcpyAsync(P.d_cdesc, descs.data(), sizeof(ClassDesc) * descs.size(),
+                                 cudaMemcpyHostToDevice, stream));
     // the array keeps the previous call's contents: the records are rewritten,
     // the per-grid values cleared, and run_solve / run_combine zero the counters
     CUDA_TRY(cudaMemcpyAsync(P.d_insts, P.insts.data(), sizeof(InstDev) * P.insts.size(),

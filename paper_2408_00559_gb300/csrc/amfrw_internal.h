@@ -11,6 +11,7 @@
 namespace amfrw {
 
 constexpr int kMaxDim = 8;
+constexpr int kCtaMaxThreads = 256;  // CTA work groups (grids of more than 64 Inner nodes)
 
 // Per-instance parameters on the device (one per pricing problem).
 struct InstDev {
@@ -139,6 +140,12 @@ AMFRW_HD Layout make_layout(int N, const int8_t* lv, bool mixed, bool lu_smem, i
     return y;
 }
 
+// One grid class of a warp-group launch: grids of one size solved by work
+// groups of 2^glog lanes (several groups per warp when glog < 5).
+struct ClassDesc {
+    int32_t glog, item_begin, item_count, smem_group, qidx, pad;  // qidx: its work counter
+};
+
 // Launch-time arguments of the solver kernels.
 struct SolveArgs {
     const Item* items;
@@ -150,9 +157,12 @@ struct SolveArgs {
     double* u_out;        // [n grids] u_l(x*)
     double* state;        // state pool (Inner values of Y), may be null
     int32_t* queue;       // work counter, zero before the launch
-    int32_t glog;         // warp groups: log2 lanes per group (grids of 2^glog <= 32 nodes share a warp)
     unsigned char* lu_scratch;  // CTA groups: Thomas factors, lu_stride bytes per block
     int64_t lu_stride;
+    // warp groups: the classes of this launch, walked in order by every warp
+    const ClassDesc* classes;
+    int32_t n_classes;
+    int32_t smem_warp;    // dynamic shared bytes per warp
 };
 
 constexpr int kLoadState = 1;

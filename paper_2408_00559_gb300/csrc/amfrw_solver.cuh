@@ -919,36 +919,48 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
     gsync<WARP>(gm);  // the group's shared memory is reused by its next grid
 }
 
+// The solver kernel.  CTA groups: one grid per block at a time from the
+// launch's work counter.  Warp groups: a persistent multi-class launch -- every
+// warp walks the launch's class list (ordered largest grids first) and takes
+// chunks of 32 >> glog grids from each class's counter until it is exhausted,
+// then moves on, so classes of uneven instances share one launch and no warp
+// waits for another.
 template <int N, bool MIXED, bool WARP>
-__global__ void __launch_bounds__(WARP ? 128 : 512) solve_kernel(SolveArgs a)
+__global__ void __launch_bounds__(WARP ? 128 : kCtaMaxThreads) solve_kernel(SolveArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_item;
-    // warp groups: 2^glog lanes per grid, 32 >> glog grids per warp
-    const int glog = WARP ? a.glog : 0;
-    const int gid = WARP ? (int)(threadIdx.x >> glog) : 0;
-    const int rank = WARP ? (int)(threadIdx.x & ((1 << glog) - 1)) : (int)threadIdx.x;
-    const int gsize = WARP ? (1 << glog) : (int)blockDim.x;
-    const int lane = threadIdx.x & 31;
-    unsigned char* base = smem + (size_t)gid * (size_t)a.smem_group;
-    for (;;) {
-        int item;
-        if (WARP) {
+    if constexpr (WARP) {
+        const int warp = threadIdx.x >> 5;
+        const int lane = threadIdx.x & 31;
+        unsigned char* wbase = smem + (size_t)warp * (size_t)a.smem_warp;
+        int c = 0;
+        while (c < a.n_classes) {
+            const ClassDesc cd = a.classes[c];
             int chunk = 0;
-            if (lane == 0) chunk = atomicAdd(a.queue, 32 >> glog);
+            if (lane == 0) chunk = atomicAdd(a.queue + cd.qidx, 32 >> cd.glog);
             chunk = __shfl_sync(0xffffffffu, chunk, 0);
-            if (chunk >= a.n_items) break;
-            item = chunk + (lane >> glog);
-        } else {
+            if (chunk >= cd.item_count) {
+                ++c;
+                continue;
+            }
+            const int item = chunk + (lane >> cd.glog);
+            if (item < cd.item_count) {
+                const Item it = a.items[cd.item_begin + item];
+                const int gsize = 1 << cd.glog;
+                unsigned char* base = wbase + (size_t)(lane >> cd.glog) * (size_t)cd.smem_group;
+                solve_item<N, MIXED, true>(a, it, base, lane & (gsize - 1), gsize);
+            }
+        }
+    } else {
+        __shared__ int s_item;
+        for (;;) {
             if (threadIdx.x == 0) s_item = atomicAdd(a.queue, 1);
             __syncthreads();
-            item = s_item;
+            const int item = s_item;
             __syncthreads();
             if (item >= a.n_items) break;
-        }
-        if (item < a.n_items) {
             const Item it = a.items[item];
-            solve_item<N, MIXED, WARP>(a, it, base, rank, gsize);
+            solve_item<N, MIXED, false>(a, it, smem, (int)threadIdx.x, (int)blockDim.x);
         }
     }
 }
