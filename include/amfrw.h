@@ -207,6 +207,18 @@ int amfrw_batch_io_bytes(const amfrw_batch *b, int64_t *h2d_bytes, int64_t *d2h_
 void amfrw_batch_destroy(amfrw_batch *b);
 
 /* ------------------------------------------------------------------------
+ * Surrogate network building block (the paper has no counterpart; the
+ * surrogate is an addition to the method).  C[M x N] = A[M x K] * B[N x K]^T
+ * on the tensor cores (tcgen05, BF16 operands, FP32 accumulation).  A, B:
+ * DEVICE, row-major BF16 with leading dimensions lda, ldb (multiples of 8,
+ * >= K, 16-byte aligned); C: DEVICE FP32 row-major with leading dimension
+ * ldc >= N.  Requires N a multiple of 16 (and of 256 when above 256), K a
+ * multiple of 16.  Synchronises.  Errors: EINVAL, ENOMEM, ECUDA, ETIMEOUT
+ * (a bounded wait inside the kernel gave up; the result is not valid). */
+int amfrw_tc_gemm_bf16(const void *dA, int32_t lda, const void *dB, int32_t ldb, float *dC,
+                       int32_t ldc, int32_t M, int32_t N, int32_t K, void *cuda_stream);
+
+/* ------------------------------------------------------------------------
  * Pricing without device allocation.  The paper has no counterpart: this is
  * an integration entry point of the library.
  *

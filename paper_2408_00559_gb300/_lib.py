@@ -27,7 +27,7 @@ EXPORTS = [
     "amfrw_problem_destroy", "amfrw_solve_batch", "amfrw_batch_create", "amfrw_batch_run",
     "amfrw_batch_launches", "amfrw_batch_destroy", "amfrw_status_string", "amfrw_last_error",
     "amfrw_batch_enable_timing", "amfrw_batch_kernel_times", "amfrw_batch_io_bytes",
-    "amfrw_solve_noalloc", "amfrw_batch_autotune",
+    "amfrw_solve_noalloc", "amfrw_batch_autotune", "amfrw_tc_gemm_bf16",
 ]
 
 
@@ -85,6 +85,8 @@ def lib():
         L.amfrw_batch_io_bytes.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         L.amfrw_solve_noalloc.argtypes = [pp, C.c_int32, vp, vp]
         L.amfrw_batch_autotune.argtypes = [vp, C.c_int32, C.POINTER(C.c_int32)]
+        i32 = C.c_int32
+        L.amfrw_tc_gemm_bf16.argtypes = [vp, i32, vp, i32, vp, i32, i32, i32, i32, vp]
         L.amfrw_status_string.restype = C.c_char_p
         L.amfrw_status_string.argtypes = [C.c_int]
         L.amfrw_last_error.restype = C.c_char_p
@@ -277,3 +279,17 @@ def solve_noalloc(insts: list[dict], d_prices_ptr: int, stream=None):
     m = _Marshal(insts)
     _check(lib().amfrw_solve_noalloc(m.arr, len(insts), C.c_void_p(int(d_prices_ptr)),
                                      _stream_ptr(stream)), "amfrw_solve_noalloc")
+
+
+def tc_gemm_bf16(A, B, C, stream=None):
+    """C = A @ B.T on the tensor cores; A [M,K], B [N,K] BF16, C [M,N] FP32
+    CUDA tensors (row-major, contiguous)."""
+    M, K = A.shape
+    N = B.shape[0]
+    _check(lib().amfrw_tc_gemm_bf16(C_void(A.data_ptr()), A.stride(0), C_void(B.data_ptr()), B.stride(0),
+                                    C_void(C.data_ptr()), C.stride(0), M, N, K, _stream_ptr(stream)),
+           "amfrw_tc_gemm_bf16")
+
+
+def C_void(p):
+    return C.c_void_p(int(p))
