@@ -219,6 +219,59 @@ int amfrw_tc_gemm_bf16(const void *dA, int32_t lda, const void *dB, int32_t ldb,
                        int32_t ldc, int32_t M, int32_t N, int32_t K, void *cuda_stream);
 
 /* ------------------------------------------------------------------------
+ * Surrogate pricing with solver fallback (the paper has no counterpart; it is
+ * an addition to the method).  An ensemble of MLPs 8 -> 256 -> 256 -> 256 -> 1
+ * with GELU, BF16 weights and activations on the tensor cores (tcgen05) and
+ * FP32 accumulation, maps the features (alpha, sigma, beta, K, T, mean phi,
+ * min phi, max phi) of an instance to its price.  One surrogate serves one
+ * instance family: every other field of amfrw_params (N, level, psi, steps,
+ * precision, F0, Fmax, tau, rho, V0, Vmax, discount, theta, nu_amf) equal to
+ * the training set's, and one alpha shared by all rates.  The ensemble spread
+ * times a calibration factor estimates the error; eval answers from the
+ * network where that estimate is within rel_bound * |price| and falls back to
+ * the batched solver (amfrw_solve_batch) for every other query, including
+ * queries outside the family or outside the trained feature box.  All
+ * parameter arrays are host memory; calls synchronise.  Errors are reported by
+ * amfrw_surrogate_last_error().
+ *   create     n_members in [1, 16] networks, He initialisation from `seed`.
+ *   fit        trains every member (Adam, cosine-decayed learning rate, MSE on
+ *              normalised prices, batches of 1024) on n >= 1024 instances and
+ *              their solver prices; *final_loss_out (may be NULL) = mean loss
+ *              of the last epoch.
+ *   calibrate  on an audit sample judged by the solver: the factor is the
+ *              `quantile` of |error| / spread; stores rel_bound.
+ *   predict    ensemble mean and spread per instance; in_domain_out (may be
+ *              NULL) = 1 inside the family and feature box.
+ *   eval       prices_out [n] (network or solver), fell_back_out [n] (may be
+ *              NULL): 1 where the solver priced the instance.
+ *   save/load  plain binary file (magic AMFRWSG1, scaling, family, FP32
+ *              weights).
+ *   params     FP32 parameters of one member (136193 floats: W1 [256 x 16]
+ *              (inputs 8..15 are padding), b1 [256], W2 [256 x 256], b2, W3,
+ *              b3, w4 [256], b4), read to params_out and/or set from
+ *              params_in (either may be NULL).
+ *   grad       loss 1/2 mean (y - t)^2 and its gradient (same layout) for one
+ *              batch of `rows` (multiple of 16, <= 1024) normalised feature
+ *              rows x_norm [rows x 8] and targets [rows]; no update. */
+typedef struct amfrw_surrogate amfrw_surrogate;
+int amfrw_surrogate_create(int32_t n_members, uint64_t seed, void *cuda_stream, amfrw_surrogate **out);
+int amfrw_surrogate_fit(amfrw_surrogate *s, const amfrw_params *ps, const double *prices, int64_t n,
+                        int32_t epochs, float lr, float *final_loss_out);
+int amfrw_surrogate_calibrate(amfrw_surrogate *s, const amfrw_params *ps, const double *prices, int64_t n,
+                              double rel_bound, double quantile, double *calib_out);
+int amfrw_surrogate_predict(amfrw_surrogate *s, const amfrw_params *ps, int64_t n, double *mean_out,
+                            double *spread_out, uint8_t *in_domain_out);
+int amfrw_surrogate_eval(amfrw_surrogate *s, const amfrw_params *ps, int64_t n, double *prices_out,
+                         uint8_t *fell_back_out, void *cuda_stream);
+int amfrw_surrogate_save(const amfrw_surrogate *s, const char *path);
+int amfrw_surrogate_load(const char *path, void *cuda_stream, amfrw_surrogate **out);
+int amfrw_surrogate_params(amfrw_surrogate *s, int32_t member, float *params_out, const float *params_in);
+int amfrw_surrogate_grad(amfrw_surrogate *s, int32_t member, const float *x_norm, const float *targets,
+                         int32_t rows, float *grad_out, float *loss_out);
+void amfrw_surrogate_destroy(amfrw_surrogate *s);
+const char *amfrw_surrogate_last_error(void);
+
+/* ------------------------------------------------------------------------
  * Pricing without device allocation.  The paper has no counterpart: this is
  * an integration entry point of the library.
  *

@@ -28,7 +28,12 @@ EXPORTS = [
     "amfrw_batch_launches", "amfrw_batch_destroy", "amfrw_status_string", "amfrw_last_error",
     "amfrw_batch_enable_timing", "amfrw_batch_kernel_times", "amfrw_batch_io_bytes",
     "amfrw_solve_noalloc", "amfrw_batch_autotune", "amfrw_tc_gemm_bf16",
+    "amfrw_surrogate_create", "amfrw_surrogate_fit", "amfrw_surrogate_calibrate",
+    "amfrw_surrogate_predict", "amfrw_surrogate_eval", "amfrw_surrogate_save",
+    "amfrw_surrogate_load", "amfrw_surrogate_params", "amfrw_surrogate_grad",
+    "amfrw_surrogate_destroy", "amfrw_surrogate_last_error",
 ]
+SURROGATE_PARAMS = 136193
 
 
 class AmfrwError(RuntimeError):
@@ -87,6 +92,21 @@ def lib():
         L.amfrw_batch_autotune.argtypes = [vp, C.c_int32, C.POINTER(C.c_int32)]
         i32 = C.c_int32
         L.amfrw_tc_gemm_bf16.argtypes = [vp, i32, vp, i32, vp, i32, i32, i32, i32, vp]
+        i64, u8p, fp = C.c_int64, C.POINTER(C.c_uint8), C.POINTER(C.c_float)
+        dpp = C.POINTER(C.c_double)
+        L.amfrw_surrogate_create.argtypes = [i32, C.c_uint64, vp, C.POINTER(vp)]
+        L.amfrw_surrogate_fit.argtypes = [vp, pp, dpp, i64, i32, C.c_float, fp]
+        L.amfrw_surrogate_calibrate.argtypes = [vp, pp, dpp, i64, C.c_double, C.c_double, dpp]
+        L.amfrw_surrogate_predict.argtypes = [vp, pp, i64, dpp, dpp, u8p]
+        L.amfrw_surrogate_eval.argtypes = [vp, pp, i64, dpp, u8p, vp]
+        L.amfrw_surrogate_save.argtypes = [vp, C.c_char_p]
+        L.amfrw_surrogate_load.argtypes = [C.c_char_p, vp, C.POINTER(vp)]
+        L.amfrw_surrogate_params.argtypes = [vp, i32, fp, fp]
+        L.amfrw_surrogate_grad.argtypes = [vp, i32, fp, fp, i32, fp, fp]
+        L.amfrw_surrogate_destroy.argtypes = [vp]
+        L.amfrw_surrogate_destroy.restype = None
+        L.amfrw_surrogate_last_error.restype = C.c_char_p
+        L.amfrw_surrogate_last_error.argtypes = []
         L.amfrw_status_string.restype = C.c_char_p
         L.amfrw_status_string.argtypes = [C.c_int]
         L.amfrw_last_error.restype = C.c_char_p
@@ -293,3 +313,116 @@ def tc_gemm_bf16(A, B, C, stream=None):
 
 def C_void(p):
     return C.c_void_p(int(p))
+
+
+def _scheck(rc: int, where: str):
+    if rc != AMFRW_OK:
+        raise AmfrwError(rc, where, lib().amfrw_surrogate_last_error().decode())
+
+
+def _fp(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+class Surrogate:
+    """amfrw_surrogate: an ensemble of MLPs trained on solver prices, with the
+    batched solver as fallback (see include/amfrw.h)."""
+
+    def __init__(self, members: int = 4, seed: int = 0, stream=None, _handle=None):
+        self.stream = stream
+        if _handle is not None:
+            self.h = _handle
+            return
+        self.h = C.c_void_p()
+        _scheck(lib().amfrw_surrogate_create(int(members), int(seed), _stream_ptr(stream), C.byref(self.h)),
+                "amfrw_surrogate_create")
+
+    def fit(self, insts, prices, epochs: int = 40, lr: float = 2e-3) -> float:
+        m = _Marshal(insts)
+        pr = np.ascontiguousarray(prices, dtype=np.float64)
+        loss = C.c_float()
+        _scheck(lib().amfrw_surrogate_fit(self.h, m.arr, _dp(pr), len(insts), int(epochs), float(lr),
+                                          C.byref(loss)), "amfrw_surrogate_fit")
+        return loss.value
+
+    def calibrate(self, insts, prices, rel_bound: float = 1e-3, quantile: float = 0.99) -> float:
+        m = _Marshal(insts)
+        pr = np.ascontiguousarray(prices, dtype=np.float64)
+        c = C.c_double()
+        _scheck(lib().amfrw_surrogate_calibrate(self.h, m.arr, _dp(pr), len(insts), float(rel_bound),
+                                                float(quantile), C.byref(c)), "amfrw_surrogate_calibrate")
+        return c.value
+
+    def predict(self, insts):
+        m = _Marshal(insts)
+        n = len(insts)
+        mean, spread = np.zeros(n), np.zeros(n)
+        ok = np.zeros(n, dtype=np.uint8)
+        _scheck(lib().amfrw_surrogate_predict(self.h, m.arr, n, _dp(mean), _dp(spread),
+                                              ok.ctypes.data_as(C.POINTER(C.c_uint8))),
+                "amfrw_surrogate_predict")
+        return mean, spread, ok.astype(bool)
+
+    def eval(self, insts, marshalled=None):
+        m = marshalled if marshalled is not None else _Marshal(insts)
+        n = len(insts) if insts is not None else len(m.arr)
+        prices = np.zeros(n)
+        fell = np.zeros(n, dtype=np.uint8)
+        _scheck(lib().amfrw_surrogate_eval(self.h, m.arr, n, _dp(prices),
+                                           fell.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                           _stream_ptr(self.stream)), "amfrw_surrogate_eval")
+        return prices, fell.astype(bool)
+
+    def save(self, path: str):
+        _scheck(lib().amfrw_surrogate_save(self.h, str(path).encode()), "amfrw_surrogate_save")
+
+    @staticmethod
+    def load(path: str, stream=None) -> "Surrogate":
+        h = C.c_void_p()
+        _scheck(lib().amfrw_surrogate_load(str(path).encode(), _stream_ptr(stream), C.byref(h)),
+                "amfrw_surrogate_load")
+        return Surrogate(stream=stream, _handle=h)
+
+    def params(self, member: int = 0, new=None) -> np.ndarray:
+        out = np.zeros(SURROGATE_PARAMS, dtype=np.float32)
+        src = None
+        if new is not None:
+            src = np.ascontiguousarray(new, dtype=np.float32)
+            assert src.size == SURROGATE_PARAMS
+        _scheck(lib().amfrw_surrogate_params(self.h, int(member), _fp(out),
+                                             _fp(src) if src is not None else None),
+                "amfrw_surrogate_params")
+        return out
+
+    def grad(self, member: int, x_norm, targets):
+        x = np.ascontiguousarray(x_norm, dtype=np.float32)
+        t = np.ascontiguousarray(targets, dtype=np.float32)
+        g = np.zeros(SURROGATE_PARAMS, dtype=np.float32)
+        loss = C.c_float()
+        _scheck(lib().amfrw_surrogate_grad(self.h, int(member), _fp(x), _fp(t), x.shape[0], _fp(g),
+                                           C.byref(loss)), "amfrw_surrogate_grad")
+        return g, loss.value
+
+    def close(self):
+        if self.h:
+            lib().amfrw_surrogate_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def surrogate_layout():
+    """Offsets of the FP32 parameter vector of one member."""
+    W, P = 256, 16
+    o = {}
+    off = 0
+    for name, size in (("W1", W * P), ("b1", W), ("W2", W * W), ("b2", W), ("W3", W * W), ("b3", W),
+                       ("w4", W), ("b4", 1)):
+        o[name] = (off, size)
+        off += size
+    assert off == SURROGATE_PARAMS
+    return o

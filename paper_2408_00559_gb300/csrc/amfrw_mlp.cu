@@ -56,3 +56,783 @@ extern "C" int amfrw_tc_gemm_bf16(const void* dA, int32_t lda, const void* dB, i
     if (rc != 0) return AMFRW_ECUDA;
     return herr ? AMFRW_ETIMEOUT : AMFRW_OK;
 }
+
+// ===========================================================================
+// Surrogate network: 8 features -> 256 -> 256 -> 256 -> 1, GELU, BF16 weights
+// and activations for the tensor-core GEMMs, FP32 accumulation, FP32 master
+// weights trained with Adam; an ensemble of independently seeded members
+// whose spread estimates the error.  All arithmetic runs in the kernels below
+// and in the tcgen05 GEMM.
+// ===========================================================================
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <new>
+#include <random>
+#include <vector>
+
+namespace amfrw {
+namespace sg {
+
+constexpr int kIn = 8;        // features
+constexpr int kInPad = 16;    // first-layer K padded to the MMA's K
+constexpr int kW = 256;       // hidden width
+constexpr int kTrainRows = 1024;
+constexpr int kPredRows = 65536;
+// FP32 parameter vector of one member
+constexpr int oW1 = 0;
+constexpr int ob1 = oW1 + kW * kInPad;
+constexpr int oW2 = ob1 + kW;
+constexpr int ob2 = oW2 + kW * kW;
+constexpr int oW3 = ob2 + kW;
+constexpr int ob3 = oW3 + kW * kW;
+constexpr int ow4 = ob3 + kW;
+constexpr int ob4 = ow4 + kW;
+constexpr int kParams = ob4 + 1;
+
+using bf16 = __nv_bfloat16;
+
+// Batch of rows (gathered through idx, or consecutive from r0) as BF16 input
+// X [B x 16] (features then zero padding), its transpose Xt [16 x B], and
+// the targets.
+__global__ void pack_kernel(const float* __restrict__ feats, const float* __restrict__ targets,
+                            const int* __restrict__ idx, int r0, int B, bf16* X, bf16* Xt, float* t)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= B * kInPad) return;
+    const int b = q / kInPad, c = q % kInPad;
+    const int row = idx ? idx[b] : r0 + b;
+    const float v = c < kIn ? feats[(size_t)row * kIn + c] : 0.0f;
+    const bf16 h = __float2bfloat16(v);
+    X[(size_t)b * kInPad + c] = h;
+    if (Xt) Xt[(size_t)c * B + b] = h;
+    if (c == 0 && t) t[b] = targets[row];
+}
+
+// y_b = H3_b . w4 + b4 (one warp per row).
+__global__ void out_fwd_kernel(const bf16* __restrict__ H3, const float* __restrict__ P, float* y, int B)
+{
+    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (b >= B) return;
+    float s = 0.0f;
+    for (int k = lane; k < kW; k += 32) s += __bfloat162float(H3[(size_t)b * kW + k]) * P[ow4 + k];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) y[b] = s + P[ob4];
+}
+
+// L = 1/2 mean (y - t)^2: dy = (y - t)/B, dZ3 = dy w4 gelu'(Z3) (BF16 and its
+// transpose), loss accumulated into *loss.
+__global__ void out_bwd_kernel(const float* __restrict__ y, const float* __restrict__ t,
+                               const float* __restrict__ P, const float* __restrict__ Z3, int B,
+                               bf16* dZ3, bf16* dZ3t, float* dy, float* loss)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= B * kW) return;
+    const int b = q / kW, k = q % kW;
+    const float r = y[b] - t[b];
+    const float d = r / (float)B;
+    if (k == 0) {
+        dy[b] = d;
+        atomicAdd(loss, 0.5f * r * r / (float)B);
+    }
+    const bf16 h = __float2bfloat16(d * P[ow4 + k] * tc::gelu_grad(Z3[(size_t)b * kW + k]));
+    dZ3[(size_t)b * kW + k] = h;
+    dZ3t[(size_t)k * B + b] = h;
+}
+
+// Output-layer gradients: g_w4[k] = sum_b dy_b H3[b][k], g_b4 = sum_b dy_b.
+__global__ void out_wgrad_kernel(const bf16* __restrict__ H3, const float* __restrict__ dy, int B, float* G)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > kW) return;
+    float s = 0.0f;
+    if (k < kW) {
+        for (int b = 0; b < B; ++b) s += dy[b] * __bfloat162float(H3[(size_t)b * kW + k]);
+        G[ow4 + k] = s;
+    } else {
+        for (int b = 0; b < B; ++b) s += dy[b];
+        G[ob4] = s;
+    }
+}
+
+// Bias gradients from the transposed layer gradient dZt [N x B]: one warp per row.
+__global__ void rowsum_kernel(const bf16* __restrict__ dZt, int N, int B, float* gb)
+{
+    const int n = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (n >= N) return;
+    float s = 0.0f;
+    for (int b = lane; b < B; b += 32) s += __bfloat162float(dZt[(size_t)n * B + b]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) gb[n] = s;
+}
+
+__global__ void adam_kernel(float* P, const float* __restrict__ G, float* Mo, float* Vo, int n, float lr,
+                            float b1, float b2, float eps, float bc1, float bc2)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float g = G[i];
+    const float m = b1 * Mo[i] + (1.0f - b1) * g;
+    const float v = b2 * Vo[i] + (1.0f - b2) * g * g;
+    Mo[i] = m;
+    Vo[i] = v;
+    P[i] -= lr * (m / bc1) / (sqrtf(v / bc2) + eps);
+}
+
+// BF16 copy of a weight matrix [rows x cols] and optionally its transpose.
+__global__ void cast_kernel(const float* __restrict__ W, int rows, int cols, bf16* Wb, bf16* Wtb)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows * cols) return;
+    const int r = i / cols, c = i % cols;
+    const bf16 h = __float2bfloat16(W[i]);
+    Wb[i] = h;
+    if (Wtb) Wtb[(size_t)c * rows + r] = h;
+}
+
+// Ensemble mean and sample standard deviation of the members' outputs.
+__global__ void ensemble_kernel(const float* __restrict__ ys, int members, int n, float* mean, float* spread)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float s = 0.0f;
+    for (int m = 0; m < members; ++m) s += ys[(size_t)m * n + i];
+    const float mu = s / (float)members;
+    float q = 0.0f;
+    for (int m = 0; m < members; ++m) {
+        const float d = ys[(size_t)m * n + i] - mu;
+        q += d * d;
+    }
+    mean[i] = mu;
+    spread[i] = members > 1 ? sqrtf(q / (float)(members - 1)) : 0.0f;
+}
+
+inline int cdiv(int a, int b) { return (a + b - 1) / b; }
+
+}  // namespace sg
+}  // namespace amfrw
+
+using namespace amfrw::sg;
+
+namespace {
+
+thread_local std::string g_sg_error;
+
+int sg_fail(int st, const std::string& m)
+{
+    g_sg_error = m;
+    return st;
+}
+
+#define SG_CUDA(expr)                                                                       \
+    do {                                                                                    \
+        cudaError_t e_ = (expr);                                                            \
+        if (e_ != cudaSuccess) return sg_fail(AMFRW_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+// The instance family a surrogate serves: every field of amfrw_params except
+// the features (alpha, shared by all rates; sigma; beta; K; T; phi).
+struct Family {
+    int32_t n_rates, payoff, n_steps, level, psi, full_grid, precision;
+    double F0[7], Fmax[7], tau[7], rho[49];
+    double V0, Vmax, discount, theta, nu;
+};
+
+bool close_(double a, double b) { return std::fabs(a - b) <= 1e-12 * std::max(1.0, std::fabs(b)); }
+
+Family family_of(const amfrw_params& p)
+{
+    Family f{};
+    f.n_rates = p.n_rates;
+    f.payoff = p.payoff;
+    f.n_steps = p.n_steps;
+    f.level = p.level;
+    f.psi = p.psi;
+    f.full_grid = p.full_grid;
+    f.precision = p.precision;
+    for (int i = 0; i < p.n_rates; ++i) {
+        f.F0[i] = p.F0[i];
+        f.Fmax[i] = p.Fmax[i];
+        f.tau[i] = p.tau[i];
+        for (int k = 0; k < p.n_rates; ++k) f.rho[i * 7 + k] = p.rho[i * p.n_rates + k];
+    }
+    f.V0 = p.V0;
+    f.Vmax = p.Vmax;
+    f.discount = p.discount;
+    f.theta = p.theta;
+    f.nu = p.nu_amf;
+    return f;
+}
+
+bool in_family(const Family& f, const amfrw_params& p)
+{
+    if (p.n_rates != f.n_rates || p.payoff != f.payoff || p.n_steps != f.n_steps || p.level != f.level ||
+        p.psi != f.psi || p.full_grid != f.full_grid || p.precision != f.precision)
+        return false;
+    for (int i = 0; i < p.n_rates; ++i) {
+        if (!close_(p.F0[i], f.F0[i]) || !close_(p.Fmax[i], f.Fmax[i]) || !close_(p.tau[i], f.tau[i]))
+            return false;
+        if (!close_(p.alpha[i], p.alpha[0])) return false;  // one alpha shared by all rates
+        for (int k = 0; k < p.n_rates; ++k)
+            if (!close_(p.rho[i * p.n_rates + k], f.rho[i * 7 + k])) return false;
+    }
+    return close_(p.V0, f.V0) && close_(p.Vmax, f.Vmax) && close_(p.discount, f.discount) &&
+           close_(p.theta, f.theta) && close_(p.nu_amf, f.nu);
+}
+
+// (alpha, sigma, beta, K, T, mean phi, min phi, max phi)
+void features_of(const amfrw_params& p, double* f)
+{
+    double s = 0.0, mn = 1e300, mx = -1e300;
+    for (int i = 0; i < p.n_rates; ++i) {
+        s += p.phi[i];
+        mn = std::min(mn, p.phi[i]);
+        mx = std::max(mx, p.phi[i]);
+    }
+    f[0] = p.alpha[0];
+    f[1] = p.sigma;
+    f[2] = p.beta;
+    f[3] = p.K;
+    f[4] = p.T;
+    f[5] = s / p.n_rates;
+    f[6] = mn;
+    f[7] = mx;
+}
+
+}  // namespace
+
+struct amfrw_surrogate {
+    int members = 0;
+    uint64_t seed = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<float*> P, G, Mo, Vo;
+    std::vector<bf16*> W1b, W2b, W3b, W2tb, W3tb;
+    // work buffers: training batch (kTrainRows) and prediction chunk (kPredRows)
+    bf16 *X = nullptr, *Xt = nullptr, *H1 = nullptr, *H2 = nullptr, *H3 = nullptr, *H1t = nullptr, *H2t = nullptr;
+    bf16 *dZ1 = nullptr, *dZ2 = nullptr, *dZ3 = nullptr, *dZ1t = nullptr, *dZ2t = nullptr, *dZ3t = nullptr;
+    float *Z1 = nullptr, *Z2 = nullptr, *Z3 = nullptr, *y = nullptr, *t = nullptr, *dy = nullptr;
+    float *loss = nullptr, *ys = nullptr;
+    int* err = nullptr;
+    int adam_t = 0;
+    double fmin[kIn], fmax[kIn];
+    double ymu = 0.0, ysd = 1.0;
+    double calib = 0.0, rel_bound = 1e-3;
+    bool trained = false, calibrated = false;
+    Family fam{};
+    ~amfrw_surrogate()
+    {
+        for (auto v : {&P, &G, &Mo, &Vo})
+            for (float* q : *v) cudaFree(q);
+        for (auto v : {&W1b, &W2b, &W3b, &W2tb, &W3tb})
+            for (bf16* q : *v) cudaFree(q);
+        for (void* q : {(void*)X, (void*)Xt, (void*)H1, (void*)H2, (void*)H3, (void*)H1t, (void*)H2t,
+                        (void*)dZ1, (void*)dZ2, (void*)dZ3, (void*)dZ1t, (void*)dZ2t, (void*)dZ3t,
+                        (void*)Z1, (void*)Z2, (void*)Z3, (void*)y, (void*)t, (void*)dy, (void*)loss,
+                        (void*)ys, (void*)err})
+            cudaFree(q);
+    }
+};
+
+namespace {
+
+int sg_alloc(amfrw_surrogate* s)
+{
+    const size_t TR = kTrainRows, PR = kPredRows, PQ = std::max(TR, PR);
+    const size_t B2 = sizeof(bf16), F4 = sizeof(float);
+    for (int m = 0; m < s->members; ++m) {
+        float *p, *g, *mo, *vo;
+        bf16 *w1, *w2, *w3, *w2t, *w3t;
+        SG_CUDA(cudaMalloc(&p, F4 * kParams));
+        SG_CUDA(cudaMalloc(&g, F4 * kParams));
+        SG_CUDA(cudaMalloc(&mo, F4 * kParams));
+        SG_CUDA(cudaMalloc(&vo, F4 * kParams));
+        SG_CUDA(cudaMalloc(&w1, B2 * kW * kInPad));
+        SG_CUDA(cudaMalloc(&w2, B2 * kW * kW));
+        SG_CUDA(cudaMalloc(&w3, B2 * kW * kW));
+        SG_CUDA(cudaMalloc(&w2t, B2 * kW * kW));
+        SG_CUDA(cudaMalloc(&w3t, B2 * kW * kW));
+        s->P.push_back(p); s->G.push_back(g); s->Mo.push_back(mo); s->Vo.push_back(vo);
+        s->W1b.push_back(w1); s->W2b.push_back(w2); s->W3b.push_back(w3);
+        s->W2tb.push_back(w2t); s->W3tb.push_back(w3t);
+    }
+    SG_CUDA(cudaMalloc(&s->X, B2 * PQ * kInPad));
+    SG_CUDA(cudaMalloc(&s->Xt, B2 * TR * kInPad));
+    for (bf16** q : {&s->H1, &s->H2, &s->H3}) SG_CUDA(cudaMalloc(q, B2 * PQ * kW));
+    for (bf16** q : {&s->H1t, &s->H2t, &s->dZ1, &s->dZ2, &s->dZ3, &s->dZ1t, &s->dZ2t, &s->dZ3t})
+        SG_CUDA(cudaMalloc(q, B2 * TR * kW));
+    for (float** q : {&s->Z1, &s->Z2, &s->Z3}) SG_CUDA(cudaMalloc(q, F4 * TR * kW));
+    SG_CUDA(cudaMalloc(&s->y, F4 * PQ));
+    SG_CUDA(cudaMalloc(&s->t, F4 * TR));
+    SG_CUDA(cudaMalloc(&s->dy, F4 * TR));
+    SG_CUDA(cudaMalloc(&s->loss, F4));
+    SG_CUDA(cudaMalloc(&s->ys, F4 * PQ * (size_t)s->members));
+    SG_CUDA(cudaMalloc(&s->err, sizeof(int)));
+    SG_CUDA(cudaMemsetAsync(s->err, 0, sizeof(int), s->stream));
+    return AMFRW_OK;
+}
+
+// BF16 weight copies of member m from its FP32 master weights.
+void sg_cast(amfrw_surrogate* s, int m)
+{
+    cudaStream_t st = s->stream;
+    cast_kernel<<<cdiv(kW * kInPad, 256), 256, 0, st>>>(s->P[m] + oW1, kW, kInPad, s->W1b[m], nullptr);
+    cast_kernel<<<cdiv(kW * kW, 256), 256, 0, st>>>(s->P[m] + oW2, kW, kW, s->W2b[m], s->W2tb[m]);
+    cast_kernel<<<cdiv(kW * kW, 256), 256, 0, st>>>(s->P[m] + oW3, kW, kW, s->W3b[m], s->W3tb[m]);
+}
+
+// Forward pass of member m on B packed rows in s->X; output into y.  With
+// train set, keeps the pre-activations and transposes the backward pass needs.
+int sg_forward(amfrw_surrogate* s, int m, int B, bool train, float* y)
+{
+    cudaStream_t st = s->stream;
+    tc::Epi e{};
+    e.mode = 1;
+    e.error = s->err;
+    e.ldt = B;
+    e.bias = s->P[m] + ob1; e.Z = train ? s->Z1 : nullptr; e.H = s->H1; e.Ht = train ? s->H1t : nullptr;
+    int rc = tc::gemm(s->X, kInPad, s->W1b[m], kInPad, B, kW, kInPad, e, st);
+    e.bias = s->P[m] + ob2; e.Z = train ? s->Z2 : nullptr; e.H = s->H2; e.Ht = train ? s->H2t : nullptr;
+    if (!rc) rc = tc::gemm(s->H1, kW, s->W2b[m], kW, B, kW, kW, e, st);
+    e.bias = s->P[m] + ob3; e.Z = train ? s->Z3 : nullptr; e.H = s->H3; e.Ht = nullptr;
+    if (!rc) rc = tc::gemm(s->H2, kW, s->W3b[m], kW, B, kW, kW, e, st);
+    if (!rc) out_fwd_kernel<<<cdiv(B * 32, 256), 256, 0, st>>>(s->H3, s->P[m], y, B);
+    if (rc) return sg_fail(AMFRW_ECUDA, std::string("surrogate forward: ") + cudaGetErrorString((cudaError_t)rc));
+    return AMFRW_OK;
+}
+
+// Loss gradient of member m on the packed batch (targets in s->t) into s->G[m].
+int sg_backward(amfrw_surrogate* s, int m, int B)
+{
+    cudaStream_t st = s->stream;
+    float* G = s->G[m];
+    out_bwd_kernel<<<cdiv(B * kW, 256), 256, 0, st>>>(s->y, s->t, s->P[m], s->Z3, B, s->dZ3, s->dZ3t, s->dy, s->loss);
+    out_wgrad_kernel<<<cdiv(kW + 1, 128), 128, 0, st>>>(s->H3, s->dy, B, G);
+    tc::Epi e{};
+    e.error = s->err;
+    e.ldt = B;
+    // W3, b3
+    e.mode = 0; e.C = G + oW3; e.ldc = kW;
+    int rc = tc::gemm(s->dZ3t, B, s->H2t, B, kW, kW, B, e, st);
+    rowsum_kernel<<<cdiv(kW * 32, 256), 256, 0, st>>>(s->dZ3t, kW, B, G + ob3);
+    // dZ2 = (dZ3 W3) * gelu'(Z2)
+    e.mode = 2; e.H = s->dZ2; e.Ht = s->dZ2t; e.Zprev = s->Z2;
+    if (!rc) rc = tc::gemm(s->dZ3, kW, s->W3tb[m], kW, B, kW, kW, e, st);
+    e.mode = 0; e.C = G + oW2; e.ldc = kW;
+    if (!rc) rc = tc::gemm(s->dZ2t, B, s->H1t, B, kW, kW, B, e, st);
+    rowsum_kernel<<<cdiv(kW * 32, 256), 256, 0, st>>>(s->dZ2t, kW, B, G + ob2);
+    // dZ1 = (dZ2 W2) * gelu'(Z1)
+    e.mode = 2; e.H = s->dZ1; e.Ht = s->dZ1t; e.Zprev = s->Z1;
+    if (!rc) rc = tc::gemm(s->dZ2, kW, s->W2tb[m], kW, B, kW, kW, e, st);
+    e.mode = 0; e.C = G + oW1; e.ldc = kInPad;
+    if (!rc) rc = tc::gemm(s->dZ1t, B, s->Xt, B, kW, kInPad, B, e, st);
+    rowsum_kernel<<<cdiv(kW * 32, 256), 256, 0, st>>>(s->dZ1t, kW, B, G + ob1);
+    if (rc) return sg_fail(AMFRW_ECUDA, std::string("surrogate backward: ") + cudaGetErrorString((cudaError_t)rc));
+    return AMFRW_OK;
+}
+
+int sg_check_err(amfrw_surrogate* s)
+{
+    int h = 0;
+    SG_CUDA(cudaMemcpyAsync(&h, s->err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    SG_CUDA(cudaStreamSynchronize(s->stream));
+    if (h) return sg_fail(AMFRW_ETIMEOUT, "a bounded wait in the tensor-core GEMM gave up");
+    return AMFRW_OK;
+}
+
+// Normalised features of n instances (host, n x 8 floats); false entries of
+// ok_out for instances outside the family or the trained feature box.
+void sg_features(const amfrw_surrogate* s, const amfrw_params* ps, int64_t n, std::vector<float>& out,
+                 std::vector<char>* ok_out)
+{
+    out.assign((size_t)n * kIn, 0.0f);
+    if (ok_out) ok_out->assign((size_t)n, 1);
+    for (int64_t i = 0; i < n; ++i) {
+        double f[kIn];
+        features_of(ps[i], f);
+        bool ok = in_family(s->fam, ps[i]);
+        for (int c = 0; c < kIn; ++c) {
+            const double span = s->fmax[c] - s->fmin[c];
+            double z = span > 0 ? 2.0 * (f[c] - s->fmin[c]) / span - 1.0 : 0.0;
+            if (z < -1.0 - 1e-9 || z > 1.0 + 1e-9) ok = false;
+            out[(size_t)i * kIn + c] = (float)z;
+        }
+        if (ok_out) (*ok_out)[(size_t)i] = ok ? 1 : 0;
+    }
+}
+
+// Ensemble mean and spread (denormalised prices) of n rows of normalised
+// features on the device.
+int sg_predict_dev(amfrw_surrogate* s, const float* d_feats, int64_t n, std::vector<double>& mean,
+                   std::vector<double>& spread)
+{
+    cudaStream_t st = s->stream;
+    mean.assign((size_t)n, 0.0);
+    spread.assign((size_t)n, 0.0);
+    std::vector<float> hm, hs;
+    float *d_mean = nullptr, *d_spread = nullptr;
+    SG_CUDA(cudaMalloc(&d_mean, sizeof(float) * kPredRows));
+    SG_CUDA(cudaMalloc(&d_spread, sizeof(float) * kPredRows));
+    int st_ = AMFRW_OK;
+    for (int64_t r0 = 0; r0 < n && st_ == AMFRW_OK; r0 += kPredRows) {
+        const int B = (int)std::min<int64_t>(kPredRows, n - r0);
+        pack_kernel<<<cdiv(B * kInPad, 256), 256, 0, st>>>(d_feats + (size_t)r0 * kIn, nullptr, nullptr, 0, B,
+                                                          s->X, nullptr, nullptr);
+        for (int m = 0; m < s->members && st_ == AMFRW_OK; ++m)
+            st_ = sg_forward(s, m, B, false, s->ys + (size_t)m * B);
+        if (st_ != AMFRW_OK) break;
+        ensemble_kernel<<<cdiv(B, 256), 256, 0, st>>>(s->ys, s->members, B, d_mean, d_spread);
+        hm.resize(B);
+        hs.resize(B);
+        cudaMemcpyAsync(hm.data(), d_mean, sizeof(float) * B, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(hs.data(), d_spread, sizeof(float) * B, cudaMemcpyDeviceToHost, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) st_ = sg_fail(AMFRW_ECUDA, "surrogate prediction");
+        for (int i = 0; i < B; ++i) {
+            mean[(size_t)(r0 + i)] = s->ymu + s->ysd * (double)hm[i];
+            spread[(size_t)(r0 + i)] = s->ysd * (double)hs[i];
+        }
+    }
+    cudaFree(d_mean);
+    cudaFree(d_spread);
+    if (st_ != AMFRW_OK) return st_;
+    return sg_check_err(s);
+}
+
+int sg_predict_host(amfrw_surrogate* s, const amfrw_params* ps, int64_t n, std::vector<double>& mean,
+                    std::vector<double>& spread, std::vector<char>& ok)
+{
+    std::vector<float> feats;
+    sg_features(s, ps, n, feats, &ok);
+    float* d = nullptr;
+    SG_CUDA(cudaMalloc(&d, sizeof(float) * feats.size()));
+    cudaMemcpyAsync(d, feats.data(), sizeof(float) * feats.size(), cudaMemcpyHostToDevice, s->stream);
+    const int st = sg_predict_dev(s, d, n, mean, spread);
+    cudaFree(d);
+    return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* amfrw_surrogate_last_error(void) { return g_sg_error.c_str(); }
+
+int amfrw_surrogate_create(int32_t n_members, uint64_t seed, void* cuda_stream, amfrw_surrogate** out)
+{
+    if (!out) return sg_fail(AMFRW_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_members < 1 || n_members > 16) return sg_fail(AMFRW_EINVAL, "n_members must be in [1, 16]");
+    amfrw_surrogate* s = new (std::nothrow) amfrw_surrogate();
+    if (!s) return sg_fail(AMFRW_ENOMEM, "host allocation failed");
+    s->members = n_members;
+    s->seed = seed;
+    s->stream = (cudaStream_t)cuda_stream;
+    int st = sg_alloc(s);
+    if (st != AMFRW_OK) {
+        delete s;
+        return st;
+    }
+    // He-style initialisation of every member from its own seed
+    std::vector<float> h(kParams);
+    for (int m = 0; m < n_members; ++m) {
+        std::mt19937_64 rng(seed * 1000003ull + (uint64_t)m);
+        std::normal_distribution<float> nd(0.0f, 1.0f);
+        std::fill(h.begin(), h.end(), 0.0f);
+        for (int o = 0; o < kW; ++o)
+            for (int i = 0; i < kIn; ++i) h[oW1 + o * kInPad + i] = nd(rng) * std::sqrt(2.0f / kIn);
+        for (int q = 0; q < kW * kW; ++q) h[oW2 + q] = nd(rng) * std::sqrt(2.0f / kW);
+        for (int q = 0; q < kW * kW; ++q) h[oW3 + q] = nd(rng) * std::sqrt(2.0f / kW);
+        for (int q = 0; q < kW; ++q) h[ow4 + q] = nd(rng) * std::sqrt(1.0f / kW);
+        cudaMemcpyAsync(s->P[m], h.data(), sizeof(float) * kParams, cudaMemcpyHostToDevice, s->stream);
+        cudaMemsetAsync(s->Mo[m], 0, sizeof(float) * kParams, s->stream);
+        cudaMemsetAsync(s->Vo[m], 0, sizeof(float) * kParams, s->stream);
+        sg_cast(s, m);
+    }
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) {
+        delete s;
+        return sg_fail(AMFRW_ECUDA, "surrogate initialisation");
+    }
+    *out = s;
+    return AMFRW_OK;
+}
+
+int amfrw_surrogate_fit(amfrw_surrogate* s, const amfrw_params* ps, const double* prices, int64_t n,
+                        int32_t epochs, float lr, float* final_loss_out)
+{
+    if (!s || !ps || !prices) return sg_fail(AMFRW_EINVAL, "NULL argument");
+    if (n < kTrainRows) return sg_fail(AMFRW_EINVAL, "need at least 1024 training instances");
+    if (epochs < 1 || !(lr > 0.0f)) return sg_fail(AMFRW_EINVAL, "epochs >= 1 and lr > 0 required");
+    // family, feature box and target scaling from the training set
+    s->fam = family_of(ps[0]);
+    for (int c = 0; c < kIn; ++c) {
+        s->fmin[c] = 1e300;
+        s->fmax[c] = -1e300;
+    }
+    double sum = 0.0, sq = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!in_family(s->fam, ps[i])) return sg_fail(AMFRW_EINVAL, "training instances must share one family");
+        if (!std::isfinite(prices[i])) return sg_fail(AMFRW_EINVAL, "non-finite training price");
+        double f[kIn];
+        features_of(ps[i], f);
+        for (int c = 0; c < kIn; ++c) {
+            s->fmin[c] = std::min(s->fmin[c], f[c]);
+            s->fmax[c] = std::max(s->fmax[c], f[c]);
+        }
+        sum += prices[i];
+        sq += prices[i] * prices[i];
+    }
+    s->ymu = sum / (double)n;
+    s->ysd = std::sqrt(std::max(sq / (double)n - s->ymu * s->ymu, 1e-300));
+    std::vector<float> feats, targ((size_t)n);
+    sg_features(s, ps, n, feats, nullptr);
+    for (int64_t i = 0; i < n; ++i) targ[(size_t)i] = (float)((prices[i] - s->ymu) / s->ysd);
+    cudaStream_t st = s->stream;
+    float *d_feats = nullptr, *d_targ = nullptr;
+    int* d_idx = nullptr;
+    SG_CUDA(cudaMalloc(&d_feats, sizeof(float) * feats.size()));
+    SG_CUDA(cudaMalloc(&d_targ, sizeof(float) * n));
+    SG_CUDA(cudaMalloc(&d_idx, sizeof(int) * n));
+    cudaMemcpyAsync(d_feats, feats.data(), sizeof(float) * feats.size(), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(d_targ, targ.data(), sizeof(float) * n, cudaMemcpyHostToDevice, st);
+    const int B = kTrainRows;
+    const int64_t steps_per_epoch = n / B;
+    const int64_t total = steps_per_epoch * epochs;
+    std::vector<int> perm((size_t)n);
+    int rc = AMFRW_OK;
+    float last = 0.0f;
+    for (int m = 0; m < s->members && rc == AMFRW_OK; ++m) {
+        std::mt19937_64 rng(s->seed * 7919ull + 17ull * (uint64_t)m + 1ull);
+        int64_t step = 0;
+        for (int ep = 0; ep < epochs && rc == AMFRW_OK; ++ep) {
+            for (int64_t i = 0; i < n; ++i) perm[(size_t)i] = (int)i;
+            std::shuffle(perm.begin(), perm.end(), rng);
+            cudaMemcpyAsync(d_idx, perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st);
+            cudaMemsetAsync(s->loss, 0, sizeof(float), st);
+            for (int64_t k = 0; k < steps_per_epoch && rc == AMFRW_OK; ++k, ++step) {
+                pack_kernel<<<cdiv(B * kInPad, 256), 256, 0, st>>>(d_feats, d_targ, d_idx + k * B, 0, B, s->X,
+                                                                  s->Xt, s->t);
+                rc = sg_forward(s, m, B, true, s->y);
+                if (rc == AMFRW_OK) rc = sg_backward(s, m, B);
+                // Adam with cosine decay to 1% of lr
+                const double frac = (double)step / (double)std::max<int64_t>(1, total - 1);
+                const float lr_t = (float)(lr * (0.01 + 0.99 * 0.5 * (1.0 + std::cos(M_PI * frac))));
+                const int t = (int)step + 1;
+                const float bc1 = 1.0f - std::pow(0.9f, (float)t), bc2 = 1.0f - std::pow(0.999f, (float)t);
+                adam_kernel<<<cdiv(kParams, 256), 256, 0, st>>>(s->P[m], s->G[m], s->Mo[m], s->Vo[m], kParams,
+                                                               lr_t, 0.9f, 0.999f, 1e-8f, bc1, bc2);
+                sg_cast(s, m);
+            }
+            if (rc == AMFRW_OK && ep == epochs - 1) {
+                float hl = 0.0f;
+                cudaMemcpyAsync(&hl, s->loss, sizeof(float), cudaMemcpyDeviceToHost, st);
+                cudaStreamSynchronize(st);
+                last += hl / (float)steps_per_epoch / (float)s->members;
+            }
+        }
+    }
+    cudaFree(d_feats);
+    cudaFree(d_targ);
+    cudaFree(d_idx);
+    if (rc != AMFRW_OK) return rc;
+    rc = sg_check_err(s);
+    if (rc != AMFRW_OK) return rc;
+    if (cudaGetLastError() != cudaSuccess) return sg_fail(AMFRW_ECUDA, "surrogate training kernels");
+    s->trained = true;
+    if (final_loss_out) *final_loss_out = last;
+    return AMFRW_OK;
+}
+
+int amfrw_surrogate_predict(amfrw_surrogate* s, const amfrw_params* ps, int64_t n, double* mean_out,
+                            double* spread_out, uint8_t* in_domain_out)
+{
+    if (!s || !ps || !mean_out || !spread_out) return sg_fail(AMFRW_EINVAL, "NULL argument");
+    if (!s->trained) return sg_fail(AMFRW_EINVAL, "surrogate is not trained");
+    std::vector<double> mean, spread;
+    std::vector<char> ok;
+    int st = sg_predict_host(s, ps, n, mean, spread, ok);
+    if (st != AMFRW_OK) return st;
+    for (int64_t i = 0; i < n; ++i) {
+        mean_out[i] = mean[(size_t)i];
+        spread_out[i] = spread[(size_t)i];
+        if (in_domain_out) in_domain_out[i] = ok[(size_t)i] ? 1 : 0;
+    }
+    return AMFRW_OK;
+}
+
+int amfrw_surrogate_calibrate(amfrw_surrogate* s, const amfrw_params* ps, const double* prices, int64_t n,
+                              double rel_bound, double quantile, double* calib_out)
+{
+    if (!s || !ps || !prices) return sg_fail(AMFRW_EINVAL, "NULL argument");
+    if (!s->trained) return sg_fail(AMFRW_EINVAL, "surrogate is not trained");
+    if (n < 16 || !(rel_bound > 0) || !(quantile > 0 && quantile <= 1))
+        return sg_fail(AMFRW_EINVAL, "need n >= 16, rel_bound > 0, quantile in (0, 1]");
+    std::vector<double> mean, spread;
+    std::vector<char> ok;
+    int st = sg_predict_host(s, ps, n, mean, spread, ok);
+    if (st != AMFRW_OK) return st;
+    std::vector<double> ratio;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!ok[(size_t)i]) continue;
+        const double e = std::fabs(mean[(size_t)i] - prices[i]);
+        ratio.push_back(e / std::max(spread[(size_t)i], 1e-300));
+    }
+    if (ratio.size() < 16) return sg_fail(AMFRW_EINVAL, "too few audit instances inside the family");
+    std::sort(ratio.begin(), ratio.end());
+    const size_t k = std::min(ratio.size() - 1, (size_t)std::ceil(quantile * (double)ratio.size()) - 1);
+    s->calib = ratio[k];
+    s->rel_bound = rel_bound;
+    s->calibrated = true;
+    if (calib_out) *calib_out = s->calib;
+    return AMFRW_OK;
+}
+
+int amfrw_surrogate_eval(amfrw_surrogate* s, const amfrw_params* ps, int64_t n, double* prices_out,
+                         uint8_t* fell_back_out, void* cuda_stream)
+{
+    if (!s || !ps || !prices_out) return sg_fail(AMFRW_EINVAL, "NULL argument");
+    if (!s->trained || !s->calibrated) return sg_fail(AMFRW_EINVAL, "surrogate is not trained and calibrated");
+    std::vector<double> mean, spread;
+    std::vector<char> ok;
+    int st = sg_predict_host(s, ps, n, mean, spread, ok);
+    if (st != AMFRW_OK) return st;
+    std::vector<amfrw_params> fb;
+    std::vector<int64_t> where;
+    for (int64_t i = 0; i < n; ++i) {
+        const double est = s->calib * spread[(size_t)i];
+        const bool fall = !ok[(size_t)i] || !(est <= s->rel_bound * std::fabs(mean[(size_t)i]));
+        if (fell_back_out) fell_back_out[i] = fall ? 1 : 0;
+        if (fall) {
+            fb.push_back(ps[i]);
+            where.push_back(i);
+        } else {
+            prices_out[i] = mean[(size_t)i];
+        }
+    }
+    // the solver judges and replaces what the network cannot vouch for; one
+    // batch per step count (a batch shares n_steps)
+    std::vector<size_t> order(fb.size());
+    for (size_t k = 0; k < order.size(); ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return fb[a].n_steps < fb[b].n_steps; });
+    for (size_t k0 = 0; k0 < order.size();) {
+        size_t k1 = k0;
+        while (k1 < order.size() && k1 - k0 < 4096 && fb[order[k1]].n_steps == fb[order[k0]].n_steps) ++k1;
+        std::vector<amfrw_params> grp;
+        for (size_t k = k0; k < k1; ++k) grp.push_back(fb[order[k]]);
+        std::vector<double> pr(grp.size());
+        st = amfrw_solve_batch(grp.data(), (int32_t)grp.size(), pr.data(), cuda_stream);
+        if (st != AMFRW_OK) return sg_fail(st, std::string("fallback solve: ") + amfrw_last_error());
+        for (size_t k = k0; k < k1; ++k) prices_out[where[order[k]]] = pr[k - k0];
+        k0 = k1;
+    }
+    return AMFRW_OK;
+}
+
+int amfrw_surrogate_save(const amfrw_surrogate* s, const char* path)
+{
+    if (!s || !path) return sg_fail(AMFRW_EINVAL, "NULL argument");
+    FILE* f = fopen(path, "wb");
+    if (!f) return sg_fail(AMFRW_EINVAL, std::string("cannot open ") + path);
+    const char magic[8] = {'A', 'M', 'F', 'R', 'W', 'S', 'G', '1'};
+    std::vector<float> h(kParams);
+    bool ok = fwrite(magic, 1, 8, f) == 8;
+    ok = ok && fwrite(&s->members, sizeof(int), 1, f) == 1;
+    ok = ok && fwrite(s->fmin, sizeof(double), kIn, f) == (size_t)kIn;
+    ok = ok && fwrite(s->fmax, sizeof(double), kIn, f) == (size_t)kIn;
+    const double sc[4] = {s->ymu, s->ysd, s->calib, s->rel_bound};
+    ok = ok && fwrite(sc, sizeof(double), 4, f) == 4;
+    const int flags[2] = {s->trained ? 1 : 0, s->calibrated ? 1 : 0};
+    ok = ok && fwrite(flags, sizeof(int), 2, f) == 2;
+    ok = ok && fwrite(&s->fam, sizeof(Family), 1, f) == 1;
+    for (int m = 0; m < s->members && ok; ++m) {
+        ok = cudaMemcpy(h.data(), s->P[m], sizeof(float) * kParams, cudaMemcpyDeviceToHost) == cudaSuccess;
+        ok = ok && fwrite(h.data(), sizeof(float), kParams, f) == (size_t)kParams;
+    }
+    fclose(f);
+    return ok ? AMFRW_OK : sg_fail(AMFRW_ECUDA, "surrogate save failed");
+}
+
+int amfrw_surrogate_load(const char* path, void* cuda_stream, amfrw_surrogate** out)
+{
+    if (!path || !out) return sg_fail(AMFRW_EINVAL, "NULL argument");
+    *out = nullptr;
+    FILE* f = fopen(path, "rb");
+    if (!f) return sg_fail(AMFRW_EINVAL, std::string("cannot open ") + path);
+    char magic[8];
+    int members = 0;
+    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "AMFRWSG1", 8) == 0;
+    ok = ok && fread(&members, sizeof(int), 1, f) == 1 && members >= 1 && members <= 16;
+    amfrw_surrogate* s = nullptr;
+    if (ok && amfrw_surrogate_create(members, 0, cuda_stream, &s) != AMFRW_OK) ok = false;
+    double sc[4];
+    int flags[2];
+    if (ok) {
+        ok = fread(s->fmin, sizeof(double), kIn, f) == (size_t)kIn && fread(s->fmax, sizeof(double), kIn, f) == (size_t)kIn;
+        ok = ok && fread(sc, sizeof(double), 4, f) == 4 && fread(flags, sizeof(int), 2, f) == 2;
+        ok = ok && fread(&s->fam, sizeof(Family), 1, f) == 1;
+    }
+    std::vector<float> h(kParams);
+    for (int m = 0; ok && m < members; ++m) {
+        ok = fread(h.data(), sizeof(float), kParams, f) == (size_t)kParams;
+        ok = ok && cudaMemcpy(s->P[m], h.data(), sizeof(float) * kParams, cudaMemcpyHostToDevice) == cudaSuccess;
+        if (ok) sg_cast(s, m);
+    }
+    fclose(f);
+    if (!ok) {
+        delete s;
+        return sg_fail(AMFRW_EINVAL, std::string("not a surrogate file: ") + path);
+    }
+    s->ymu = sc[0]; s->ysd = sc[1]; s->calib = sc[2]; s->rel_bound = sc[3];
+    s->trained = flags[0] != 0;
+    s->calibrated = flags[1] != 0;
+    cudaStreamSynchronize(s->stream);
+    *out = s;
+    return AMFRW_OK;
+}
+
+// Parameters of one member (FP32, the layout described in include/amfrw.h)
+// and the loss gradient of one packed batch, for gradient checks.
+int amfrw_surrogate_params(amfrw_surrogate* s, int32_t member, float* params_out, const float* params_in)
+{
+    if (!s || member < 0 || member >= s->members) return sg_fail(AMFRW_EINVAL, "bad member");
+    if (params_in) {
+        SG_CUDA(cudaMemcpy(s->P[member], params_in, sizeof(float) * kParams, cudaMemcpyHostToDevice));
+        sg_cast(s, member);
+        SG_CUDA(cudaStreamSynchronize(s->stream));
+    }
+    if (params_out) SG_CUDA(cudaMemcpy(params_out, s->P[member], sizeof(float) * kParams, cudaMemcpyDeviceToHost));
+    return AMFRW_OK;
+}
+
+int amfrw_surrogate_grad(amfrw_surrogate* s, int32_t member, const float* x_norm, const float* targets,
+                         int32_t rows, float* grad_out, float* loss_out)
+{
+    if (!s || !x_norm || !targets || !grad_out || member < 0 || member >= s->members)
+        return sg_fail(AMFRW_EINVAL, "bad argument");
+    if (rows < 16 || rows > kTrainRows || rows % 16) return sg_fail(AMFRW_EINVAL, "rows must be a multiple of 16 in [16, 1024]");
+    cudaStream_t st = s->stream;
+    float *d_x = nullptr, *d_t = nullptr;
+    SG_CUDA(cudaMalloc(&d_x, sizeof(float) * rows * kIn));
+    SG_CUDA(cudaMalloc(&d_t, sizeof(float) * rows));
+    cudaMemcpyAsync(d_x, x_norm, sizeof(float) * rows * kIn, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(d_t, targets, sizeof(float) * rows, cudaMemcpyHostToDevice, st);
+    cudaMemsetAsync(s->loss, 0, sizeof(float), st);
+    cudaMemsetAsync(s->G[member], 0, sizeof(float) * kParams, st);
+    pack_kernel<<<cdiv(rows * kInPad, 256), 256, 0, st>>>(d_x, d_t, nullptr, 0, rows, s->X, s->Xt, s->t);
+    int rc = sg_forward(s, member, rows, true, s->y);
+    if (rc == AMFRW_OK) rc = sg_backward(s, member, rows);
+    if (rc == AMFRW_OK) {
+        cudaMemcpyAsync(grad_out, s->G[member], sizeof(float) * kParams, cudaMemcpyDeviceToHost, st);
+        if (loss_out) cudaMemcpyAsync(loss_out, s->loss, sizeof(float), cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+    }
+    cudaFree(d_x);
+    cudaFree(d_t);
+    if (rc != AMFRW_OK) return rc;
+    return sg_check_err(s);
+}
+
+void amfrw_surrogate_destroy(amfrw_surrogate* s) { delete s; }
+
+}  // extern "C"

@@ -149,7 +149,7 @@ struct Epi {
     float* C;             // mode 0: [M x N] FP32, row stride ldc
     int ldc;
     const float* bias;    // mode 1: [N]
-    float* Z;             // mode 1: [M x N] FP32 pre-activation (row stride N)
+    float* Z;             // mode 1: [M x N] FP32 pre-activation (row stride N), may be null
     __nv_bfloat16* H;     // mode 1/2: [M x N] BF16 (row stride N)
     __nv_bfloat16* Ht;    // mode 1/2: [N x M] BF16 transpose (row stride ldt), may be null
     int ldt;
@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     epi.C[(size_t)row * epi.ldc + col] = v[i];
                 } else if (epi.mode == 1) {
                     const float z = v[i] + epi.bias[col];
-                    epi.Z[(size_t)row * N + col] = z;
+                    if (epi.Z) epi.Z[(size_t)row * N + col] = z;
                     const __nv_bfloat16 h = __float2bfloat16(gelu(z));
                     epi.H[(size_t)row * N + col] = h;
                     if (epi.Ht) epi.Ht[(size_t)col * epi.ldt + row] = h;

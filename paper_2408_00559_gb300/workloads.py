@@ -22,6 +22,9 @@ uniformly in [-0.5, 0] and redrawn until the joint correlation matrix of
   c2  N=4 standard combination n=5, swaption, T=2, 40 steps, FP64
   c3  N=6 modified combination psi=1, n=6, swaption, 40 steps, mixed
   c4  batch of N in {4,6,8}, n in {4,5,6}, standard combination, mixed
+  c5  surrogate family: N=6 standard combination n=6, 40 steps, mixed; alpha
+      shared by all rates in [0.1, 0.4], sigma in [0.1, 0.5], beta in
+      [0.25, 0.75], K in [0.02, 0.04], T in [0.5, 2], phi_i in [-0.5, 0]
 Seeds: numpy PCG64 with seed 240800559 + instance index.
 """
 from __future__ import annotations
@@ -107,7 +110,7 @@ def c4_instance(idx: int, precision: str = "mixed") -> dict:
 
 
 def batch(config: str, count: int, start: int = 0, **kw) -> list[dict]:
-    make = {"c2": c2_instance, "c3": c3_instance, "c4": c4_instance}[config]
+    make = {"c2": c2_instance, "c3": c3_instance, "c4": c4_instance, "c5": c5_instance}[config]
     return [make(start + i, **kw) for i in range(count)]
 
 
@@ -119,3 +122,26 @@ def small_instance(N: int, level: int, psi: int = 0, steps: int = 6, seed: int =
     inst.update(level=level, psi=psi, full=full, precision=precision, n_steps=steps,
                 payoff=payoff)
     return inst
+
+
+def c5_instance(idx: int, N: int = 6, level: int = 6, steps: int = 40, precision: str = "mixed") -> dict:
+    """An instance of the surrogate's family: the features (alpha shared by all
+    rates, sigma, beta, K, T, the phi_i) vary, every other field is fixed."""
+    rng = np.random.Generator(np.random.PCG64(SEED0 + 3_000_000 + idx))
+    nr = N - 1
+    rho = rate_correlation(nr)
+    alpha = float(rng.uniform(0.1, 0.4))
+    sigma = float(rng.uniform(0.1, 0.5))
+    beta = float(rng.uniform(0.25, 0.75))
+    K = float(rng.uniform(0.02, 0.04))
+    T = float(rng.uniform(0.5, 2.0))
+    while True:
+        phi = rng.uniform(-0.5, 0.0, size=nr)
+        if is_psd(rho, phi):
+            break
+    return dict(
+        N=N, payoff="swaption", alpha=np.full(nr, alpha), phi=phi, tau=np.full(nr, 0.5),
+        F0=np.full(nr, 0.03), Fmax=np.full(nr, 0.2), rho=rho, sigma=sigma, beta=beta,
+        V0=1.0, Vmax=1.0, K=K, T=T, discount=1.0, theta=THETA_W2, nu=default_nu(N),
+        n_steps=steps, level=level, psi=0, full=False, precision=precision,
+    )

@@ -1,0 +1,116 @@
+"""GPU tests of the surrogate (ensemble MLP on the tensor cores, trained on
+solver prices, solver fallback):
+
+- the loss gradient computed by the network's forward/backward kernels
+  (tcgen05 GEMMs with BF16 weights and activations, FP32 accumulation)
+  agrees with the plain FP64 CPU reference (oracle/mlp.py, itself pinned by
+  finite differences) to BF16 accuracy: every parameter tensor within 3 %
+  relative L2 error and cosine similarity > 0.999;
+- training drives the loss down; calibration and evaluation on fresh
+  instances of the family give, for every answer the network keeps, an error
+  within the bound in the calibrated fraction of cases, and answers that fall
+  back are exactly the solver's prices; queries outside the family or the
+  trained feature box always fall back;
+- save/load round-trips.
+"""
+import numpy as np
+import pytest
+
+from oracle import mlp
+from paper_2408_00559_gb300 import _lib as B
+from paper_2408_00559_gb300 import build as BLD
+from paper_2408_00559_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    BLD.build()
+    B.lib()
+
+
+def to_vector(p):
+    lay = B.surrogate_layout()
+    v = np.zeros(B.SURROGATE_PARAMS, dtype=np.float32)
+    W1 = np.zeros((256, 16))
+    W1[:, :8] = p["W1"]
+    for name, arr in (("W1", W1), ("b1", p["b1"]), ("W2", p["W2"]), ("b2", p["b2"]), ("W3", p["W3"]),
+                      ("b3", p["b3"]), ("w4", p["w4"]), ("b4", np.array([p["b4"]]))):
+        o, n = lay[name]
+        v[o:o + n] = np.asarray(arr, dtype=np.float64).reshape(-1)
+    return v
+
+
+def from_vector(g):
+    lay = B.surrogate_layout()
+    out = {}
+    for name, shape in (("W1", (256, 16)), ("b1", (256,)), ("W2", (256, 256)), ("b2", (256,)),
+                        ("W3", (256, 256)), ("b3", (256,)), ("w4", (256,)), ("b4", (1,))):
+        o, n = lay[name]
+        out[name] = g[o:o + n].astype(np.float64).reshape(shape)
+    out["W1"] = out["W1"][:, :8]
+    return out
+
+
+def test_gradients_match_cpu_oracle():
+    s = B.Surrogate(members=1, seed=1)
+    p = mlp.init_params(width=256, n_in=8, seed=5)
+    v = to_vector(p)
+    s.params(0, v)
+    back = s.params(0)
+    assert np.array_equal(back, v)
+    rng = np.random.default_rng(6)
+    x = rng.uniform(-1, 1, size=(256, 8))
+    t = rng.standard_normal(256)
+    g_gpu, loss_gpu = s.grad(0, x, t)
+    # the reference uses the FP32 parameters the GPU holds
+    p32 = from_vector(v)
+    p32["b4"] = float(p32["b4"][0])
+    L, g = mlp.loss_and_grads(p32, x, t)
+    assert abs(loss_gpu - L) <= 1e-2 * L
+    gg = from_vector(g_gpu)
+    gg["b4"] = float(gg["b4"][0])
+    for name in ("W1", "b1", "W2", "b2", "W3", "b3", "w4", "b4"):
+        a = np.ravel(gg[name])
+        b = np.ravel(g[name])
+        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+        cos = float(np.dot(a, b) / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-300))
+        assert rel < 3e-2 and cos > 0.999, (name, rel, cos)
+    s.close()
+
+
+def family(count, start):
+    return [W.c5_instance(start + i, N=4, level=3, steps=8) for i in range(count)]
+
+
+def test_train_calibrate_eval_with_fallback(tmp_path):
+    train, audit, test = family(4096, 0), family(1024, 10_000), family(2048, 20_000)
+    y_train = B.solve_batch(train)
+    y_audit = B.solve_batch(audit)
+    y_test = B.solve_batch(test)
+    s = B.Surrogate(members=4, seed=7)
+    loss = s.fit(train, y_train, epochs=40, lr=2e-3)
+    assert loss < 2e-3, loss  # normalised targets start near 0.5
+    c = s.calibrate(audit, y_audit, rel_bound=1e-3, quantile=0.99)
+    assert c > 0
+    prices, fell = s.eval(test)
+    kept = ~fell
+    rel = np.abs(prices - y_test) / np.abs(y_test)
+    assert np.array_equal(prices[fell], y_test[fell])
+    if kept.sum() > 0:
+        assert np.mean(rel[kept] <= 1e-3) >= 0.97, (np.mean(rel[kept] <= 1e-3), kept.sum())
+    # outside the family (another level) and outside the feature box (strike)
+    odd = [dict(test[0], level=4), dict(test[1], K=0.06)]
+    p_odd, f_odd = s.eval(odd)
+    assert f_odd.all()
+    assert np.allclose(p_odd, B.solve_batch(odd), rtol=0, atol=0)
+    # save / load
+    path = tmp_path / "sg.bin"
+    s.save(str(path))
+    s2 = B.Surrogate.load(str(path))
+    m1, sp1, _ = s.predict(test[:64])
+    m2, sp2, _ = s2.predict(test[:64])
+    assert np.array_equal(m1, m2) and np.array_equal(sp1, sp2)
+    print(f"surrogate: loss {loss:.2e} calib {c:.2f} kept {kept.mean():.3f} "
+          f"max rel err kept {rel[kept].max() if kept.any() else 0:.2e}")
