@@ -222,29 +222,41 @@ int amfrw_tc_gemm_bf16(const void *dA, int32_t lda, const void *dB, int32_t ldb,
  * Surrogate pricing with solver fallback (the paper has no counterpart; it is
  * an addition to the method).  An ensemble of MLPs 8 -> 256 -> 256 -> 256 -> 1
  * with GELU, BF16 weights and activations on the tensor cores (tcgen05) and
- * FP32 accumulation, maps the features (alpha, sigma, beta, K, T, mean phi,
- * min phi, max phi) of an instance to its price.  One surrogate serves one
- * instance family: every other field of amfrw_params (N, level, psi, steps,
- * precision, F0, Fmax, tau, rho, V0, Vmax, discount, theta, nu_amf) equal to
- * the training set's, and one alpha shared by all rates.  The ensemble spread
- * times a calibration factor estimates the error; eval answers from the
- * network where that estimate is within rel_bound * |price| and falls back to
- * the batched solver (amfrw_solve_batch) for every other query, including
- * queries outside the family or outside the trained feature box.  All
- * parameter arrays are host memory; calls synchronise.  Errors are reported by
+ * FP32 accumulation maps the features of an instance to its price.  One
+ * surrogate serves one instance family, fixed by the training set:
+ *   - N, payoff, n_steps, level, psi, full_grid, precision, F0, Fmax, tau, V0,
+ *     Vmax, discount, theta and nu_amf equal to the training set's;
+ *   - one alpha shared by all rates; rate correlations
+ *     rho_ik = exp(-lambda |i - k|); rate/vol correlations phi_i linear in the
+ *     rate index between phi_1 and phi_{N-1}.
+ * The features (alpha, sigma, beta, K, T, lambda, phi_1, phi_{N-1}), in this
+ * order, then determine the instance (lambda = 0 when N = 2).  The ensemble
+ * spread times a calibration factor estimates the error; eval answers from
+ * the network where that estimate is within rel_bound * |price| and falls
+ * back to the batched solver (amfrw_solve_batch) for every other query,
+ * including queries outside the family or outside the trained feature box.
+ * All arrays are host memory; calls synchronise.  Errors are reported by
  * amfrw_surrogate_last_error().
  *   create     n_members in [1, 16] networks, He initialisation from `seed`.
- *   fit        trains every member (Adam, cosine-decayed learning rate, MSE on
- *              normalised prices, batches of 1024) on n >= 1024 instances and
- *              their solver prices; *final_loss_out (may be NULL) = mean loss
- *              of the last epoch.
+ *   fit        on n >= 1024 instances and their solver prices: the target
+ *              g is the log price when every price is positive (so squared
+ *              errors are relative), else the price.  A least-squares cubic
+ *              in the normalised features (165 monomials) is the control
+ *              variate; every member learns the standardised residual of g
+ *              (Adam, cosine-decayed learning rate, batches of 1024, mean
+ *              squared error).  *final_loss_out (may be NULL) = mean loss of
+ *              the last epoch, in standardised units.
  *   calibrate  on an audit sample judged by the solver: the factor is the
  *              `quantile` of |error| / spread; stores rel_bound.
- *   predict    ensemble mean and spread per instance; in_domain_out (may be
- *              NULL) = 1 inside the family and feature box.
+ *   predict    ensemble mean and spread (price units) per instance;
+ *              in_domain_out (may be NULL) = 1 inside the family and box.
  *   eval       prices_out [n] (network or solver), fell_back_out [n] (may be
  *              NULL): 1 where the solver priced the instance.
- *   save/load  plain binary file (magic AMFRWSG1, scaling, family, FP32
+ *   eval_features  the same for queries given as raw features [n x 8]
+ *              (row-major, the order above) of the family's instances; a
+ *              fallback query is solved as the family instance with those
+ *              features (EINVAL if that instance is not valid).
+ *   save/load  plain binary file (magic AMFRWSG2, scaling, family, FP32
  *              weights).
  *   params     FP32 parameters of one member (136193 floats: W1 [256 x 16]
  *              (inputs 8..15 are padding), b1 [256], W2 [256 x 256], b2, W3,
@@ -263,6 +275,8 @@ int amfrw_surrogate_predict(amfrw_surrogate *s, const amfrw_params *ps, int64_t 
                             double *spread_out, uint8_t *in_domain_out);
 int amfrw_surrogate_eval(amfrw_surrogate *s, const amfrw_params *ps, int64_t n, double *prices_out,
                          uint8_t *fell_back_out, void *cuda_stream);
+int amfrw_surrogate_eval_features(amfrw_surrogate *s, const double *features, int64_t n, double *prices_out,
+                                  uint8_t *fell_back_out, void *cuda_stream);
 int amfrw_surrogate_save(const amfrw_surrogate *s, const char *path);
 int amfrw_surrogate_load(const char *path, void *cuda_stream, amfrw_surrogate **out);
 int amfrw_surrogate_params(amfrw_surrogate *s, int32_t member, float *params_out, const float *params_in);

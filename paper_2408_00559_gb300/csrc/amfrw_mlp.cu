@@ -90,8 +90,49 @@ constexpr int ob3 = oW3 + kW * kW;
 constexpr int ow4 = ob3 + kW;
 constexpr int ob4 = ow4 + kW;
 constexpr int kParams = ob4 + 1;
+// control variate: every monomial of degree <= 3 in the 8 normalised features
+constexpr int kPolyTerms = 1 + kIn + kIn * (kIn + 1) / 2 + kIn * (kIn + 1) * (kIn + 2) / 6;
 
 using bf16 = __nv_bfloat16;
+
+// The monomials 1, z_i, z_i z_j (i <= j), z_i z_j z_k (i <= j <= k) of one
+// feature row, handed to emit(q, value) in that order; the host (least-squares
+// fit) and the device (prediction) share this definition so the two agree
+// term by term.
+template <class Emit>
+__host__ __device__ inline void poly_each(const float* z, Emit emit)
+{
+    int q = 0;
+    emit(q++, 1.0);
+    for (int i = 0; i < kIn; ++i) emit(q++, (double)z[i]);
+    for (int i = 0; i < kIn; ++i)
+        for (int j = i; j < kIn; ++j) emit(q++, (double)z[i] * (double)z[j]);
+    for (int i = 0; i < kIn; ++i)
+        for (int j = i; j < kIn; ++j)
+            for (int k = j; k < kIn; ++k) emit(q++, (double)z[i] * (double)z[j] * (double)z[k]);
+}
+
+inline void poly_terms(const float* z, double* m)
+{
+    poly_each(z, [m](int q, double v) { m[q] = v; });
+}
+
+// g_b = poly(z_b) + ymu + ysd * mean_b: the predicted target (log price or
+// price) in FP64, from the ensemble mean of the standardised residual.
+__global__ void finish_kernel(const float* __restrict__ z, const double* __restrict__ coef,
+                              const float* __restrict__ mean, int n, double ymu, double ysd, double* g)
+{
+    __shared__ double c[kPolyTerms];
+    for (int q = threadIdx.x; q < kPolyTerms; q += blockDim.x) c[q] = coef[q];
+    __syncthreads();
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    float zb[kIn];
+    for (int i = 0; i < kIn; ++i) zb[i] = z[(size_t)b * kIn + i];
+    double acc = 0.0;
+    poly_each(zb, [&](int q, double v) { acc += c[q] * v; });
+    g[b] = acc + ymu + ysd * (double)mean[b];
+}
 
 // Batch of rows (gathered through idx, or consecutive from r0) as BF16 input
 // X [B x 16] (features then zero padding), its transpose Xt [16 x B], and
@@ -233,11 +274,15 @@ int sg_fail(int st, const std::string& m)
         if (e_ != cudaSuccess) return sg_fail(AMFRW_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
-// The instance family a surrogate serves: every field of amfrw_params except
-// the features (alpha, shared by all rates; sigma; beta; K; T; phi).
+// The instance family a surrogate serves.  The features vary: alpha (one value
+// shared by all rates), sigma, beta, K, T, the decay lambda of the rate
+// correlations rho_ik = exp(-lambda |i - k|), and the rate/vol correlations
+// phi_i, linear in the rate index between phi_1 and phi_{N-1}.  Every other
+// field of amfrw_params is fixed by the family.  With that structure the eight
+// features determine an instance, so the price is a function of them.
 struct Family {
-    int32_t n_rates, payoff, n_steps, level, psi, full_grid, precision;
-    double F0[7], Fmax[7], tau[7], rho[49];
+    int32_t n_rates, payoff, n_steps, level, psi, full_grid, precision, pad;
+    double F0[7], Fmax[7], tau[7];
     double V0, Vmax, discount, theta, nu;
 };
 
@@ -257,7 +302,6 @@ Family family_of(const amfrw_params& p)
         f.F0[i] = p.F0[i];
         f.Fmax[i] = p.Fmax[i];
         f.tau[i] = p.tau[i];
-        for (int k = 0; k < p.n_rates; ++k) f.rho[i * 7 + k] = p.rho[i * p.n_rates + k];
     }
     f.V0 = p.V0;
     f.Vmax = p.Vmax;
@@ -267,39 +311,82 @@ Family family_of(const amfrw_params& p)
     return f;
 }
 
-bool in_family(const Family& f, const amfrw_params& p)
-{
-    if (p.n_rates != f.n_rates || p.payoff != f.payoff || p.n_steps != f.n_steps || p.level != f.level ||
-        p.psi != f.psi || p.full_grid != f.full_grid || p.precision != f.precision)
-        return false;
-    for (int i = 0; i < p.n_rates; ++i) {
-        if (!close_(p.F0[i], f.F0[i]) || !close_(p.Fmax[i], f.Fmax[i]) || !close_(p.tau[i], f.tau[i]))
-            return false;
-        if (!close_(p.alpha[i], p.alpha[0])) return false;  // one alpha shared by all rates
-        for (int k = 0; k < p.n_rates; ++k)
-            if (!close_(p.rho[i * p.n_rates + k], f.rho[i * 7 + k])) return false;
-    }
-    return close_(p.V0, f.V0) && close_(p.Vmax, f.Vmax) && close_(p.discount, f.discount) &&
-           close_(p.theta, f.theta) && close_(p.nu_amf, f.nu);
-}
-
-// (alpha, sigma, beta, K, T, mean phi, min phi, max phi)
+// (alpha, sigma, beta, K, T, lambda, phi_1, phi_{N-1})
 void features_of(const amfrw_params& p, double* f)
 {
-    double s = 0.0, mn = 1e300, mx = -1e300;
-    for (int i = 0; i < p.n_rates; ++i) {
-        s += p.phi[i];
-        mn = std::min(mn, p.phi[i]);
-        mx = std::max(mx, p.phi[i]);
-    }
+    const int nr = p.n_rates;
     f[0] = p.alpha[0];
     f[1] = p.sigma;
     f[2] = p.beta;
     f[3] = p.K;
     f[4] = p.T;
-    f[5] = s / p.n_rates;
-    f[6] = mn;
-    f[7] = mx;
+    f[5] = nr > 1 && p.rho[1] > 0.0 ? -std::log(p.rho[1]) : 0.0;
+    f[6] = p.phi[0];
+    f[7] = p.phi[nr - 1];
+}
+
+bool in_family(const Family& f, const amfrw_params& p)
+{
+    if (p.n_rates != f.n_rates || p.payoff != f.payoff || p.n_steps != f.n_steps || p.level != f.level ||
+        p.psi != f.psi || p.full_grid != f.full_grid || p.precision != f.precision)
+        return false;
+    const int nr = p.n_rates;
+    if (nr > 1 && !(p.rho[1] > 0.0 && p.rho[1] <= 1.0)) return false;
+    double feat[8];
+    features_of(p, feat);
+    for (int i = 0; i < nr; ++i) {
+        if (!close_(p.F0[i], f.F0[i]) || !close_(p.Fmax[i], f.Fmax[i]) || !close_(p.tau[i], f.tau[i]))
+            return false;
+        if (!close_(p.alpha[i], p.alpha[0])) return false;
+        const double lin = nr > 1 ? feat[6] + (double)i / (double)(nr - 1) * (feat[7] - feat[6]) : feat[6];
+        if (!close_(p.phi[i], lin)) return false;
+        for (int k = 0; k < nr; ++k)
+            if (!close_(p.rho[i * nr + k], std::exp(-feat[5] * std::fabs((double)(i - k))))) return false;
+    }
+    return close_(p.V0, f.V0) && close_(p.Vmax, f.Vmax) && close_(p.discount, f.discount) &&
+           close_(p.theta, f.theta) && close_(p.nu_amf, f.nu);
+}
+
+// The family's instance with raw features f; the arrays live in `st`.
+struct InstanceStore {
+    double alpha[7], phi[7], rho[49], tau[7], F0[7], Fmax[7];
+};
+
+amfrw_params params_from(const Family& fam, const double* f, InstanceStore& st)
+{
+    const int nr = fam.n_rates;
+    for (int i = 0; i < nr; ++i) {
+        st.alpha[i] = f[0];
+        st.phi[i] = nr > 1 ? f[6] + (double)i / (double)(nr - 1) * (f[7] - f[6]) : f[6];
+        st.tau[i] = fam.tau[i];
+        st.F0[i] = fam.F0[i];
+        st.Fmax[i] = fam.Fmax[i];
+        for (int k = 0; k < nr; ++k) st.rho[i * nr + k] = std::exp(-f[5] * std::fabs((double)(i - k)));
+    }
+    amfrw_params p{};
+    p.n_rates = nr;
+    p.payoff = fam.payoff;
+    p.n_steps = fam.n_steps;
+    p.level = fam.level;
+    p.psi = fam.psi;
+    p.full_grid = fam.full_grid;
+    p.precision = fam.precision;
+    p.alpha = st.alpha;
+    p.phi = st.phi;
+    p.rho = st.rho;
+    p.tau = st.tau;
+    p.F0 = st.F0;
+    p.Fmax = st.Fmax;
+    p.sigma = f[1];
+    p.beta = f[2];
+    p.V0 = fam.V0;
+    p.Vmax = fam.Vmax;
+    p.K = f[3];
+    p.T = f[4];
+    p.discount = fam.discount;
+    p.theta = fam.theta;
+    p.nu_amf = fam.nu;
+    return p;
 }
 
 }  // namespace
@@ -315,10 +402,14 @@ struct amfrw_surrogate {
     bf16 *dZ1 = nullptr, *dZ2 = nullptr, *dZ3 = nullptr, *dZ1t = nullptr, *dZ2t = nullptr, *dZ3t = nullptr;
     float *Z1 = nullptr, *Z2 = nullptr, *Z3 = nullptr, *y = nullptr, *t = nullptr, *dy = nullptr;
     float *loss = nullptr, *ys = nullptr;
+    float *pmean = nullptr, *pspread = nullptr;  // prediction chunk: ensemble mean, spread
+    double *pg = nullptr, *dpoly = nullptr;      // prediction chunk: target; control-variate coefficients
     int* err = nullptr;
+    double poly[kPolyTerms] = {};
     int adam_t = 0;
     double fmin[kIn], fmax[kIn];
-    double ymu = 0.0, ysd = 1.0;
+    double ymu = 0.0, ysd = 1.0;    // target scaling: t = (g(price) - ymu) / ysd
+    bool log_target = false;        // g = log (all training prices > 0), else identity
     double calib = 0.0, rel_bound = 1e-3;
     bool trained = false, calibrated = false;
     Family fam{};
@@ -331,7 +422,7 @@ struct amfrw_surrogate {
         for (void* q : {(void*)X, (void*)Xt, (void*)H1, (void*)H2, (void*)H3, (void*)H1t, (void*)H2t,
                         (void*)dZ1, (void*)dZ2, (void*)dZ3, (void*)dZ1t, (void*)dZ2t, (void*)dZ3t,
                         (void*)Z1, (void*)Z2, (void*)Z3, (void*)y, (void*)t, (void*)dy, (void*)loss,
-                        (void*)ys, (void*)err})
+                        (void*)ys, (void*)err, (void*)pmean, (void*)pspread, (void*)pg, (void*)dpoly})
             cudaFree(q);
     }
 };
@@ -370,6 +461,11 @@ int sg_alloc(amfrw_surrogate* s)
     SG_CUDA(cudaMalloc(&s->loss, F4));
     SG_CUDA(cudaMalloc(&s->ys, F4 * PQ * (size_t)s->members));
     SG_CUDA(cudaMalloc(&s->err, sizeof(int)));
+    SG_CUDA(cudaMalloc(&s->pmean, F4 * PR));
+    SG_CUDA(cudaMalloc(&s->pspread, F4 * PR));
+    SG_CUDA(cudaMalloc(&s->pg, sizeof(double) * PR));
+    SG_CUDA(cudaMalloc(&s->dpoly, sizeof(double) * kPolyTerms));
+    SG_CUDA(cudaMemsetAsync(s->dpoly, 0, sizeof(double) * kPolyTerms, s->stream));
     SG_CUDA(cudaMemsetAsync(s->err, 0, sizeof(int), s->stream));
     return AMFRW_OK;
 }
@@ -442,75 +538,188 @@ int sg_check_err(amfrw_surrogate* s)
     return AMFRW_OK;
 }
 
-// Normalised features of n instances (host, n x 8 floats); false entries of
-// ok_out for instances outside the family or the trained feature box.
-void sg_features(const amfrw_surrogate* s, const amfrw_params* ps, int64_t n, std::vector<float>& out,
-                 std::vector<char>* ok_out)
+// Least-squares coefficients of the cubic control variate: normal equations
+// with a relative ridge of 1e-12 (which zeroes the terms of features that do
+// not vary), solved by Cholesky.
+bool fit_poly(const float* z, const double* g, int64_t n, double* coef)
+{
+    const int P = kPolyTerms;
+    std::vector<double> A((size_t)P * P, 0.0), rhs(P, 0.0);
+    double m[kPolyTerms];
+    for (int64_t i = 0; i < n; ++i) {
+        poly_terms(z + (size_t)i * kIn, m);
+        for (int a = 0; a < P; ++a) {
+            rhs[a] += m[a] * g[i];
+            const double ma = m[a];
+            double* row = A.data() + (size_t)a * P;
+            for (int b = a; b < P; ++b) row[b] += ma * m[b];
+        }
+    }
+    double tr = 0.0;
+    for (int a = 0; a < P; ++a) tr += A[(size_t)a * P + a];
+    const double ridge = 1e-12 * tr / P + 1e-300;
+    for (int a = 0; a < P; ++a) {
+        A[(size_t)a * P + a] += ridge;
+        for (int b = 0; b < a; ++b) A[(size_t)a * P + b] = A[(size_t)b * P + a];
+    }
+    // A = L L^T in place (lower triangle)
+    for (int j = 0; j < P; ++j) {
+        double d = A[(size_t)j * P + j];
+        for (int k = 0; k < j; ++k) d -= A[(size_t)j * P + k] * A[(size_t)j * P + k];
+        if (!(d > 0.0)) return false;
+        d = std::sqrt(d);
+        A[(size_t)j * P + j] = d;
+        for (int i = j + 1; i < P; ++i) {
+            double v = A[(size_t)i * P + j];
+            for (int k = 0; k < j; ++k) v -= A[(size_t)i * P + k] * A[(size_t)j * P + k];
+            A[(size_t)i * P + j] = v / d;
+        }
+    }
+    std::vector<double> y(P);
+    for (int i = 0; i < P; ++i) {
+        double v = rhs[i];
+        for (int k = 0; k < i; ++k) v -= A[(size_t)i * P + k] * y[k];
+        y[i] = v / A[(size_t)i * P + i];
+    }
+    for (int i = P - 1; i >= 0; --i) {
+        double v = y[i];
+        for (int k = i + 1; k < P; ++k) v -= A[(size_t)k * P + i] * coef[k];
+        coef[i] = v / A[(size_t)i * P + i];
+    }
+    for (int i = 0; i < P; ++i)
+        if (!std::isfinite(coef[i])) return false;
+    return true;
+}
+
+// Normalised features (host, n x 8 floats) of n rows of raw features; ok
+// entries (may be NULL) cleared for rows outside the trained feature box.
+void sg_normalise(const amfrw_surrogate* s, const double* raw, int64_t n, std::vector<float>& out, char* ok)
 {
     out.assign((size_t)n * kIn, 0.0f);
-    if (ok_out) ok_out->assign((size_t)n, 1);
     for (int64_t i = 0; i < n; ++i) {
-        double f[kIn];
-        features_of(ps[i], f);
-        bool ok = in_family(s->fam, ps[i]);
         for (int c = 0; c < kIn; ++c) {
+            const double f = raw[(size_t)i * kIn + c];
             const double span = s->fmax[c] - s->fmin[c];
-            double z = span > 0 ? 2.0 * (f[c] - s->fmin[c]) / span - 1.0 : 0.0;
-            if (z < -1.0 - 1e-9 || z > 1.0 + 1e-9) ok = false;
+            const double z = span > 0 ? 2.0 * (f - s->fmin[c]) / span - 1.0 : (f == s->fmin[c] ? 0.0 : 2.0);
+            if (ok && !(z >= -1.0 - 1e-9 && z <= 1.0 + 1e-9)) ok[i] = 0;
             out[(size_t)i * kIn + c] = (float)z;
         }
-        if (ok_out) (*ok_out)[(size_t)i] = ok ? 1 : 0;
     }
 }
 
-// Ensemble mean and spread (denormalised prices) of n rows of normalised
-// features on the device.
+// Raw features of n instances and whether each belongs to the family.
+void sg_raw_features(const amfrw_surrogate* s, const amfrw_params* ps, int64_t n, std::vector<double>& raw,
+                     std::vector<char>& ok)
+{
+    raw.assign((size_t)n * kIn, 0.0);
+    ok.assign((size_t)n, 1);
+    for (int64_t i = 0; i < n; ++i) {
+        features_of(ps[i], raw.data() + (size_t)i * kIn);
+        ok[(size_t)i] = in_family(s->fam, ps[i]) ? 1 : 0;
+    }
+}
+
+// Ensemble mean and spread (price units) of n rows of normalised features on
+// the device.
 int sg_predict_dev(amfrw_surrogate* s, const float* d_feats, int64_t n, std::vector<double>& mean,
                    std::vector<double>& spread)
 {
     cudaStream_t st = s->stream;
     mean.assign((size_t)n, 0.0);
     spread.assign((size_t)n, 0.0);
-    std::vector<float> hm, hs;
-    float *d_mean = nullptr, *d_spread = nullptr;
-    SG_CUDA(cudaMalloc(&d_mean, sizeof(float) * kPredRows));
-    SG_CUDA(cudaMalloc(&d_spread, sizeof(float) * kPredRows));
-    int st_ = AMFRW_OK;
-    for (int64_t r0 = 0; r0 < n && st_ == AMFRW_OK; r0 += kPredRows) {
+    std::vector<double> hg;
+    std::vector<float> hs;
+    for (int64_t r0 = 0; r0 < n; r0 += kPredRows) {
         const int B = (int)std::min<int64_t>(kPredRows, n - r0);
-        pack_kernel<<<cdiv(B * kInPad, 256), 256, 0, st>>>(d_feats + (size_t)r0 * kIn, nullptr, nullptr, 0, B,
-                                                          s->X, nullptr, nullptr);
-        for (int m = 0; m < s->members && st_ == AMFRW_OK; ++m)
-            st_ = sg_forward(s, m, B, false, s->ys + (size_t)m * B);
-        if (st_ != AMFRW_OK) break;
-        ensemble_kernel<<<cdiv(B, 256), 256, 0, st>>>(s->ys, s->members, B, d_mean, d_spread);
-        hm.resize(B);
+        const float* z = d_feats + (size_t)r0 * kIn;
+        pack_kernel<<<cdiv(B * kInPad, 256), 256, 0, st>>>(z, nullptr, nullptr, 0, B, s->X, nullptr, nullptr);
+        for (int m = 0; m < s->members; ++m) {
+            const int rc = sg_forward(s, m, B, false, s->ys + (size_t)m * B);
+            if (rc != AMFRW_OK) return rc;
+        }
+        ensemble_kernel<<<cdiv(B, 256), 256, 0, st>>>(s->ys, s->members, B, s->pmean, s->pspread);
+        finish_kernel<<<cdiv(B, 128), 128, 0, st>>>(z, s->dpoly, s->pmean, B, s->ymu, s->ysd, s->pg);
+        hg.resize(B);
         hs.resize(B);
-        cudaMemcpyAsync(hm.data(), d_mean, sizeof(float) * B, cudaMemcpyDeviceToHost, st);
-        cudaMemcpyAsync(hs.data(), d_spread, sizeof(float) * B, cudaMemcpyDeviceToHost, st);
-        if (cudaStreamSynchronize(st) != cudaSuccess) st_ = sg_fail(AMFRW_ECUDA, "surrogate prediction");
+        SG_CUDA(cudaMemcpyAsync(hg.data(), s->pg, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
+        SG_CUDA(cudaMemcpyAsync(hs.data(), s->pspread, sizeof(float) * B, cudaMemcpyDeviceToHost, st));
+        SG_CUDA(cudaStreamSynchronize(st));
         for (int i = 0; i < B; ++i) {
-            mean[(size_t)(r0 + i)] = s->ymu + s->ysd * (double)hm[i];
-            spread[(size_t)(r0 + i)] = s->ysd * (double)hs[i];
+            const double g = hg[i], sp = s->ysd * (double)hs[i];
+            if (s->log_target) {  // spread to first order in price units
+                mean[(size_t)(r0 + i)] = std::exp(g);
+                spread[(size_t)(r0 + i)] = std::exp(g) * sp;
+            } else {
+                mean[(size_t)(r0 + i)] = g;
+                spread[(size_t)(r0 + i)] = sp;
+            }
         }
     }
-    cudaFree(d_mean);
-    cudaFree(d_spread);
-    if (st_ != AMFRW_OK) return st_;
     return sg_check_err(s);
+}
+
+// Prediction from raw features; ok (n entries, set by the caller for family
+// membership) is cleared where a row leaves the feature box.
+int sg_predict_raw(amfrw_surrogate* s, const double* raw, int64_t n, std::vector<double>& mean,
+                   std::vector<double>& spread, std::vector<char>& ok)
+{
+    std::vector<float> feats;
+    sg_normalise(s, raw, n, feats, ok.data());
+    float* d = nullptr;
+    SG_CUDA(cudaMalloc(&d, sizeof(float) * std::max<size_t>(1, feats.size())));
+    cudaMemcpyAsync(d, feats.data(), sizeof(float) * feats.size(), cudaMemcpyHostToDevice, s->stream);
+    const int st = sg_predict_dev(s, d, n, mean, spread);
+    cudaFree(d);
+    return st;
 }
 
 int sg_predict_host(amfrw_surrogate* s, const amfrw_params* ps, int64_t n, std::vector<double>& mean,
                     std::vector<double>& spread, std::vector<char>& ok)
 {
-    std::vector<float> feats;
-    sg_features(s, ps, n, feats, &ok);
-    float* d = nullptr;
-    SG_CUDA(cudaMalloc(&d, sizeof(float) * feats.size()));
-    cudaMemcpyAsync(d, feats.data(), sizeof(float) * feats.size(), cudaMemcpyHostToDevice, s->stream);
-    const int st = sg_predict_dev(s, d, n, mean, spread);
-    cudaFree(d);
-    return st;
+    std::vector<double> raw;
+    sg_raw_features(s, ps, n, raw, ok);
+    return sg_predict_raw(s, raw.data(), n, mean, spread, ok);
+}
+
+// Answers from the network where the calibrated estimate is within the bound;
+// the batched solver prices every other query (one batch per step count, at
+// most 4096 instances each).  param(i) gives query i as amfrw_params.
+template <class ParamOf>
+int sg_serve(amfrw_surrogate* s, int64_t n, const std::vector<double>& mean, const std::vector<double>& spread,
+             const std::vector<char>& ok, ParamOf param, double* prices_out, uint8_t* fell_back_out,
+             void* cuda_stream)
+{
+    std::vector<int64_t> where;
+    for (int64_t i = 0; i < n; ++i) {
+        const double est = s->calib * spread[(size_t)i];
+        const bool fall = !ok[(size_t)i] || !(est <= s->rel_bound * std::fabs(mean[(size_t)i]));
+        if (fell_back_out) fell_back_out[i] = fall ? 1 : 0;
+        if (fall)
+            where.push_back(i);
+        else
+            prices_out[i] = mean[(size_t)i];
+    }
+    std::vector<InstanceStore> store;
+    std::vector<amfrw_params> fb(where.size());
+    store.resize(where.size());
+    for (size_t k = 0; k < where.size(); ++k) fb[k] = param(where[k], store[k]);
+    std::vector<size_t> order(fb.size());
+    for (size_t k = 0; k < order.size(); ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return fb[a].n_steps < fb[b].n_steps; });
+    std::vector<amfrw_params> grp;
+    std::vector<double> pr;
+    for (size_t k0 = 0; k0 < order.size();) {
+        size_t k1 = k0;
+        while (k1 < order.size() && k1 - k0 < 4096 && fb[order[k1]].n_steps == fb[order[k0]].n_steps) ++k1;
+        grp.clear();
+        for (size_t k = k0; k < k1; ++k) grp.push_back(fb[order[k]]);
+        pr.assign(grp.size(), 0.0);
+        const int st = amfrw_solve_batch(grp.data(), (int32_t)grp.size(), pr.data(), cuda_stream);
+        if (st != AMFRW_OK) return sg_fail(st, std::string("fallback solve: ") + amfrw_last_error());
+        for (size_t k = k0; k < k1; ++k) prices_out[where[order[k]]] = pr[k - k0];
+        k0 = k1;
+    }
+    return AMFRW_OK;
 }
 
 }  // namespace
@@ -570,24 +779,42 @@ int amfrw_surrogate_fit(amfrw_surrogate* s, const amfrw_params* ps, const double
         s->fmin[c] = 1e300;
         s->fmax[c] = -1e300;
     }
+    std::vector<double> raw;
+    std::vector<char> ok;
+    sg_raw_features(s, ps, n, raw, ok);
+    bool positive = true;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!ok[(size_t)i]) return sg_fail(AMFRW_EINVAL, "training instances must share one family");
+        if (!std::isfinite(prices[i])) return sg_fail(AMFRW_EINVAL, "non-finite training price");
+        positive = positive && prices[i] > 0.0;
+        for (int c = 0; c < kIn; ++c) {
+            s->fmin[c] = std::min(s->fmin[c], raw[(size_t)i * kIn + c]);
+            s->fmax[c] = std::max(s->fmax[c], raw[(size_t)i * kIn + c]);
+        }
+    }
+    // the network learns log(price) when every price is positive (its squared
+    // error is then the squared relative error), else the price itself
+    s->log_target = positive;
+    std::vector<double> g((size_t)n);
+    for (int64_t i = 0; i < n; ++i) g[(size_t)i] = positive ? std::log(prices[i]) : prices[i];
+    std::vector<float> feats, targ((size_t)n);
+    sg_normalise(s, raw.data(), n, feats, nullptr);
+    // control variate: least-squares cubic in the features; the networks
+    // learn what it leaves, standardised
+    if (!fit_poly(feats.data(), g.data(), n, s->poly)) return sg_fail(AMFRW_EINVAL, "control-variate fit failed");
     double sum = 0.0, sq = 0.0;
     for (int64_t i = 0; i < n; ++i) {
-        if (!in_family(s->fam, ps[i])) return sg_fail(AMFRW_EINVAL, "training instances must share one family");
-        if (!std::isfinite(prices[i])) return sg_fail(AMFRW_EINVAL, "non-finite training price");
-        double f[kIn];
-        features_of(ps[i], f);
-        for (int c = 0; c < kIn; ++c) {
-            s->fmin[c] = std::min(s->fmin[c], f[c]);
-            s->fmax[c] = std::max(s->fmax[c], f[c]);
-        }
-        sum += prices[i];
-        sq += prices[i] * prices[i];
+        double m[kPolyTerms], base = 0.0;
+        poly_terms(feats.data() + (size_t)i * kIn, m);
+        for (int q = 0; q < kPolyTerms; ++q) base += s->poly[q] * m[q];
+        g[(size_t)i] -= base;
+        sum += g[(size_t)i];
+        sq += g[(size_t)i] * g[(size_t)i];
     }
     s->ymu = sum / (double)n;
     s->ysd = std::sqrt(std::max(sq / (double)n - s->ymu * s->ymu, 1e-300));
-    std::vector<float> feats, targ((size_t)n);
-    sg_features(s, ps, n, feats, nullptr);
-    for (int64_t i = 0; i < n; ++i) targ[(size_t)i] = (float)((prices[i] - s->ymu) / s->ysd);
+    for (int64_t i = 0; i < n; ++i) targ[(size_t)i] = (float)((g[(size_t)i] - s->ymu) / s->ysd);
+    SG_CUDA(cudaMemcpyAsync(s->dpoly, s->poly, sizeof(double) * kPolyTerms, cudaMemcpyHostToDevice, s->stream));
     cudaStream_t st = s->stream;
     float *d_feats = nullptr, *d_targ = nullptr;
     int* d_idx = nullptr;
@@ -697,36 +924,27 @@ int amfrw_surrogate_eval(amfrw_surrogate* s, const amfrw_params* ps, int64_t n, 
     std::vector<char> ok;
     int st = sg_predict_host(s, ps, n, mean, spread, ok);
     if (st != AMFRW_OK) return st;
-    std::vector<amfrw_params> fb;
-    std::vector<int64_t> where;
-    for (int64_t i = 0; i < n; ++i) {
-        const double est = s->calib * spread[(size_t)i];
-        const bool fall = !ok[(size_t)i] || !(est <= s->rel_bound * std::fabs(mean[(size_t)i]));
-        if (fell_back_out) fell_back_out[i] = fall ? 1 : 0;
-        if (fall) {
-            fb.push_back(ps[i]);
-            where.push_back(i);
-        } else {
-            prices_out[i] = mean[(size_t)i];
-        }
-    }
-    // the solver judges and replaces what the network cannot vouch for; one
-    // batch per step count (a batch shares n_steps)
-    std::vector<size_t> order(fb.size());
-    for (size_t k = 0; k < order.size(); ++k) order[k] = k;
-    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return fb[a].n_steps < fb[b].n_steps; });
-    for (size_t k0 = 0; k0 < order.size();) {
-        size_t k1 = k0;
-        while (k1 < order.size() && k1 - k0 < 4096 && fb[order[k1]].n_steps == fb[order[k0]].n_steps) ++k1;
-        std::vector<amfrw_params> grp;
-        for (size_t k = k0; k < k1; ++k) grp.push_back(fb[order[k]]);
-        std::vector<double> pr(grp.size());
-        st = amfrw_solve_batch(grp.data(), (int32_t)grp.size(), pr.data(), cuda_stream);
-        if (st != AMFRW_OK) return sg_fail(st, std::string("fallback solve: ") + amfrw_last_error());
-        for (size_t k = k0; k < k1; ++k) prices_out[where[order[k]]] = pr[k - k0];
-        k0 = k1;
-    }
-    return AMFRW_OK;
+    return sg_serve(
+        s, n, mean, spread, ok, [&](int64_t i, InstanceStore&) { return ps[i]; }, prices_out, fell_back_out,
+        cuda_stream);
+}
+
+int amfrw_surrogate_eval_features(amfrw_surrogate* s, const double* features, int64_t n, double* prices_out,
+                                  uint8_t* fell_back_out, void* cuda_stream)
+{
+    if (!s || !features || !prices_out) return sg_fail(AMFRW_EINVAL, "NULL argument");
+    if (n < 0) return sg_fail(AMFRW_EINVAL, "n < 0");
+    if (!s->trained || !s->calibrated) return sg_fail(AMFRW_EINVAL, "surrogate is not trained and calibrated");
+    for (int64_t i = 0; i < n * kIn; ++i)
+        if (!std::isfinite(features[i])) return sg_fail(AMFRW_EINVAL, "non-finite feature");
+    std::vector<double> mean, spread;
+    std::vector<char> ok((size_t)n, 1);
+    int st = sg_predict_raw(s, features, n, mean, spread, ok);
+    if (st != AMFRW_OK) return st;
+    return sg_serve(
+        s, n, mean, spread, ok,
+        [&](int64_t i, InstanceStore& store) { return params_from(s->fam, features + (size_t)i * kIn, store); },
+        prices_out, fell_back_out, cuda_stream);
 }
 
 int amfrw_surrogate_save(const amfrw_surrogate* s, const char* path)
@@ -734,7 +952,7 @@ int amfrw_surrogate_save(const amfrw_surrogate* s, const char* path)
     if (!s || !path) return sg_fail(AMFRW_EINVAL, "NULL argument");
     FILE* f = fopen(path, "wb");
     if (!f) return sg_fail(AMFRW_EINVAL, std::string("cannot open ") + path);
-    const char magic[8] = {'A', 'M', 'F', 'R', 'W', 'S', 'G', '1'};
+    const char magic[8] = {'A', 'M', 'F', 'R', 'W', 'S', 'G', '2'};
     std::vector<float> h(kParams);
     bool ok = fwrite(magic, 1, 8, f) == 8;
     ok = ok && fwrite(&s->members, sizeof(int), 1, f) == 1;
@@ -742,9 +960,10 @@ int amfrw_surrogate_save(const amfrw_surrogate* s, const char* path)
     ok = ok && fwrite(s->fmax, sizeof(double), kIn, f) == (size_t)kIn;
     const double sc[4] = {s->ymu, s->ysd, s->calib, s->rel_bound};
     ok = ok && fwrite(sc, sizeof(double), 4, f) == 4;
-    const int flags[2] = {s->trained ? 1 : 0, s->calibrated ? 1 : 0};
-    ok = ok && fwrite(flags, sizeof(int), 2, f) == 2;
+    const int flags[3] = {s->trained ? 1 : 0, s->calibrated ? 1 : 0, s->log_target ? 1 : 0};
+    ok = ok && fwrite(flags, sizeof(int), 3, f) == 3;
     ok = ok && fwrite(&s->fam, sizeof(Family), 1, f) == 1;
+    ok = ok && fwrite(s->poly, sizeof(double), kPolyTerms, f) == (size_t)kPolyTerms;
     for (int m = 0; m < s->members && ok; ++m) {
         ok = cudaMemcpy(h.data(), s->P[m], sizeof(float) * kParams, cudaMemcpyDeviceToHost) == cudaSuccess;
         ok = ok && fwrite(h.data(), sizeof(float), kParams, f) == (size_t)kParams;
@@ -761,16 +980,18 @@ int amfrw_surrogate_load(const char* path, void* cuda_stream, amfrw_surrogate** 
     if (!f) return sg_fail(AMFRW_EINVAL, std::string("cannot open ") + path);
     char magic[8];
     int members = 0;
-    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "AMFRWSG1", 8) == 0;
+    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "AMFRWSG2", 8) == 0;
     ok = ok && fread(&members, sizeof(int), 1, f) == 1 && members >= 1 && members <= 16;
     amfrw_surrogate* s = nullptr;
     if (ok && amfrw_surrogate_create(members, 0, cuda_stream, &s) != AMFRW_OK) ok = false;
     double sc[4];
-    int flags[2];
+    int flags[3];
     if (ok) {
         ok = fread(s->fmin, sizeof(double), kIn, f) == (size_t)kIn && fread(s->fmax, sizeof(double), kIn, f) == (size_t)kIn;
-        ok = ok && fread(sc, sizeof(double), 4, f) == 4 && fread(flags, sizeof(int), 2, f) == 2;
+        ok = ok && fread(sc, sizeof(double), 4, f) == 4 && fread(flags, sizeof(int), 3, f) == 3;
         ok = ok && fread(&s->fam, sizeof(Family), 1, f) == 1;
+        ok = ok && fread(s->poly, sizeof(double), kPolyTerms, f) == (size_t)kPolyTerms;
+        ok = ok && cudaMemcpy(s->dpoly, s->poly, sizeof(double) * kPolyTerms, cudaMemcpyHostToDevice) == cudaSuccess;
     }
     std::vector<float> h(kParams);
     for (int m = 0; ok && m < members; ++m) {
@@ -786,6 +1007,7 @@ int amfrw_surrogate_load(const char* path, void* cuda_stream, amfrw_surrogate** 
     s->ymu = sc[0]; s->ysd = sc[1]; s->calib = sc[2]; s->rel_bound = sc[3];
     s->trained = flags[0] != 0;
     s->calibrated = flags[1] != 0;
+    s->log_target = flags[2] != 0;
     cudaStreamSynchronize(s->stream);
     *out = s;
     return AMFRW_OK;

@@ -6,11 +6,14 @@ solver prices, solver fallback):
   agrees with the plain FP64 CPU reference (oracle/mlp.py, itself pinned by
   finite differences) to BF16 accuracy: every parameter tensor within 3 %
   relative L2 error and cosine similarity > 0.999;
-- training drives the loss down; calibration and evaluation on fresh
+- training (cubic control variate plus networks on the residual of the log
+  price) drives the loss down; calibration and evaluation on fresh
   instances of the family give, for every answer the network keeps, an error
   within the bound in the calibrated fraction of cases, and answers that fall
   back are exactly the solver's prices; queries outside the family or the
   trained feature box always fall back;
+- the same queries given as raw features get identical answers, faster than
+  the solver alone prices them (the gain the network brings);
 - save/load round-trips.
 """
 import numpy as np
@@ -80,28 +83,45 @@ def test_gradients_match_cpu_oracle():
     s.close()
 
 
+FAMILY = dict(N=4, level=5, steps=8)
+
+
 def family(count, start):
-    return [W.c5_instance(start + i, N=4, level=3, steps=8) for i in range(count)]
+    F = W.c5_features(count, start, N=FAMILY["N"])
+    return F, [W.c5_instance_from(f, **FAMILY) for f in F]
 
 
 def test_train_calibrate_eval_with_fallback(tmp_path):
-    train, audit, test = family(4096, 0), family(1024, 10_000), family(2048, 20_000)
+    import time
+    import torch
+    (_, train), (_, audit), (F_test, test) = family(32768, 0), family(4096, 10_000), family(8192, 20_000)
     y_train = B.solve_batch(train)
     y_audit = B.solve_batch(audit)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     y_test = B.solve_batch(test)
+    t_solver = time.perf_counter() - t0
+    assert (y_train > 0).all()
     s = B.Surrogate(members=4, seed=7)
-    loss = s.fit(train, y_train, epochs=40, lr=2e-3)
-    assert loss < 2e-3, loss  # normalised targets start near 0.5
+    loss = s.fit(train, y_train, epochs=300, lr=3e-3)
+    assert loss < 1e-3, loss  # standardised residual targets start near 0.5
     c = s.calibrate(audit, y_audit, rel_bound=1e-3, quantile=0.99)
     assert c > 0
     prices, fell = s.eval(test)
     kept = ~fell
     rel = np.abs(prices - y_test) / np.abs(y_test)
     assert np.array_equal(prices[fell], y_test[fell])
-    if kept.sum() > 0:
-        assert np.mean(rel[kept] <= 1e-3) >= 0.97, (np.mean(rel[kept] <= 1e-3), kept.sum())
+    assert kept.mean() >= 0.5, kept.mean()
+    assert np.mean(rel[kept] <= 1e-3) >= 0.98, np.mean(rel[kept] <= 1e-3)
+    # the same queries as raw features: identical answers, and the gain over
+    # the solver alone
+    t0 = time.perf_counter()
+    p_f, fell_f = s.eval_features(F_test)
+    t_sur = time.perf_counter() - t0
+    assert np.array_equal(p_f, prices) and np.array_equal(fell_f, fell)
+    assert t_sur < t_solver, (t_sur, t_solver)
     # outside the family (another level) and outside the feature box (strike)
-    odd = [dict(test[0], level=4), dict(test[1], K=0.06)]
+    odd = [dict(test[0], level=4), dict(test[1], K=0.031)]
     p_odd, f_odd = s.eval(odd)
     assert f_odd.all()
     assert np.allclose(p_odd, B.solve_batch(odd), rtol=0, atol=0)
@@ -113,4 +133,6 @@ def test_train_calibrate_eval_with_fallback(tmp_path):
     m2, sp2, _ = s2.predict(test[:64])
     assert np.array_equal(m1, m2) and np.array_equal(sp1, sp2)
     print(f"surrogate: loss {loss:.2e} calib {c:.2f} kept {kept.mean():.3f} "
-          f"max rel err kept {rel[kept].max() if kept.any() else 0:.2e}")
+          f"kept within 1e-3 {np.mean(rel[kept] <= 1e-3):.4f} max rel err kept {rel[kept].max():.2e} "
+          f"median {np.median(rel[kept]):.2e}; {len(test)} queries: solver {t_solver:.3f} s, "
+          f"surrogate+fallback {t_sur:.3f} s ({t_solver / t_sur:.1f}x)")
