@@ -33,7 +33,7 @@ class OrcParams(C.Structure):
         ("N", C.c_int32),
         ("payoff", C.c_int32),
         ("n_steps", C.c_int32),
-        ("pad_", C.c_int32),
+        ("bc", C.c_int32),
         ("alpha", C.c_double * MAXD),
         ("phi", C.c_double * MAXD),
         ("tau", C.c_double * MAXD),
@@ -80,6 +80,8 @@ def lib():
         L.orc_apply_Fi.argtypes = [pp, ip, C.c_int32, dp, dp]
         L.orc_line_solve.argtypes = [pp, ip, C.c_int32, C.c_double, dp, dp]
         L.orc_run.argtypes = [pp, ip, dp, C.c_int32]
+        L.orc_run_theta_gs.restype = C.c_int32
+        L.orc_run_theta_gs.argtypes = [pp, ip, dp, C.c_int32, C.c_int32]
         L.orc_interp.restype = C.c_double
         L.orc_interp.argtypes = [pp, ip, dp, dp]
         L.orc_solve_grid.restype = C.c_double
@@ -104,7 +106,8 @@ def make_params(inst: dict) -> OrcParams:
     """Fill the oracle's parameter struct from a plain instance dict.
 
     Keys: N, payoff ('caplet'|'swaption'), n_steps, alpha, phi, tau, F0, Fmax,
-    Vmax, rho (n_rates x n_rates), sigma, beta, V0, K, T, theta, nu, discount.
+    Vmax, rho (n_rates x n_rates), sigma, beta, V0, K, T, theta, nu, discount;
+    optional bc ('neumann', the default: Sketch 1; 'dirichlet': eq. bound1_0).
     """
     p = OrcParams()
     N = int(inst["N"])
@@ -112,6 +115,7 @@ def make_params(inst: dict) -> OrcParams:
     p.N = N
     p.payoff = {"caplet": 0, "swaption": 1}[inst["payoff"]]
     p.n_steps = int(inst["n_steps"])
+    p.bc = {"neumann": 0, "dirichlet": 1}[inst.get("bc", "neumann")]
     for name in ("alpha", "phi", "tau", "F0"):
         v = np.asarray(inst[name], dtype=np.float64)
         assert v.shape == (nr,), (name, v.shape)
@@ -182,6 +186,19 @@ def run(inst: dict, levels, Y0: np.ndarray, n_steps: int | None = None) -> np.nd
     lv = np.ascontiguousarray(levels, dtype=np.int32)
     Y = np.array(Y0, dtype=np.float64, copy=True)
     lib().orc_run(C.byref(p), _ip(lv), _dp(Y), int(p.n_steps if n_steps is None else n_steps))
+    return Y
+
+
+def run_theta_gs(inst: dict, levels, Y0: np.ndarray, s_iter: int, n_steps: int | None = None) -> np.ndarray:
+    """theta-method + Gauss-Seidel W-method (Sec. 4.2) with s_iter iterations
+    per step, theta = inst['theta'], dt = T / inst['n_steps'] (small grids)."""
+    p = make_params(inst)
+    lv = np.ascontiguousarray(levels, dtype=np.int32)
+    Y = np.array(Y0, dtype=np.float64, copy=True)
+    rc = lib().orc_run_theta_gs(C.byref(p), _ip(lv), _dp(Y),
+                                int(p.n_steps if n_steps is None else n_steps), int(s_iter))
+    if rc != 0:
+        raise ValueError("theta-GS oracle: grid above 4096 nodes or s_iter < 1")
     return Y
 
 

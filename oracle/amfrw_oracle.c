@@ -41,7 +41,9 @@ typedef struct {
     int32_t N;        /* spatial axes: N-1 forward rates and V (Sec. 2)        */
     int32_t payoff;   /* 0: caplet (F_1-K)^+ ; 1: swaption payoff of Sec. 2    */
     int32_t n_steps;  /* uniform time steps over [0,T]                         */
-    int32_t pad_;
+    int32_t bc;       /* 0: Neumann upper faces (Sketch 1); 1: the earlier
+                         Dirichlet conditions of eq. (bound1_0): u = g also on
+                         every face F_j = F_j^max of a rate                      */
     double alpha[ORC_MAXD];            /* alpha_i, rates 1..N-1                */
     double phi[ORC_MAXD];              /* phi_i rate/vol correlations          */
     double tau[ORC_MAXD];              /* accrual fractions tau_i              */
@@ -53,6 +55,7 @@ typedef struct {
 
 typedef struct {
     int N;
+    int bc;               /* orc_params.bc                                      */
     int M[ORC_MAXD];      /* M_i: the grid has M_i+1 nodes on axis i          */
     long E[ORC_MAXD];     /* E_1 = 1, E_i = prod_{r<i} (M_r+1)   (Sec. 3)      */
     long size;            /* prod (M_i+1)                                      */
@@ -62,6 +65,7 @@ typedef struct {
 static void grid_init(orc_grid *g, const orc_params *p, const int32_t *levels)
 {
     g->N = p->N;
+    g->bc = p->bc;
     g->size = 1;
     for (int i = 0; i < p->N; ++i) {
         g->M[i] = 1 << levels[i];
@@ -82,10 +86,14 @@ static void decode(const orc_grid *g, long J, int *j)
     }
 }
 
+/* Outer (Dirichlet) nodes: a lower face of any axis; under eq. (bound1_0) also
+ * the upper face of every rate axis (V keeps dU/dV = 0 at V^max). */
 static int is_outer(const orc_grid *g, const int *j)
 {
-    for (int i = 0; i < g->N; ++i)
+    for (int i = 0; i < g->N; ++i) {
         if (j[i] == 0) return 1;
+        if (g->bc && i < g->N - 1 && j[i] == g->M[i]) return 1;
+    }
     return 0;
 }
 
@@ -198,18 +206,21 @@ static void apply_F_part(const orc_params *p, const orc_grid *g, const double *Y
 }
 
 /* Lemma "ls" / Algorithm 1: solve (I - nu*dt*A_i) K = G for one axis.  Every
- * line of M_i Inner nodes along the axis is a tridiagonal system (eq.
- * decomp1): row 1 has no sub-diagonal (its neighbour is Outer), row M_i has
- * the doubled sub-diagonal of the Neumann ghost node.  Outer rows are the
- * identity.  Solved by Thomas elimination (the matrix is strictly diagonally
- * dominant).  K may alias G. */
+ * line of Inner nodes along the axis is a tridiagonal system (eq. decomp1):
+ * row 1 has no sub-diagonal (its neighbour is Outer); the last row is the
+ * Neumann face M_i with the doubled sub-diagonal of the ghost node, or, under
+ * eq. (bound1_0) on a rate axis, row M_i - 1 whose upper neighbour is Outer
+ * (no super-diagonal).  Outer rows are the identity.  Solved by Thomas
+ * elimination (the matrix is strictly diagonally dominant).  K may alias G. */
 static void line_solve(const orc_params *p, const orc_grid *g, int axis,
                        double nu_dt, const double *G, double *K)
 {
     int N = g->N;
-    int Mi = g->M[axis];
+    int neumann = !(g->bc && axis < N - 1);
+    int Mi = neumann ? g->M[axis] : g->M[axis] - 1;   /* Inner rows per line */
     long Ei = g->E[axis];
     if (K != G) memcpy(K, G, sizeof(double) * (size_t)g->size);
+    if (Mi < 1) return;
     double *R = (double *)malloc(sizeof(double) * (size_t)Mi);
     double *lo = (double *)malloc(sizeof(double) * (size_t)Mi);
     double *di = (double *)malloc(sizeof(double) * (size_t)Mi);
@@ -218,14 +229,10 @@ static void line_solve(const orc_params *p, const orc_grid *g, int axis,
     int j[ORC_MAXD];
     double F[ORC_MAXD];
     double h2 = g->h[axis] * g->h[axis];
-    /* every line start: j_axis = 1, all other indices in 1..M_l */
+    /* every line start: the Inner node with j_axis = 1 */
     for (long J0 = 0; J0 < g->size; ++J0) {
         decode(g, J0, j);
-        if (j[axis] != 1) continue;
-        int ok = 1;
-        for (int l = 0; l < N; ++l)
-            if (j[l] < 1) ok = 0;
-        if (!ok) continue;
+        if (j[axis] != 1 || is_outer(g, j)) continue;
         for (int r = 1; r <= Mi; ++r) {
             long J = J0 + (long)(r - 1) * Ei;
             j[axis] = r;
@@ -236,7 +243,7 @@ static void line_solve(const orc_params *p, const orc_grid *g, int axis,
             up[r - 1] = (r < Mi) ? -nu_dt * P : 0.0;
             if (r == 1)
                 lo[r - 1] = 0.0;
-            else if (r < Mi)
+            else if (r < Mi || !neumann)
                 lo[r - 1] = -nu_dt * P;
             else
                 lo[r - 1] = -2.0 * nu_dt * P;
@@ -303,6 +310,37 @@ static void amfrw2_step(const orc_params *p, const orc_grid *g, double dt, doubl
         Y[J] = y;
     }
     free(Kr[0]); free(Kr[1]); free(W); free(T); free(K0); free(KN);
+}
+
+/* The theta-method with a fixed number of Gauss-Seidel iterations, read as a
+ * W-method (Sec. 4.2, eqs. thetamet and GS): eq. (row-s) with W = P, the lower
+ * triangle (diagonal included) of A = F'(Y) in the node order of theta_0,
+ * a_rj = theta, q_rj = -1, b_r = 1 and s = s_iter stages:
+ *   (I - theta dt P) K_r = dt F(Y_n + theta sum_{j<r} K_j) - sum_{j<r} K_j,
+ *   Y_{n+1} = Y_n + sum_r K_r.
+ * A (n x n, row-major) is the dense matrix of the linear map F; each stage's
+ * triangular system is solved by forward substitution in node order. */
+static void theta_gs_step(const orc_params *p, const orc_grid *g, const double *A, double dt,
+                          int s_iter, double *Y)
+{
+    size_t n = (size_t)g->size;
+    double *sumK = (double *)calloc(n, sizeof(double));
+    double *W = (double *)malloc(sizeof(double) * n);
+    double *T = (double *)malloc(sizeof(double) * n);
+    double *Kr = (double *)malloc(sizeof(double) * n);
+    double th = p->theta;
+    for (int r = 0; r < s_iter; ++r) {
+        for (size_t J = 0; J < n; ++J) W[J] = Y[J] + th * sumK[J];
+        apply_F_part(p, g, W, T, -1);
+        for (size_t J = 0; J < n; ++J) {
+            double v = dt * T[J] - sumK[J];
+            for (size_t c = 0; c < J; ++c) v += th * dt * A[J * n + c] * Kr[c];
+            Kr[J] = v / (1.0 - th * dt * A[J * n + J]);
+        }
+        for (size_t J = 0; J < n; ++J) sumK[J] += Kr[J];
+    }
+    for (size_t J = 0; J < n; ++J) Y[J] += sumK[J];
+    free(sumK); free(W); free(T); free(Kr);
 }
 
 /* Multilinear interpolation of the grid function Y at x (Sec. 5.1, Sec. 6). */
@@ -392,6 +430,32 @@ void orc_run(const orc_params *p, const int32_t *levels, double *Y, int32_t n_st
     grid_init(&g, p, levels);
     double dt = p->T / (double)p->n_steps;
     for (int n = 0; n < n_steps; ++n) amfrw2_step(p, &g, dt, Y);
+}
+
+/* n_steps steps of the theta-method + Gauss-Seidel W-method with s_iter
+ * iterations, dt = T / p->n_steps, theta = p->theta, starting from Y
+ * (in/out).  The dense matrix of F is assembled column by column, F(e_c), so
+ * the grid may have at most 4096 nodes; returns -1 (Y untouched) beyond. */
+int32_t orc_run_theta_gs(const orc_params *p, const int32_t *levels, double *Y, int32_t n_steps,
+                         int32_t s_iter)
+{
+    orc_grid g;
+    grid_init(&g, p, levels);
+    size_t n = (size_t)g.size;
+    if (n > 4096 || s_iter < 1) return -1;
+    double *A = (double *)malloc(sizeof(double) * n * n);
+    double *e = (double *)calloc(n, sizeof(double));
+    double *col = (double *)malloc(sizeof(double) * n);
+    for (size_t c = 0; c < n; ++c) {
+        e[c] = 1.0;
+        apply_F_part(p, &g, e, col, -1);
+        e[c] = 0.0;
+        for (size_t J = 0; J < n; ++J) A[J * n + c] = col[J];
+    }
+    double dt = p->T / (double)p->n_steps;
+    for (int k = 0; k < n_steps; ++k) theta_gs_step(p, &g, A, dt, s_iter, Y);
+    free(A); free(e); free(col);
+    return 0;
 }
 
 double orc_interp(const orc_params *p, const int32_t *levels, const double *Y,
