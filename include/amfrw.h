@@ -250,6 +250,8 @@ int amfrw_tc_gemm_bf16(const void *dA, int32_t lda, const void *dB, int32_t ldb,
  *              `quantile` of |error| / spread; stores rel_bound.
  *   predict    ensemble mean and spread (price units) per instance;
  *              in_domain_out (may be NULL) = 1 inside the family and box.
+ *   predict_features  the same for raw feature rows [n x 8]; in_box_out
+ *              (may be NULL) = 1 inside the trained feature box.
  *   eval       prices_out [n] (network or solver), fell_back_out [n] (may be
  *              NULL): 1 where the solver priced the instance.
  *   eval_features  the same for queries given as raw features [n x 8]
@@ -273,6 +275,8 @@ int amfrw_surrogate_calibrate(amfrw_surrogate *s, const amfrw_params *ps, const 
                               double rel_bound, double quantile, double *calib_out);
 int amfrw_surrogate_predict(amfrw_surrogate *s, const amfrw_params *ps, int64_t n, double *mean_out,
                             double *spread_out, uint8_t *in_domain_out);
+int amfrw_surrogate_predict_features(amfrw_surrogate *s, const double *features, int64_t n, double *mean_out,
+                                     double *spread_out, uint8_t *in_box_out);
 int amfrw_surrogate_eval(amfrw_surrogate *s, const amfrw_params *ps, int64_t n, double *prices_out,
                          uint8_t *fell_back_out, void *cuda_stream);
 int amfrw_surrogate_eval_features(amfrw_surrogate *s, const double *features, int64_t n, double *prices_out,

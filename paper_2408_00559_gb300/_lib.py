@@ -29,7 +29,8 @@ EXPORTS = [
     "amfrw_batch_enable_timing", "amfrw_batch_kernel_times", "amfrw_batch_io_bytes",
     "amfrw_solve_noalloc", "amfrw_batch_autotune", "amfrw_tc_gemm_bf16",
     "amfrw_surrogate_create", "amfrw_surrogate_fit", "amfrw_surrogate_calibrate",
-    "amfrw_surrogate_predict", "amfrw_surrogate_eval", "amfrw_surrogate_eval_features",
+    "amfrw_surrogate_predict", "amfrw_surrogate_predict_features", "amfrw_surrogate_eval",
+    "amfrw_surrogate_eval_features",
     "amfrw_surrogate_save",
     "amfrw_surrogate_load", "amfrw_surrogate_params", "amfrw_surrogate_grad",
     "amfrw_surrogate_destroy", "amfrw_surrogate_last_error",
@@ -101,6 +102,7 @@ def lib():
         L.amfrw_surrogate_predict.argtypes = [vp, pp, i64, dpp, dpp, u8p]
         L.amfrw_surrogate_eval.argtypes = [vp, pp, i64, dpp, u8p, vp]
         L.amfrw_surrogate_eval_features.argtypes = [vp, dpp, i64, dpp, u8p, vp]
+        L.amfrw_surrogate_predict_features.argtypes = [vp, dpp, i64, dpp, dpp, u8p]
         L.amfrw_surrogate_save.argtypes = [vp, C.c_char_p]
         L.amfrw_surrogate_load.argtypes = [C.c_char_p, vp, C.POINTER(vp)]
         L.amfrw_surrogate_params.argtypes = [vp, i32, fp, fp]
@@ -363,6 +365,16 @@ class Surrogate:
         _scheck(lib().amfrw_surrogate_predict(self.h, m.arr, n, _dp(mean), _dp(spread),
                                               ok.ctypes.data_as(C.POINTER(C.c_uint8))),
                 "amfrw_surrogate_predict")
+        return mean, spread, ok.astype(bool)
+
+    def predict_features(self, features):
+        f = np.ascontiguousarray(features, dtype=np.float64)
+        n = f.shape[0]
+        mean, spread = np.zeros(n), np.zeros(n)
+        ok = np.zeros(n, dtype=np.uint8)
+        _scheck(lib().amfrw_surrogate_predict_features(self.h, _dp(f), n, _dp(mean), _dp(spread),
+                                                       ok.ctypes.data_as(C.POINTER(C.c_uint8))),
+                "amfrw_surrogate_predict_features")
         return mean, spread, ok.astype(bool)
 
     def eval(self, insts, marshalled=None):

@@ -888,6 +888,24 @@ int amfrw_surrogate_predict(amfrw_surrogate* s, const amfrw_params* ps, int64_t 
     return AMFRW_OK;
 }
 
+int amfrw_surrogate_predict_features(amfrw_surrogate* s, const double* features, int64_t n, double* mean_out,
+                                     double* spread_out, uint8_t* in_box_out)
+{
+    if (!s || !features || !mean_out || !spread_out) return sg_fail(AMFRW_EINVAL, "NULL argument");
+    if (n < 0) return sg_fail(AMFRW_EINVAL, "n < 0");
+    if (!s->trained) return sg_fail(AMFRW_EINVAL, "surrogate is not trained");
+    std::vector<double> mean, spread;
+    std::vector<char> ok((size_t)n, 1);
+    int st = sg_predict_raw(s, features, n, mean, spread, ok);
+    if (st != AMFRW_OK) return st;
+    for (int64_t i = 0; i < n; ++i) {
+        mean_out[i] = mean[(size_t)i];
+        spread_out[i] = spread[(size_t)i];
+        if (in_box_out) in_box_out[i] = ok[(size_t)i] ? 1 : 0;
+    }
+    return AMFRW_OK;
+}
+
 int amfrw_surrogate_calibrate(amfrw_surrogate* s, const amfrw_params* ps, const double* prices, int64_t n,
                               double rel_bound, double quantile, double* calib_out)
 {
