@@ -90,10 +90,16 @@ enum amfrw_precision {
  *   psi       0: standard combination; >= 1: modified combination.
  *   full_grid nonzero: one full grid with `level` on every axis.
  *   precision AMFRW_FP64 or AMFRW_MIXED.
+ *   flags     0, or AMFRW_FLAG_GLOBAL_GRIDS: solve every component grid with
+ *             its state in global memory, the path that grids too large for
+ *             shared memory (or with lines of more than 256 rows) always
+ *             take; the result is the same to rounding.  Other bits: EINVAL.
  *   theta     W-method parameter; AMFR-W2 has order 3 for (3+sqrt(3))/6.
  *   nu_amf    AMF parameter nu > 0 of eq. (Wmat1) (the paper's nu; named so
  *             apart from the volatility of volatility).
  */
+#define AMFRW_FLAG_GLOBAL_GRIDS 1
+
 typedef struct amfrw_params {
     int32_t n_rates;
     int32_t payoff;
@@ -102,7 +108,7 @@ typedef struct amfrw_params {
     int32_t psi;
     int32_t full_grid;
     int32_t precision;
-    int32_t reserved0;
+    int32_t flags;
     const double *alpha;
     const double *phi;
     const double *rho;

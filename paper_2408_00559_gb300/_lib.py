@@ -19,6 +19,7 @@ STATUS = {0: "AMFRW_OK", 1: "AMFRW_EINVAL", 2: "AMFRW_ENOTPSD", 3: "AMFRW_ENOMEM
           4: "AMFRW_ECUDA", 5: "AMFRW_ETIMEOUT", 6: "AMFRW_ENONFINITE", 7: "AMFRW_ETOOBIG"}
 PAYOFF = {"caplet": 0, "swaption": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
+FLAG_GLOBAL_GRIDS = 1
 
 # every symbol include/amfrw.h declares
 EXPORTS = [
@@ -48,7 +49,7 @@ class Params(C.Structure):
     _fields_ = [
         ("n_rates", C.c_int32), ("payoff", C.c_int32), ("n_steps", C.c_int32),
         ("level", C.c_int32), ("psi", C.c_int32), ("full_grid", C.c_int32),
-        ("precision", C.c_int32), ("reserved0", C.c_int32),
+        ("precision", C.c_int32), ("flags", C.c_int32),
         ("alpha", C.POINTER(C.c_double)), ("phi", C.POINTER(C.c_double)),
         ("rho", C.POINTER(C.c_double)), ("tau", C.POINTER(C.c_double)),
         ("F0", C.POINTER(C.c_double)), ("Fmax", C.POINTER(C.c_double)),
@@ -151,6 +152,7 @@ class _Marshal:
         p.psi = int(inst.get("psi", 0))
         p.full_grid = int(bool(inst.get("full", False)))
         p.precision = PRECISION[inst.get("precision", "fp64")]
+        p.flags = FLAG_GLOBAL_GRIDS if inst.get("global_grids", False) else 0
         for name in ("alpha", "phi", "tau", "F0", "Fmax"):
             setattr(p, name, _dp(self._vec(inst[name])))
         p.rho = _dp(self._vec(inst["rho"]))

@@ -89,6 +89,7 @@ int validate(const amfrw_params* p)
     if (p->precision != AMFRW_FP64 && p->precision != AMFRW_MIXED)
         return fail(AMFRW_EINVAL, "unknown precision");
     if (p->n_steps < 1) return fail(AMFRW_EINVAL, "n_steps must be >= 1");
+    if (p->flags & ~AMFRW_FLAG_GLOBAL_GRIDS) return fail(AMFRW_EINVAL, "unknown flag bits");
     if (p->level < 0 || p->psi < 0) return fail(AMFRW_EINVAL, "level and psi must be >= 0");
     const double sc[] = {p->sigma, p->beta, p->V0, p->Vmax, p->K, p->T, p->discount, p->theta, p->nu_amf};
     for (double v : sc)
@@ -227,14 +228,21 @@ int num_sms()
 struct LaunchClass {
     int N;
     bool mixed, warp;
+    int kind;            // kWarpGroup, kCtaGroup or kMemGroup
     int item_begin, item_count;
     int block, grid;
     size_t smem;
     int smem_group;
     int glog;            // warp groups: log2 lanes per group
-    int64_t lu_stride;   // bytes of Thomas factors per block (CTA groups)
+    int64_t lu_stride;   // bytes of scratch per block: Thomas factors (CTA
+                         // groups) or the whole grid state (global-memory groups)
     int64_t lu_offset;   // this class's part of the plan's scratch array
 };
+
+// Global-memory groups: at most this much scratch per launch class (it bounds
+// the number of resident blocks, each holding one grid's state).
+constexpr int64_t kMemScratchBudget = int64_t(8) << 30;
+constexpr int kMemBlock = 256;
 
 struct Plan {
     int device = 0;
@@ -314,86 +322,130 @@ int plan_host(const amfrw_params* ps, int n, bool keep_state, Plan& P)
             g_last_error = "instance " + std::to_string(i) + ": " + g_last_error;
             return st;
         }
-        const amfrw_params* p = ps + i;
-        std::vector<GridSpec> grids = enumerate(p->n_rates + 1, p->level, p->psi, p->full_grid != 0);
-        for (const GridSpec& g : grids) {
-            int sumlv = 0, maxlv = 0;
-            for (int a = 0; a <= p->n_rates; ++a) {
-                sumlv += g.lv[a];
-                maxlv = std::max(maxlv, (int)g.lv[a]);
-            }
-            if (sumlv > 20)
-                return fail(AMFRW_ETOOBIG, "instance " + std::to_string(i) +
-                                               ": a component grid has more than 2^20 Inner nodes");
-            if (maxlv > 5 + kRowsLogCta)
-                return fail(AMFRW_ETOOBIG, "instance " + std::to_string(i) +
-                                               ": an axis has more than 256 Inner nodes");
-        }
     }
     P.n_inst = n;
     const int smem_cap = max_smem_optin();
-    struct Tmp { Item it; int L; int N; bool mixed; bool warp; int smem_group; };
-    std::vector<Tmp> all;
+    // The grids of one instance shape (N, level, psi, full grid, precision,
+    // flags) with their work-group kind and layout size, shared by every
+    // instance of that shape.
+    struct GridInfo { GridSpec g; int L; int kind; bool warp; int smem_group; int rank; };
+    using ShapeId = std::tuple<int, int, int, int, int, int>;
+    std::map<ShapeId, std::vector<GridInfo>> shapes;
+    std::vector<std::vector<GridInfo>*> inst_shape((size_t)n);
+    for (int i = 0; i < n; ++i) {
+        const amfrw_params* p = ps + i;
+        const int N = p->n_rates + 1;
+        const bool mixed = p->precision == AMFRW_MIXED;
+        const bool force_mem = (p->flags & AMFRW_FLAG_GLOBAL_GRIDS) != 0;
+        const ShapeId id{N, p->level, p->psi, p->full_grid != 0, mixed, force_mem};
+        auto it = shapes.find(id);
+        if (it == shapes.end()) {
+            std::vector<GridInfo> gi;
+            for (const GridSpec& g : enumerate(N, p->level, p->psi, p->full_grid != 0)) {
+                int llog = 0, maxlv = 0;
+                for (int a = 0; a < N; ++a) {
+                    llog += g.lv[a];
+                    maxlv = std::max(maxlv, (int)g.lv[a]);
+                }
+                if (llog > 20)
+                    return fail(AMFRW_ETOOBIG, "instance " + std::to_string(i) +
+                                                   ": a component grid has more than 2^20 Inner nodes");
+                const bool warp = (1 << llog) <= kWarpMaxL && !force_mem;
+                // warp groups: one lane per node up to 32 nodes (at least 8 lanes), so
+                // small grids share a warp
+                int kind = warp ? kWarpGroup : kCtaGroup;
+                Layout lay = make_layout(N, g.lv, mixed, kind,
+                                         warp ? std::max(std::min(llog, 5), kMinGroupLog) : 5);
+                // grids beyond shared memory, or with lines longer than the register
+                // sweeps take, keep their state in global memory
+                if (force_mem || lay.total > smem_cap || (!warp && maxlv > 5 + kRowsLogCta)) {
+                    kind = kMemGroup;
+                    lay = make_layout(N, g.lv, mixed, kind, log2i(kMemBlock));
+                }
+                gi.push_back(GridInfo{g, lay.L, kind, warp, lay.total, 0});
+            }
+            it = shapes.emplace(id, std::move(gi)).first;
+        }
+        inst_shape[(size_t)i] = &it->second;
+    }
+    // classes: (N, precision, group kind) and, for warp groups, the grid size;
+    // inside a class the largest grids first, equal shapes adjacent and, for
+    // equal shapes, instance order.  Rank the distinct grid shapes once, then
+    // place the grids by a counting sort over the ranks.
+    struct Key { int N; bool mixed; int kind; int wl; int L; int8_t lv[kMaxDim]; };
+    auto key_less = [](const Key& a, const Key& b) {
+        const auto ta = std::make_tuple(a.N, a.mixed, a.kind, -a.wl, -a.L);
+        const auto tb = std::make_tuple(b.N, b.mixed, b.kind, -b.wl, -b.L);
+        if (ta != tb) return ta < tb;
+        return memcmp(a.lv, b.lv, sizeof(a.lv)) < 0;
+    };
+    std::vector<std::pair<Key, GridInfo*>> keys;
+    for (auto& kv : shapes) {
+        const int N = std::get<0>(kv.first);
+        const bool mixed = std::get<4>(kv.first) != 0;
+        for (GridInfo& gi : kv.second) {
+            Key k{};
+            k.N = N;
+            k.mixed = mixed;
+            k.kind = gi.kind;
+            k.wl = gi.warp ? gi.L : 0;
+            k.L = gi.L;
+            memcpy(k.lv, gi.g.lv, sizeof(k.lv));
+            keys.push_back({k, &gi});
+        }
+    }
+    std::sort(keys.begin(), keys.end(),
+              [&](const std::pair<Key, GridInfo*>& a, const std::pair<Key, GridInfo*>& b) { return key_less(a.first, b.first); });
+    int nrank = 0;
+    for (size_t q = 0; q < keys.size(); ++q) {
+        if (q > 0 && key_less(keys[q - 1].first, keys[q].first)) ++nrank;
+        keys[q].second->rank = nrank;
+    }
+    ++nrank;
+    struct Tmp { Item it; int L; int N; bool mixed; bool warp; int kind; int smem_group; };
+    std::vector<int64_t> start((size_t)nrank + 1, 0);
+    for (int i = 0; i < n; ++i)
+        for (const GridInfo& gi : *inst_shape[(size_t)i]) ++start[(size_t)gi.rank + 1];
+    for (int r = 0; r < nrank; ++r) start[(size_t)r + 1] += start[(size_t)r];
+    std::vector<Tmp> all((size_t)start[(size_t)nrank]);
     int64_t state_off = 0;
     for (int i = 0; i < n; ++i) {
         const amfrw_params* p = ps + i;
         InstDev I = to_device(p);
         const int N = I.N;
         const bool mixed = p->precision == AMFRW_MIXED;
-        std::vector<GridSpec> grids = enumerate(N, p->level, p->psi, p->full_grid != 0);
+        const std::vector<GridInfo>& grids = *inst_shape[(size_t)i];
         I.grid_begin = (int32_t)P.coefs.size();
         I.grid_count = (int32_t)grids.size();
-        for (const GridSpec& g : grids) {
-            int Lg = 1, llog = 0;
-            for (int a = 0; a < N; ++a) {
-                Lg <<= g.lv[a];
-                llog += g.lv[a];
-            }
-            const bool warp = Lg <= kWarpMaxL;
-            // warp groups: one lane per node up to 32 nodes (at least 8 lanes), so
-            // small grids share a warp
-            Layout lay = make_layout(N, g.lv, mixed, warp,
-                                     warp ? std::max(std::min(llog, 5), kMinGroupLog) : 5);
-            if (lay.total > smem_cap)
-                return fail(AMFRW_ETOOBIG, "component grid with " + std::to_string(lay.L) +
-                                               " Inner nodes needs " + std::to_string(lay.total) +
-                                               " bytes of shared memory (limit " +
-                                               std::to_string(smem_cap) + ")");
+        for (const GridInfo& gi : grids) {
             Tmp t{};
             t.it.inst = i;
             t.it.out_idx = (int32_t)P.coefs.size();
-            t.it.L = lay.L;
-            memcpy(t.it.lv, g.lv, sizeof(t.it.lv));
+            t.it.L = gi.L;
+            memcpy(t.it.lv, gi.g.lv, sizeof(t.it.lv));
             t.it.state_off = keep_state ? state_off : -1;
-            if (keep_state) state_off += lay.L;
-            t.L = lay.L;
+            if (keep_state) state_off += gi.L;
+            t.L = gi.L;
             t.N = N;
             t.mixed = mixed;
-            t.warp = warp;
-            t.smem_group = lay.total;
-            all.push_back(t);
-            P.coefs.push_back(g.coef);
-            for (int a = 0; a < kMaxDim; ++a) P.levels.push_back(a < N ? g.lv[a] : 0);
+            t.warp = gi.warp;
+            t.kind = gi.kind;
+            t.smem_group = gi.smem_group;
+            all[(size_t)start[(size_t)gi.rank]++] = t;
+            P.coefs.push_back(gi.g.coef);
+            for (int a = 0; a < kMaxDim; ++a) P.levels.push_back(a < N ? gi.g.lv[a] : 0);
         }
         P.insts.push_back(I);
         P.dim = N;
     }
     P.n_grids = (int)P.coefs.size();
     P.state_len = state_off;
-    // classes: (N, precision, group kind) and, for warp groups, the grid size;
-    // inside a class the largest grids first and equal shapes adjacent
-    std::stable_sort(all.begin(), all.end(), [](const Tmp& a, const Tmp& b) {
-        const int wa = a.warp ? a.L : 0, wb = b.warp ? b.L : 0;
-        if (std::make_tuple(a.N, a.mixed, a.warp, -wa, -a.L) != std::make_tuple(b.N, b.mixed, b.warp, -wb, -b.L))
-            return std::make_tuple(a.N, a.mixed, a.warp, -wa, -a.L) < std::make_tuple(b.N, b.mixed, b.warp, -wb, -b.L);
-        return memcmp(a.it.lv, b.it.lv, sizeof(a.it.lv)) < 0;
-    });
     const int sms = num_sms();
     for (size_t k = 0; k < all.size();) {
         size_t e = k;
         int gmax = 0, lmax = 0;
         while (e < all.size() && all[e].N == all[k].N && all[e].mixed == all[k].mixed &&
-               all[e].warp == all[k].warp && (!all[k].warp || all[e].L == all[k].L)) {
+               all[e].kind == all[k].kind && (!all[k].warp || all[e].L == all[k].L)) {
             gmax = std::max(gmax, all[e].smem_group);
             lmax = std::max(lmax, all[e].L);
             ++e;
@@ -402,6 +454,7 @@ int plan_host(const amfrw_params* ps, int n, bool keep_state, Plan& P)
         c.N = all[k].N;
         c.mixed = all[k].mixed;
         c.warp = all[k].warp;
+        c.kind = all[k].kind;
         c.item_begin = (int)P.items.size();
         c.item_count = (int)(e - k);
         c.smem_group = gmax;
@@ -414,17 +467,21 @@ int plan_host(const amfrw_params* ps, int n, bool keep_state, Plan& P)
                 return fail(AMFRW_ETOOBIG, "warp groups of a launch class do not fit in shared memory");
             c.block = 32 * wpb;
             c.smem = (size_t)gmax * gpw * wpb;
-        } else {
+        } else if (c.kind == kCtaGroup) {
             int b = 64;
             while (b < kCtaMaxThreads && b * 8 < lmax) b *= 2;
             c.block = b;
             c.smem = (size_t)gmax;
             for (size_t q = k; q < e; ++q) {
-                Layout lay = make_layout(c.N, all[q].it.lv, c.mixed, false, log2i(b));
+                Layout lay = make_layout(c.N, all[q].it.lv, c.mixed, kCtaGroup, log2i(b));
                 lumax = std::max<int64_t>(lumax, (int64_t)lay.nlu * (c.mixed ? 4 : 8));
             }
+        } else {  // global-memory groups: each block's slice holds a whole grid state
+            c.block = kMemBlock;
+            c.smem = 0;
+            lumax = gmax;
         }
-        const int per_sm = occ_for(c.N)(c.mixed, c.warp, c.block, c.smem);
+        const int per_sm = occ_for(c.N)(c.mixed, c.kind, c.block, c.smem);
         if (per_sm < 1)
             return fail(AMFRW_ETOOBIG, "no resident block possible for a launch class (shared memory " +
                                            std::to_string(c.smem) + " bytes)");
@@ -432,6 +489,8 @@ int plan_host(const amfrw_params* ps, int n, bool keep_state, Plan& P)
         const int need = (c.item_count + groups_per_block - 1) / groups_per_block;
         c.grid = std::max(1, std::min(need, per_sm * sms));
         c.lu_stride = (lumax + 255) & ~(int64_t)255;
+        if (c.kind == kMemGroup && c.lu_stride > 0)
+            c.grid = (int)std::max<int64_t>(1, std::min<int64_t>(c.grid, kMemScratchBudget / c.lu_stride));
         c.lu_offset = P.lu_scratch_len;
         P.lu_scratch_len += c.lu_stride * c.grid;
         for (size_t q = k; q < e; ++q) P.items.push_back(all[q].it);
@@ -491,7 +550,7 @@ int build_warp_launches(Plan& P)
         const int wpb = std::min(kWarpsPerBlock, std::max(1, smem_cap / w.smem_warp));
         w.block = 32 * wpb;
         w.smem = (size_t)w.smem_warp * wpb;
-        const int per_sm = occ_for(w.N)(w.mixed, true, w.block, w.smem);
+        const int per_sm = occ_for(w.N)(w.mixed, kWarpGroup, w.block, w.smem);
         if (per_sm < 1) return fail(AMFRW_ETOOBIG, "no resident block possible for a warp-group launch");
         const int need = (items + w.block - 1) / w.block;
         w.grid = std::max(1, std::min(need, per_sm * sms));
@@ -605,11 +664,11 @@ int run_solve(Plan& P, int steps, int flags, cudaEvent_t* ev = nullptr)
             a.classes = P.d_cdesc + w.desc_offset;
             a.n_classes = (int32_t)w.cls.size();
             a.smem_warp = w.smem_warp;
-            rc = launch_for(w.N)(a, w.mixed, true, w.block, w.grid, w.smem, P.stream);
+            rc = launch_for(w.N)(a, w.mixed, kWarpGroup, w.block, w.grid, w.smem, P.stream);
         } else {
             const int c = recs[r].second;
             const LaunchClass& L = P.classes[c];
-            rc = launch_for(L.N)(class_args(P, L, c, steps, flags), L.mixed, false, L.block, L.grid,
+            rc = launch_for(L.N)(class_args(P, L, c, steps, flags), L.mixed, L.kind, L.block, L.grid,
                                  L.smem, P.stream);
         }
         if (ev) CUDA_TRY(cudaEventRecordWithFlags(ev[2 * r + 1], P.stream, cudaEventRecordExternal));
@@ -668,7 +727,7 @@ std::string class_signature(const Plan& P)
 {
     std::string sig;
     for (const LaunchClass& c : P.classes) {
-        sig += std::to_string(c.N) + (c.mixed ? "m" : "d") + (c.warp ? "w" : "c") +
+        sig += std::to_string(c.N) + (c.mixed ? "m" : "d") + (c.kind == kWarpGroup ? "w" : (c.kind == kCtaGroup ? "c" : "g")) +
                std::to_string(P.items[c.item_begin].L) + ":" +
                std::to_string(c.item_count > 4096 ? 4096 : c.item_count) + ";";
     }

@@ -39,7 +39,7 @@ struct Item {
 // to size dynamic shared memory, the device to place the arrays; both call
 // this one function so they cannot disagree.
 struct Layout {
-    int32_t cd, cf, tabd, tabf, pay, lu, Z, ZZ, H, FY, K1, K0, Kw, D, C, total;
+    int32_t cd, cf, tabd, tabf, pay, lu, Z, ZZ, H, FY, K1, K0, Kw, D, C, scr, total;
     int32_t L, Lp, Lr, ntab, npay, nlu, ncoef;
 };
 
@@ -63,11 +63,26 @@ struct Consts {
 
 AMFRW_HD int32_t align16(int32_t x) { return (x + 15) & ~15; }
 
+// Work-group kinds.  kWarpGroup: a grid of at most 64 Inner nodes on (part
+// of) one warp, everything in shared memory.  kCtaGroup: one CTA per grid,
+// the grid in shared memory, line-solve factors in a global scratch slice.
+// kMemGroup: one CTA per grid with the whole grid state in its block's slice
+// of global scratch (L2/HBM resident): grids too large for shared memory or
+// with lines of more than 256 rows.
+constexpr int kWarpGroup = 0;
+constexpr int kCtaGroup = 1;
+constexpr int kMemGroup = 2;
+
 // Rows of a line per lane in a line solve: at most 2 for warp groups (grids of
-// at most 64 Inner nodes), at most 8 for CTA groups.
+// at most 64 Inner nodes), at most 8 for CTA groups (rows held in registers);
+// unbounded for global-memory groups (rows streamed from memory).
 constexpr int kRowsLogWarp = 1;
 constexpr int kRowsLogCta = 3;
-AMFRW_HD int rows_log(bool warp) { return warp ? kRowsLogWarp : kRowsLogCta; }
+constexpr int kRowsLogMem = 24;
+AMFRW_HD int rows_log(int kind)
+{
+    return kind == kWarpGroup ? kRowsLogWarp : (kind == kCtaGroup ? kRowsLogCta : kRowsLogMem);
+}
 
 // Lanes per line (as log2) for the directional solves along an axis with
 // 2^mlog rows, on a grid of 2^llog Inner nodes solved by a group of 2^tlog
@@ -88,10 +103,12 @@ AMFRW_HD int lanes_log(int mlog, int llog, int tlog, int rlog)
 // (lower, 1/pivot, upper/pivot) of the reduced interleaved systems.
 AMFRW_HD int lu_row_values(int plog) { return 2 * plog + 3; }
 
-// lu_smem: true for warp groups (line-solve factors in shared memory), false
-// for CTA groups (factors in the group's slice of a global scratch array);
-// tlog: log2 of the group's thread count.
-AMFRW_HD Layout make_layout(int N, const int8_t* lv, bool mixed, bool lu_smem, int tlog)
+// kind: the work-group kind.  Warp and global-memory groups keep the
+// line-solve factors inside the layout; CTA groups in the group's slice of a
+// global scratch array.  Global-memory groups also get FP64 scratch for the
+// factorisation (three values per matrix row of the largest axis).  tlog:
+// log2 of the group's thread count.
+AMFRW_HD Layout make_layout(int N, const int8_t* lv, bool mixed, int kind, int tlog)
 {
     Layout y{};
     int L = 1, sumM = 0, npay = 0;
@@ -113,8 +130,9 @@ AMFRW_HD Layout make_layout(int N, const int8_t* lv, bool mixed, bool lu_smem, i
     int nlu = 0;
     for (int i = 0; i < N; ++i) {
         const int rows = (i < N - 1 ? MV : 1) << lv[i];  // classes x rows
-        nlu += rows * lu_row_values(lanes_log(lv[i], llog, tlog, rows_log(lu_smem)));
+        nlu += rows * lu_row_values(lanes_log(lv[i], llog, tlog, rows_log(kind)));
     }
+    const bool lu_in = kind != kCtaGroup;
     y.nlu = nlu;
     const int sk = mixed ? 4 : 8;  // bytes of an increment / table value
     int o = 0;
@@ -123,7 +141,7 @@ AMFRW_HD Layout make_layout(int N, const int8_t* lv, bool mixed, bool lu_smem, i
     y.tabd = o; o = align16(o + 8 * y.ntab);
     y.tabf = o; o = align16(o + (mixed ? 4 * y.ntab : 0));
     y.pay = o;  o = align16(o + 8 * y.npay);
-    y.lu = o;   o = align16(o + (lu_smem ? sk * y.nlu : 0));
+    y.lu = o;   o = align16(o + (lu_in ? sk * y.nlu : 0));
     y.Z = o;    o = align16(o + 8 * y.Lp);
     y.ZZ = o;   o = align16(o + (mixed ? 8 * y.Lp : 0));
     y.H = o;    o = align16(o + sk * y.Lr);
@@ -132,10 +150,16 @@ AMFRW_HD Layout make_layout(int N, const int8_t* lv, bool mixed, bool lu_smem, i
     y.K0 = o;   o = align16(o + sk * y.Lp);
     y.Kw = o;   o = align16(o + sk * y.Lp);
     // FP64 warp groups: central differences per axis and per-node coefficients
-    const bool diff = !mixed && lu_smem;
+    const bool diff = !mixed && kind == kWarpGroup;
     y.ncoef = diff ? node_coefs(N) : 0;
     y.D = o;    o = align16(o + (diff ? 8 * N * y.Lp : 0));
     y.C = o;    o = align16(o + 8 * y.ncoef * y.Lp);
+    int rmax = 0;
+    for (int i = 0; i < N; ++i) {
+        const int rows = (i < N - 1 ? MV : 1) << lv[i];
+        rmax = rows > rmax ? rows : rmax;
+    }
+    y.scr = o;  o = align16(o + (kind == kMemGroup ? 3 * 8 * rmax : 0));
     y.total = o;
     return y;
 }
@@ -169,24 +193,24 @@ constexpr int kLoadState = 1;
 constexpr int kStoreState = 2;
 
 // Host-side launchers, one translation unit per dimension N.
-using LaunchFn = int (*)(const SolveArgs&, bool mixed, bool warp, int block, int grid,
+using LaunchFn = int (*)(const SolveArgs&, bool mixed, int kind, int block, int grid,
                          size_t smem, void* stream);
-int launch_n2(const SolveArgs&, bool, bool, int, int, size_t, void*);
-int launch_n3(const SolveArgs&, bool, bool, int, int, size_t, void*);
-int launch_n4(const SolveArgs&, bool, bool, int, int, size_t, void*);
-int launch_n5(const SolveArgs&, bool, bool, int, int, size_t, void*);
-int launch_n6(const SolveArgs&, bool, bool, int, int, size_t, void*);
-int launch_n7(const SolveArgs&, bool, bool, int, int, size_t, void*);
-int launch_n8(const SolveArgs&, bool, bool, int, int, size_t, void*);
+int launch_n2(const SolveArgs&, bool, int, int, int, size_t, void*);
+int launch_n3(const SolveArgs&, bool, int, int, int, size_t, void*);
+int launch_n4(const SolveArgs&, bool, int, int, int, size_t, void*);
+int launch_n5(const SolveArgs&, bool, int, int, int, size_t, void*);
+int launch_n6(const SolveArgs&, bool, int, int, int, size_t, void*);
+int launch_n7(const SolveArgs&, bool, int, int, int, size_t, void*);
+int launch_n8(const SolveArgs&, bool, int, int, int, size_t, void*);
 // Occupancy query for the same instantiation (blocks per SM).
-int occupancy(int N, bool mixed, bool warp, int block, size_t smem);
-using OccFn = int (*)(bool mixed, bool warp, int block, size_t smem);
-int occupancy_n2(bool, bool, int, size_t);
-int occupancy_n3(bool, bool, int, size_t);
-int occupancy_n4(bool, bool, int, size_t);
-int occupancy_n5(bool, bool, int, size_t);
-int occupancy_n6(bool, bool, int, size_t);
-int occupancy_n7(bool, bool, int, size_t);
-int occupancy_n8(bool, bool, int, size_t);
+int occupancy(int N, bool mixed, int kind, int block, size_t smem);
+using OccFn = int (*)(bool mixed, int kind, int block, size_t smem);
+int occupancy_n2(bool, int, int, size_t);
+int occupancy_n3(bool, int, int, size_t);
+int occupancy_n4(bool, int, int, size_t);
+int occupancy_n5(bool, int, int, size_t);
+int occupancy_n6(bool, int, int, size_t);
+int occupancy_n7(bool, int, int, size_t);
+int occupancy_n8(bool, int, int, size_t);
 
 }  // namespace amfrw

@@ -560,6 +560,188 @@ struct NoEpi {
     __device__ __forceinline__ void operator()(int, T) const {}
 };
 
+// ------------------------------------- line solves on grids in global memory
+// The same reduction and elimination as pcr_setup / sweep, for grids whose
+// state lives in global memory and whose lines may have any length: a lane's
+// rows are not held in registers but streamed from memory, one pass per PCR
+// level (ascending rows; the lane keeps the pre-update value of its previous
+// row and reads the next row before it is overwritten) and one pass each for
+// the Thomas forward and backward sweeps.  Lanes of a line step through their
+// rows together, so the shuffles pair the same rows as in the register
+// version and the arithmetic is the same.
+
+// PCR multipliers and Thomas factors; scr holds the running (lower, diagonal,
+// upper) of every row of the axis being factored (3 x rows doubles).
+template <int N, typename T>
+__device__ void pcr_setup_mem(const Shape<N>& s, const double* tabd, const Consts<double>& c, T* lu,
+                              double* scr, int rank, int gsize, unsigned gm)
+{
+    for (int axis = 0; axis < N; ++axis) {
+        const int M = s.M[axis];
+        const int plog = s.plog[axis];
+        const int P = 1 << plog;
+        const int R = M >> plog;
+        const int S = s.luS[axis];
+        const int ncls = (axis < N - 1) ? s.M[N - 1] : 1;
+        const int rows = ncls * M;
+        double* sa = scr;
+        double* sb = scr + rows;
+        double* su = scr + 2 * rows;
+        const int lpr = gsize >> plog;
+        const int p = rank & (P - 1);
+        const int slot = rank >> plog;
+        for (int base = 0; base < ncls; base += lpr) {  // uniform across the group
+            const int cls = base + slot;
+            const bool act = cls < ncls;
+            const int cl = act ? cls : 0;
+            T* tb = lu + s.luoff[axis] + (cl * M + p) * S;
+            const int r0 = cl * M + p;  // this lane's row q lives at r0 + P q
+            if (act)
+                for (int q = 0; q < R; ++q) {
+                    double a, b, u;
+                    matrix_row<N>(s, tabd, c, axis, cl, p + P * q, a, b, u);
+                    sa[r0 + P * q] = a;
+                    sb[r0 + P * q] = b;
+                    su[r0 + P * q] = u;
+                }
+            for (int k = 0; k < plog; ++k) {
+                const int d = 1 << k;
+                const int sm = (p - d) & (P - 1), sp = (p + d) & (P - 1);
+                const bool wm = p < d, wp = p + d >= P;
+                const bool send_prev = p >= P - d;
+                const bool send_next = p < d;
+                double pa = 0.0, pb = 1.0, pu = 0.0;  // pre-update values of row q-1
+                double ca = act ? sa[r0] : 0.0, cb = act ? sb[r0] : 1.0, cu = act ? su[r0] : 0.0;
+                for (int q = 0; q < R; ++q) {
+                    const bool nx = q + 1 < R;
+                    const int rn = r0 + P * (q + 1);
+                    const double na = (act && nx) ? sa[rn] : 0.0;
+                    const double nb = (act && nx) ? sb[rn] : 1.0;
+                    const double nu = (act && nx) ? su[rn] : 0.0;
+                    const double a_m = shfl(send_prev ? pa : ca, sm, P, gm);
+                    const double b_m = shfl(send_prev ? pb : cb, sm, P, gm);
+                    const double u_m = shfl(send_prev ? pu : cu, sm, P, gm);
+                    const double a_p = shfl(send_next ? na : ca, sp, P, gm);
+                    const double b_p = shfl(send_next ? nb : cb, sp, P, gm);
+                    const double u_p = shfl(send_next ? nu : cu, sp, P, gm);
+                    const bool hm = !wm || q >= 1;
+                    const double al = hm ? ca / b_m : 0.0;
+                    const double ga = cu / b_p;  // identity row sent past the end
+                    const double gg = (wp && !nx) ? 0.0 : ga;
+                    if (act) {
+                        tb[q * P * S + 2 * k] = (T)al;
+                        tb[q * P * S + 2 * k + 1] = (T)gg;
+                        const int rq = r0 + P * q;
+                        sb[rq] = cb - al * u_m - gg * a_p;
+                        sa[rq] = -al * a_m;
+                        su[rq] = -gg * u_p;
+                    }
+                    pa = ca;
+                    pb = cb;
+                    pu = cu;
+                    ca = na;
+                    cb = nb;
+                    cu = nu;
+                }
+            }
+            // Thomas factors of the lane's interleaved system
+            double gam = 0.0;
+            if (act)
+                for (int q = 0; q < R; ++q) {
+                    const int rq = r0 + P * q;
+                    const double inv = 1.0 / (sb[rq] - sa[rq] * gam);
+                    gam = su[rq] * inv;
+                    T* row = tb + q * P * S + 2 * plog;
+                    row[0] = (T)sa[rq];
+                    row[1] = (T)inv;
+                    row[2] = (T)gam;
+                }
+        }
+        __syncthreads();  // the next axis reuses scr
+    }
+}
+
+template <int N, typename T, class Epi>
+__device__ __forceinline__ void sweep_mem(const Shape<N>& s, int axis, const T* __restrict__ lu,
+                                          const T* src, T* dst, int rank, int gsize, unsigned gm,
+                                          Epi epi)
+{
+    const int M = s.M[axis];
+    const int plog = s.plog[axis];
+    const int P = 1 << plog;
+    const int R = M >> plog;
+    const int S = s.luS[axis];
+    const int lvA = s.lv[axis];
+    const int sh = s.sh[axis];
+    const int Spa = s.Sp[axis];
+    const int nl = s.L >> lvA;
+    const int lo_mask = (1 << sh) - 1;
+    const int MV1 = s.M[N - 1] - 1;
+    const int shV = s.sh[N - 1];
+    const int lpr = gsize >> plog;
+    const int p = rank & (P - 1);
+    const int slot = rank >> plog;
+    for (int base = 0; base < nl; base += lpr) {  // uniform across the group
+        const int line = base + slot;
+        const bool act = line < nl;
+        const int ln = act ? line : 0;
+        const int t0 = (ln & lo_mask) | ((ln >> sh) << (sh + lvA));
+        const int J0 = s.padded(t0) + p * Spa;
+        const int cls = (axis == N - 1) ? 0 : ((t0 >> shV) & MV1);
+        const T* tb = lu + s.luoff[axis] + (cls * M + p) * S;
+        const int PS = P * S, PSp = P * Spa;
+        const T* in = src;
+        for (int k = 0; k < plog; ++k) {
+            const int d = 1 << k;
+            const int sm = (p - d) & (P - 1), sp = (p + d) & (P - 1);
+            const bool send_prev = p >= P - d;
+            const bool send_next = p < d;
+            T prev = T(0);
+            T cur = act ? in[J0] : T(0);
+            for (int q = 0; q < R; ++q) {
+                const T nxt = (act && q + 1 < R) ? in[J0 + (q + 1) * PSp] : T(0);
+                const T vm = shfl(send_prev ? prev : cur, sm, P, gm);
+                const T vp = shfl(send_next ? nxt : cur, sp, P, gm);
+                const T* row = tb + q * PS;
+                if (act) dst[J0 + q * PSp] = cur - row[2 * k] * vm - row[2 * k + 1] * vp;
+                prev = cur;
+                cur = nxt;
+            }
+            in = dst;  // later levels in place
+        }
+        if (act) {
+            T y = T(0);
+            for (int q = 0; q < R; ++q) {
+                const T* row = tb + q * PS + 2 * plog;
+                y = (in[J0 + q * PSp] - row[0] * y) * row[1];
+                dst[J0 + q * PSp] = y;
+            }
+            int J = J0 + (R - 1) * PSp;
+            epi(J, y);
+            for (int q = R - 2; q >= 0; --q) {
+                J = J0 + q * PSp;
+                y = dst[J] - tb[q * PS + 2 * plog + 2] * y;
+                dst[J] = y;
+                epi(J, y);
+            }
+        }
+    }
+}
+
+// Line sweep of a work-group kind: rows in registers (warp and CTA groups)
+// or streamed from memory (global-memory groups).
+template <int N, typename T, int KIND, class Epi>
+__device__ __forceinline__ void lsweep(const Shape<N>& s, int axis, const T* __restrict__ lu,
+                                       const T* src, T* dst, int rank, int gsize, unsigned gm,
+                                       Epi epi)
+{
+    if constexpr (KIND == kMemGroup)
+        sweep_mem<N, T>(s, axis, lu, src, dst, rank, gsize, gm, epi);
+    else
+        sweep<N, T, 1 << (KIND == kWarpGroup ? kRowsLogWarp : kRowsLogCta)>(s, axis, lu, src, dst, rank,
+                                                                            gsize, gm, epi);
+}
+
 template <bool WARP>
 __device__ __forceinline__ void gsync(unsigned gm)
 {
@@ -651,31 +833,33 @@ __device__ __forceinline__ float2 split_df(double z)
 }
 
 // N directional solves: the first from `from` into `to`, the rest in place.
-template <int N, typename TK, int RMAX, bool WARP>
+template <int N, typename TK, int KIND>
 __device__ __forceinline__ void sweeps_into(const Shape<N>& s, const TK* lu, const TK* from, TK* to,
                                             int rank, int gsize, unsigned gm)
 {
-    sweep<N, TK, RMAX>(s, 0, lu, from, to, rank, gsize, gm, NoEpi());
+    constexpr bool WARP = KIND == kWarpGroup;
+    lsweep<N, TK, KIND>(s, 0, lu, from, to, rank, gsize, gm, NoEpi());
     gsync<WARP>(gm);
     for (int ax = 1; ax < N; ++ax) {
-        sweep<N, TK, RMAX>(s, ax, lu, to, to, rank, gsize, gm, NoEpi());
+        lsweep<N, TK, KIND>(s, ax, lu, to, to, rank, gsize, gm, NoEpi());
         gsync<WARP>(gm);
     }
 }
 
 // ------------------------------------------------------------- one grid
-template <int N, bool MIXED, bool WARP>
+template <int N, bool MIXED, int KIND>
 __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* base, int rank,
                            int gsize)
 {
     using TK = typename std::conditional<MIXED, float, double>::type;
+    constexpr bool WARP = KIND == kWarpGroup;
     const InstDev& P = a.insts[it.inst];
     constexpr int RMAX = 1 << (WARP ? kRowsLogWarp : kRowsLogCta);
     const int tlog = 31 - __clz(gsize);
     const unsigned gm = WARP ? group_mask(tlog) : 0xffffffffu;
     Shape<N> s;
-    make_shape<N>(s, it.lv, tlog, rows_log(WARP));
-    const Layout lay = make_layout(N, it.lv, MIXED, WARP, tlog);
+    make_shape<N>(s, it.lv, tlog, rows_log(KIND));
+    const Layout lay = make_layout(N, it.lv, MIXED, KIND, tlog);
     Consts<double>* cd = reinterpret_cast<Consts<double>*>(base + lay.cd);
     Consts<TK>* ck = MIXED ? reinterpret_cast<Consts<TK>*>(base + lay.cf)
                            : reinterpret_cast<Consts<TK>*>(base + lay.cd);
@@ -683,10 +867,11 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
     TK* tabk = MIXED ? reinterpret_cast<TK*>(base + lay.tabf) : reinterpret_cast<TK*>(tabd);
     double* pay = reinterpret_cast<double*>(base + lay.pay);
     // warp groups keep the Thomas factors on chip; a CTA group (grids of more
-    // than 256 Inner nodes) keeps them in its block's slice of global scratch,
-    // read through L1
-    TK* lu = WARP ? reinterpret_cast<TK*>(base + lay.lu)
-                  : reinterpret_cast<TK*>(a.lu_scratch + (size_t)blockIdx.x * (size_t)a.lu_stride);
+    // than 64 Inner nodes) keeps them in its block's slice of global scratch,
+    // read through L1; a global-memory group has them in its layout
+    TK* lu = KIND != kCtaGroup
+                 ? reinterpret_cast<TK*>(base + lay.lu)
+                 : reinterpret_cast<TK*>(a.lu_scratch + (size_t)blockIdx.x * (size_t)a.lu_stride);
     double* Z = reinterpret_cast<double*>(base + lay.Z);
     float2* ZZ = reinterpret_cast<float2*>(base + lay.ZZ);
     TK* H = reinterpret_cast<TK*>(base + lay.H);
@@ -707,7 +892,12 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
         for (int q = rank; q < lay.ntab; q += gsize) tabk[q] = (TK)tabd[q];
         if (rank == 0) convert_consts<TK>(*cd, ck);
     }
-    pcr_setup<N, TK, RMAX>(s, tabd, *cd, lu, rank, gsize, gm);
+    if constexpr (KIND == kMemGroup) {
+        gsync<WARP>(gm);
+        pcr_setup_mem<N, TK>(s, tabd, *cd, lu, reinterpret_cast<double*>(base + lay.scr), rank, gsize, gm);
+    } else {
+        pcr_setup<N, TK, RMAX>(s, tabd, *cd, lu, rank, gsize, gm);
+    }
 
     // 2. H = F(G)/V^2 on the rate grid (FP64), Z from the state or zero
     for (int tr = rank; tr < s.Lr; tr += gsize) {
@@ -772,7 +962,7 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
             K0[J] = k0;
         }
         gsync<WARP>(gm);
-        sweeps_into<N, TK, RMAX, WARP>(s, luc, K0, Kw, rank, gsize, gm);
+        sweeps_into<N, TK, KIND>(s, luc, K0, Kw, rank, gsize, gm);
         // refinement: Khat = 2 K^(0) - K^(N) + theta dt F(K^(N))
         if constexpr (DIFF) {
             diff_pass<N>(s, (const double*)Kw, Dd, Lp, rank, gsize);
@@ -793,15 +983,15 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
         }
         gsync<WARP>(gm);
         // N solves into K1; the last one also forms the stage-2 argument
-        sweep<N, TK, RMAX>(s, 0, luc, K0, K1, rank, gsize, gm, NoEpi());
+        lsweep<N, TK, KIND>(s, 0, luc, K0, K1, rank, gsize, gm, NoEpi());
         gsync<WARP>(gm);
         for (int ax = 1; ax < N; ++ax) {
             if (!MIXED && ax == N - 1) {  // FP64: Kw = Z + a21 K1
-                sweep<N, TK, RMAX>(s, ax, luc, K1, K1, rank, gsize, gm, [=](int J, TK x) {
+                lsweep<N, TK, KIND>(s, ax, luc, K1, K1, rank, gsize, gm, [=](int J, TK x) {
                     Kw[J] = (TK)(Z[J] + kA21 * (double)x);
                 });
             } else {
-                sweep<N, TK, RMAX>(s, ax, luc, K1, K1, rank, gsize, gm, NoEpi());
+                lsweep<N, TK, KIND>(s, ax, luc, K1, K1, rank, gsize, gm, NoEpi());
             }
             gsync<WARP>(gm);
         }
@@ -836,7 +1026,7 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
             }
         }
         gsync<WARP>(gm);
-        sweeps_into<N, TK, RMAX, WARP>(s, luc, K0, Kw, rank, gsize, gm);
+        sweeps_into<N, TK, KIND>(s, luc, K0, Kw, rank, gsize, gm);
         if constexpr (DIFF) {
             diff_pass<N>(s, (const double*)Kw, Dd, Lp, rank, gsize);
             gsync<WARP>(gm);
@@ -858,13 +1048,13 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
         // N solves in place; the last one accumulates Y_{n+1} = Y_n + b1 K1 + b2 K2
         for (int ax = 0; ax < N; ++ax) {
             if (ax == N - 1) {
-                sweep<N, TK, RMAX>(s, ax, luc, K0, K0, rank, gsize, gm, [=](int J, TK x) {
+                lsweep<N, TK, KIND>(s, ax, luc, K0, K0, rank, gsize, gm, [=](int J, TK x) {
                     const double z = fma(kB2, (double)x, fma(kB1, (double)K1[J], Z[J]));
                     Z[J] = z;
                     if constexpr (MIXED) ZZ[J] = split_df(z);
                 });
             } else {
-                sweep<N, TK, RMAX>(s, ax, luc, K0, K0, rank, gsize, gm, NoEpi());
+                lsweep<N, TK, KIND>(s, ax, luc, K0, K0, rank, gsize, gm, NoEpi());
             }
             gsync<WARP>(gm);
         }
@@ -925,11 +1115,11 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
 // chunks of 32 >> glog grids from each class's counter until it is exhausted,
 // then moves on, so classes of uneven instances share one launch and no warp
 // waits for another.
-template <int N, bool MIXED, bool WARP>
-__global__ void __launch_bounds__(WARP ? 128 : kCtaMaxThreads) solve_kernel(SolveArgs a)
+template <int N, bool MIXED, int KIND>
+__global__ void __launch_bounds__(KIND == kWarpGroup ? 128 : kCtaMaxThreads) solve_kernel(SolveArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    if constexpr (WARP) {
+    if constexpr (KIND == kWarpGroup) {
         const int warp = threadIdx.x >> 5;
         const int lane = threadIdx.x & 31;
         unsigned char* wbase = smem + (size_t)warp * (size_t)a.smem_warp;
@@ -948,10 +1138,13 @@ __global__ void __launch_bounds__(WARP ? 128 : kCtaMaxThreads) solve_kernel(Solv
                 const Item it = a.items[cd.item_begin + item];
                 const int gsize = 1 << cd.glog;
                 unsigned char* base = wbase + (size_t)(lane >> cd.glog) * (size_t)cd.smem_group;
-                solve_item<N, MIXED, true>(a, it, base, lane & (gsize - 1), gsize);
+                solve_item<N, MIXED, kWarpGroup>(a, it, base, lane & (gsize - 1), gsize);
             }
         }
     } else {
+        // CTA groups: the grid in shared memory; global-memory groups: in the
+        // block's slice of the scratch array
+        unsigned char* base = KIND == kMemGroup ? a.lu_scratch + (size_t)blockIdx.x * (size_t)a.lu_stride : smem;
         __shared__ int s_item;
         for (;;) {
             if (threadIdx.x == 0) s_item = atomicAdd(a.queue, 1);
@@ -960,32 +1153,44 @@ __global__ void __launch_bounds__(WARP ? 128 : kCtaMaxThreads) solve_kernel(Solv
             __syncthreads();
             if (item >= a.n_items) break;
             const Item it = a.items[item];
-            solve_item<N, MIXED, false>(a, it, smem, (int)threadIdx.x, (int)blockDim.x);
+            solve_item<N, MIXED, KIND>(a, it, base, (int)threadIdx.x, (int)blockDim.x);
         }
     }
 }
 
 // Host launch / occupancy helpers, instantiated once per N.
 template <int N>
-int launch_impl(const SolveArgs& a, bool mixed, bool warp, int block, int grid, size_t smem,
-                void* stream)
+const void* kernel_for(bool mixed, int kind)
+{
+    if (kind == kWarpGroup)
+        return mixed ? (const void*)solve_kernel<N, true, kWarpGroup> : (const void*)solve_kernel<N, false, kWarpGroup>;
+    if (kind == kCtaGroup)
+        return mixed ? (const void*)solve_kernel<N, true, kCtaGroup> : (const void*)solve_kernel<N, false, kCtaGroup>;
+    return mixed ? (const void*)solve_kernel<N, true, kMemGroup> : (const void*)solve_kernel<N, false, kMemGroup>;
+}
+
+template <int N>
+int launch_impl(const SolveArgs& a, bool mixed, int kind, int block, int grid, size_t smem, void* stream)
 {
     cudaStream_t st = (cudaStream_t)stream;
-    if (mixed && warp) solve_kernel<N, true, true><<<grid, block, smem, st>>>(a);
-    else if (mixed) solve_kernel<N, true, false><<<grid, block, smem, st>>>(a);
-    else if (warp) solve_kernel<N, false, true><<<grid, block, smem, st>>>(a);
-    else solve_kernel<N, false, false><<<grid, block, smem, st>>>(a);
+    if (kind == kWarpGroup) {
+        if (mixed) solve_kernel<N, true, kWarpGroup><<<grid, block, smem, st>>>(a);
+        else solve_kernel<N, false, kWarpGroup><<<grid, block, smem, st>>>(a);
+    } else if (kind == kCtaGroup) {
+        if (mixed) solve_kernel<N, true, kCtaGroup><<<grid, block, smem, st>>>(a);
+        else solve_kernel<N, false, kCtaGroup><<<grid, block, smem, st>>>(a);
+    } else {
+        if (mixed) solve_kernel<N, true, kMemGroup><<<grid, block, smem, st>>>(a);
+        else solve_kernel<N, false, kMemGroup><<<grid, block, smem, st>>>(a);
+    }
     return (int)cudaGetLastError();
 }
 
 template <int N>
-int occupancy_impl(bool mixed, bool warp, int block, size_t smem)
+int occupancy_impl(bool mixed, int kind, int block, size_t smem)
 {
     int nb = 0;
-    const void* f = mixed ? (warp ? (const void*)solve_kernel<N, true, true>
-                                  : (const void*)solve_kernel<N, true, false>)
-                          : (warp ? (const void*)solve_kernel<N, false, true>
-                                  : (const void*)solve_kernel<N, false, false>);
+    const void* f = kernel_for<N>(mixed, kind);
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, block, smem) != cudaSuccess) return 0;
@@ -996,9 +1201,9 @@ int occupancy_impl(bool mixed, bool warp, int block, size_t smem)
 
 #define AMFRW_INSTANTIATE(NN)                                                               \
     namespace amfrw {                                                                       \
-    int launch_n##NN(const SolveArgs& a, bool m, bool w, int b, int g, size_t s, void* st)  \
+    int launch_n##NN(const SolveArgs& a, bool m, int k, int b, int g, size_t s, void* st)   \
     {                                                                                       \
-        return launch_impl<NN>(a, m, w, b, g, s, st);                                       \
+        return launch_impl<NN>(a, m, k, b, g, s, st);                                       \
     }                                                                                       \
-    int occupancy_n##NN(bool m, bool w, int b, size_t s) { return occupancy_impl<NN>(m, w, b, s); } \
+    int occupancy_n##NN(bool m, int k, int b, size_t s) { return occupancy_impl<NN>(m, k, b, s); } \
     }
