@@ -553,7 +553,8 @@ def paper_instance(n_rates, psi, steps, fmax, level):
 
 def run_paper(args, local_rank):
     """Each table's rows in order of level until the next row would exceed the
-    remaining budget (its cost estimated from the previous row's growth)."""
+    table's share of the budget (its cost estimated from the previous row's
+    growth)."""
     import torch
 
     from paper_2408_00559_gb300 import _lib as L
@@ -562,9 +563,9 @@ def run_paper(args, local_rank):
     BLD.build()
     torch.cuda.set_device(local_rank)
     stream = torch.cuda.Stream()
-    left = args.budget
     rows = []
     for table, nr, psi, steps, fmax, levels in PAPER_ROWS:
+        left = args.budget / len(PAPER_ROWS)  # each table gets its share
         prev = None
         for level, bps, cpu_s in levels:
             est = prev * 4.5 if prev is not None else 1.0
