@@ -356,6 +356,34 @@ def run_ours(args, rank, world, local_rank):
     assert np.array_equal(host_prices, prices.cpu().numpy()), "e2e prices differ from the device run"
     batch.close()
 
+    # the same instances in mixed precision (FP32 F and line solves, FP64
+    # accumulation, interpolation and combination), timed the same way; every
+    # price is compared with the FP64 price of the same instance
+    variants = {}
+    if args.workload == "c2" and rank == 0:
+        p64 = prices.cpu().numpy()
+        mb = L.Batch([dict(x, precision="mixed") for x in insts], stream=stream)
+        pm = torch.empty(B, dtype=torch.float64, device=dev)
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                mb.run(pm.data_ptr())
+            stream.synchronize()
+            mev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(args.steps)]
+            for k in range(args.steps):
+                flush.fill_(k & 0xFF)
+                mev[k][0].record(stream)
+                mb.run(pm.data_ptr())
+                mev[k][1].record(stream)
+            torch.cuda.synchronize()
+        m_s = sum(a.elapsed_time(b) for a, b in mev) / 1e3
+        rel = np.abs(pm.cpu().numpy() - p64) / np.maximum(np.abs(p64), 1e-300)
+        mb.close()
+        variants["c2_mixed"] = {
+            "value": B * args.steps / m_s, "unit": UNIT, "dtype": "f32+f64",
+            "max_rel_err_vs_fp64": float(rel.max()), "instances_checked": int(B),
+            "within_1e-5": float(np.mean(rel <= 1e-5)), "speedup_vs_fp64": (B * args.steps / m_s) / value}
+
     if rank != 0:
         return
     clocks = clk.summary()
@@ -380,6 +408,7 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": n_launch * args.steps,
         "clocks": clocks,
         "parity": check,
+        "variants": variants,
     }
     print(json.dumps(line), flush=True)
 
