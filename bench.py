@@ -81,6 +81,8 @@ def parse():
     ap.add_argument("--queries", type=int, default=1 << 20, help="c5: queries served")
     ap.add_argument("--epochs", type=int, default=130, help="c5: training epochs")
     ap.add_argument("--budget", type=float, default=300.0, help="paper: GPU seconds to spend")
+    ap.add_argument("--only", default=None,
+                    help="paper: one row, TABLE:LEVEL[:STEPS] (e.g. sg_d4:12:8), for profiling")
     return ap.parse_args()
 
 
@@ -593,8 +595,14 @@ def run_paper(args, local_rank):
     torch.cuda.set_device(local_rank)
     stream = torch.cuda.Stream()
     rows = []
-    for table, nr, psi, steps, fmax, levels in PAPER_ROWS:
-        left = args.budget / len(PAPER_ROWS)  # each table gets its share
+    todo = PAPER_ROWS
+    if args.only:
+        parts = args.only.split(":")
+        todo = [(t, nr, psi, st, fm, [r for r in lv if r[0] == int(parts[1])])
+                for t, nr, psi, st, fm, lv in PAPER_ROWS
+                if t == parts[0] and (len(parts) < 3 or st == int(parts[2]))][:1]
+    for table, nr, psi, steps, fmax, levels in todo:
+        left = args.budget / len(todo)  # each table gets its share
         prev = None
         for level, bps, cpu_s in levels:
             est = prev * 4.5 if prev is not None else 1.0
