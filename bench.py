@@ -379,12 +379,30 @@ def run_ours(args, rank, world, local_rank):
                 mev[k][1].record(stream)
             torch.cuda.synchronize()
         m_s = sum(a.elapsed_time(b) for a, b in mev) / 1e3
-        rel = np.abs(pm.cpu().numpy() - p64) / np.maximum(np.abs(p64), 1e-300)
+        pmix = pm.cpu().numpy()
+        rel = np.abs(pmix - p64) / np.maximum(np.abs(p64), 1e-300)
         mb.close()
+        within = float(np.mean(rel <= 1e-5))
+        # instances beyond 1e-5: the error against the combination's own scale
+        # sum_l |c_l u_l| (from the FP64 grid values), which a price that nearly
+        # cancels makes much larger than |price|
+        worst = []
+        for i in np.argsort(-rel)[:4]:
+            if rel[i] <= 1e-5:
+                break
+            pr = L.Problem(insts[i], stream=stream)
+            pr.step(insts[i]["n_steps"])
+            _, cf = pr.grid_info()
+            scale = float(np.sum(np.abs(np.asarray(cf) * pr.grid_values())))
+            pr.close()
+            worst.append({"instance": int(i), "price_fp64": float(p64[i]), "rel_err": float(rel[i]),
+                          "combination_scale": scale,
+                          "err_rel_to_scale": float(abs(pmix[i] - p64[i]) / scale)})
+        mval = B * args.steps / m_s
         variants["c2_mixed"] = {
-            "value": B * args.steps / m_s, "unit": UNIT, "dtype": "f32+f64",
+            "value": mval, "value_at_1e-5": mval * within, "unit": UNIT, "dtype": "f32+f64",
             "max_rel_err_vs_fp64": float(rel.max()), "instances_checked": int(B),
-            "within_1e-5": float(np.mean(rel <= 1e-5)), "speedup_vs_fp64": (B * args.steps / m_s) / value}
+            "within_1e-5": within, "beyond_1e-5": worst, "speedup_vs_fp64": mval / value}
 
     if rank != 0:
         return
