@@ -690,6 +690,9 @@ __device__ __forceinline__ void sweep_mem(const Shape<N>& s, int axis, const T* 
         const int cls = (axis == N - 1) ? 0 : ((t0 >> shV) & MV1);
         const T* tb = lu + s.luoff[axis] + (cls * M + p) * S;
         const int PS = P * S, PSp = P * Spa;
+        // Loads run ahead of their use (rows two ahead, factors one ahead) so
+        // that a lane does not wait a full memory round trip per row; every
+        // load of a row precedes, in program order, the store that replaces it.
         const T* in = src;
         for (int k = 0; k < plog; ++k) {
             const int d = 1 << k;
@@ -698,31 +701,52 @@ __device__ __forceinline__ void sweep_mem(const Shape<N>& s, int axis, const T* 
             const bool send_next = p < d;
             T prev = T(0);
             T cur = act ? in[J0] : T(0);
+            T nxt = (act && R > 1) ? in[J0 + PSp] : T(0);
+            T al = act ? tb[2 * k] : T(0), ga = act ? tb[2 * k + 1] : T(0);
             for (int q = 0; q < R; ++q) {
-                const T nxt = (act && q + 1 < R) ? in[J0 + (q + 1) * PSp] : T(0);
+                const T nn = (act && q + 2 < R) ? in[J0 + (q + 2) * PSp] : T(0);
+                const bool more = act && q + 1 < R;
+                const T al_n = more ? tb[(q + 1) * PS + 2 * k] : T(0);
+                const T ga_n = more ? tb[(q + 1) * PS + 2 * k + 1] : T(0);
                 const T vm = shfl(send_prev ? prev : cur, sm, P, gm);
                 const T vp = shfl(send_next ? nxt : cur, sp, P, gm);
-                const T* row = tb + q * PS;
-                if (act) dst[J0 + q * PSp] = cur - row[2 * k] * vm - row[2 * k + 1] * vp;
+                if (act) dst[J0 + q * PSp] = cur - al * vm - ga * vp;
                 prev = cur;
                 cur = nxt;
+                nxt = nn;
+                al = al_n;
+                ga = ga_n;
             }
             in = dst;  // later levels in place
         }
         if (act) {
+            const T* th = tb + 2 * plog;  // Thomas factors (lower, 1/pivot, upper/pivot) of row q at q PS
             T y = T(0);
+            T x = in[J0], lo = th[0], iv = th[1];
+            T x1 = R > 1 ? in[J0 + PSp] : T(0);
             for (int q = 0; q < R; ++q) {
-                const T* row = tb + q * PS + 2 * plog;
-                y = (in[J0 + q * PSp] - row[0] * y) * row[1];
+                const T x2 = q + 2 < R ? in[J0 + (q + 2) * PSp] : T(0);
+                const T lo_n = q + 1 < R ? th[(q + 1) * PS] : T(0);
+                const T iv_n = q + 1 < R ? th[(q + 1) * PS + 1] : T(0);
+                y = (x - lo * y) * iv;
                 dst[J0 + q * PSp] = y;
+                x = x1;
+                x1 = x2;
+                lo = lo_n;
+                iv = iv_n;
             }
             int J = J0 + (R - 1) * PSp;
             epi(J, y);
+            T b = R > 1 ? dst[J0 + (R - 2) * PSp] : T(0), g = R > 1 ? th[(R - 2) * PS + 2] : T(0);
             for (int q = R - 2; q >= 0; --q) {
+                const T b_n = q > 0 ? dst[J0 + (q - 1) * PSp] : T(0);
+                const T g_n = q > 0 ? th[(q - 1) * PS + 2] : T(0);
                 J = J0 + q * PSp;
-                y = dst[J] - tb[q * PS + 2 * plog + 2] * y;
+                y = b - g * y;
                 dst[J] = y;
                 epi(J, y);
+                b = b_n;
+                g = g_n;
             }
         }
     }
