@@ -849,6 +849,23 @@ __device__ void convert_consts(const Consts<double>& a, Consts<T>* b)
     }
 }
 
+// Mixed mode keeps, beside the FP64 accumulation of Z, the unevaluated pair
+// hi + lo that the stencil of F(Y_n) reads.  It is advanced with the same two
+// increments by error-free transformations in FP32 (Knuth's TwoSum; the
+// product error c*x - fl(c*x) by one FMA), so it follows Z to the pair's
+// precision without converting Z every step.  The _rn intrinsics keep the
+// compiler from contracting the products into the sums.
+__device__ __forceinline__ float2 ff_axpy(float2 z, float c, float x)
+{
+    const float p = __fmul_rn(c, x);
+    const float pe = __fmaf_rn(c, x, -p);
+    const float s = __fadd_rn(z.x, p);
+    const float bb = __fsub_rn(s, z.x);
+    const float e = __fadd_rn(__fadd_rn(__fsub_rn(z.x, __fsub_rn(s, bb)), __fsub_rn(p, bb)), __fadd_rn(z.y, pe));
+    const float hi = __fadd_rn(s, e);
+    return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, s)));
+}
+
 __device__ __forceinline__ float2 split_df(double z)
 {
     const float hi = __double2float_rn(z);
@@ -1075,7 +1092,8 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
                 lsweep<N, TK, KIND>(s, ax, luc, K0, K0, rank, gsize, gm, [=](int J, TK x) {
                     const double z = fma(kB2, (double)x, fma(kB1, (double)K1[J], Z[J]));
                     Z[J] = z;
-                    if constexpr (MIXED) ZZ[J] = split_df(z);
+                    if constexpr (MIXED)
+                        ZZ[J] = ff_axpy(ff_axpy(ZZ[J], (float)kB1, (float)K1[J]), (float)kB2, (float)x);
                 });
             } else {
                 lsweep<N, TK, KIND>(s, ax, luc, K0, K0, rank, gsize, gm, NoEpi());
