@@ -160,29 +160,6 @@ __device__ __forceinline__ double payoff_at(const Shape<N>& s, const double* pay
     return payoff_at<N>(s.poff, s.phalf, pay, payoff, jj);
 }
 
-template <int N>
-struct PaySrc {  // the payoff G on every node, Outer included
-    using V = double;
-    int poff[N];  // copies, so that the grid's shape never has its address taken
-    int phalf;
-    const double* pay;
-    int payoff;
-    int j[N];
-    __device__ __forceinline__ double at(int i, int si, int k, int sk) const
-    {
-        int jj[N];
-#pragma unroll
-        for (int r = 0; r < N; ++r) jj[r] = j[r] + (r == i ? si : 0) + (r == k ? sk : 0);
-        return payoff_at<N>(poff, phalf, pay, payoff, jj);
-    }
-    __device__ __forceinline__ V ctr(int) const { return at(-1, 0, -1, 0); }
-    __device__ __forceinline__ V nb(int, int, bool, int i, int si, int k, int sk) const
-    {
-        return at(i, si, k, sk);
-    }
-    __device__ static __forceinline__ double diff(V a, V b) { return a - b; }
-};
-
 // -------------------------------------------------------------- the stencil
 // Sketch 1 at the Inner node with multi-index j, divided by V^2 (every
 // coefficient of eqs. coef_diff, coef_mix, coef_adv carries F_N^2 = V^2):
@@ -234,6 +211,101 @@ __device__ __forceinline__ TC stencil_acc(const Shape<N>& s, const int (&j)[N], 
         }
         if (i >= 1) {  // drift of rates 2..N-1 (eq. coef_adv), sum over rates 2..i
             TC S = TC(0);
+#pragma unroll
+            for (int r = 1; r <= i; ++r) S += c.rh[ltri(i, r)] * tab[s.toff[r] + 2 * s.M[r] + j[r] - 1];
+            inner += S * c.g2[i] * grad[i];
+        }
+        acc += tab[s.toff[i] + s.M[i] + j[i] - 1] * inner;
+    }
+    return acc;
+}
+
+// ------------------------------------------------- the stencil of the payoff
+// H = F(G)/V^2 at the rate multi-index j: Sketch 1 applied to the payoff G,
+// computed once per grid in FP64.  G does not depend on V, so every term that
+// differentiates along V vanishes and is skipped; the remaining terms use the
+// same coefficients, Neumann reflections and upper-face rules as stencil_acc.
+// Neighbour values come from the centre node in O(1) each: with
+// a_r = tau_r (F_r - K), b_r = 1/(1 + tau_r F_r) and the swaption payoff
+// S = sum_r a_r prod_{l<=r} b_l, the prefix products Pp_r = prod_{l<r} b_l,
+// prefix sums L_r = sum_{l<r} a_l Pp_{l+1} and suffix sums
+// T_r = b_r (a_r + T_{r+1}) give, for a change of rate i to (a', b'),
+// S' = L_i + Pp_i b' (a' + T_{i+1}), and for rates i < k
+// S'' = L_i + Pp_i b_i' (a_i' + M + Q b_k' (a_k' + T_{k+1})) with
+// Q = prod_{i<l<k} b_l and M = sum_{i<r<k} a_r prod_{i<l<=r} b_l.
+template <int N>
+__device__ __noinline__ double payoff_H(const Shape<N>& s, const double* pay, int payoff, const int (&j)[N],
+                           const double* __restrict__ tab, const Consts<double>& c)
+{
+    constexpr int n = N - 1;  // rate axes
+    const double* A = pay;
+    const double* Bv = pay + s.phalf;
+    if (payoff == 0) {  // caplet: G = (F_1 - K)^+ depends on rate 1 only
+        const int o = s.poff[0] + j[0];
+        const double x0 = fmax(A[o], 0.0);
+        const double m = fmax(A[o - 1], 0.0);
+        const double p = (j[0] == s.M[0]) ? m : fmax(A[o + 1], 0.0);
+        return tab[s.toff[0] + j[0] - 1] * ((p - x0) - (x0 - m));
+    }
+    double a[n], b[n], Pp[n + 1], L[n + 1], T[n + 1];
+#pragma unroll
+    for (int r = 0; r < n; ++r) {
+        a[r] = A[s.poff[r] + j[r]];
+        b[r] = Bv[s.poff[r] + j[r]];
+    }
+    Pp[0] = 1.0;
+    L[0] = 0.0;
+#pragma unroll
+    for (int r = 0; r < n; ++r) {
+        Pp[r + 1] = Pp[r] * b[r];
+        L[r + 1] = L[r] + a[r] * Pp[r + 1];
+    }
+    T[n] = 0.0;
+#pragma unroll
+    for (int r = n - 1; r >= 0; --r) T[r] = b[r] * (a[r] + T[r + 1]);
+    const double x0 = fmax(T[0], 0.0);
+    double lap[n], grad[n];
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        const int o = s.poff[i] + j[i];
+        const bool top = j[i] == s.M[i];
+        const double m = fmax(L[i] + Pp[i] * Bv[o - 1] * (A[o - 1] + T[i + 1]), 0.0);
+        const double p = top ? m : fmax(L[i] + Pp[i] * Bv[o + 1] * (A[o + 1] + T[i + 1]), 0.0);
+        const double dp = p - x0;
+        const double dm = x0 - m;
+        lap[i] = dp - dm;
+        grad[i] = top ? 0.0 : dp + dm;
+    }
+    double acc = 0.0;
+#pragma unroll
+    for (int i = 0; i < n; ++i) acc += tab[s.toff[i] + j[i] - 1] * lap[i];
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        double inner = 0.0;
+        if (j[i] != s.M[i]) {
+            const int oi = s.poff[i] + j[i];
+            double Q = 1.0, Mm = 0.0;
+#pragma unroll
+            for (int k = i + 1; k < n; ++k) {
+                if (j[k] != s.M[k]) {
+                    const int ok = s.poff[k] + j[k];
+                    const double tk = T[k + 1];
+                    const double kp = Q * Bv[ok + 1] * (A[ok + 1] + tk);
+                    const double km = Q * Bv[ok - 1] * (A[ok - 1] + tk);
+                    const double ip = Pp[i] * Bv[oi + 1], im = Pp[i] * Bv[oi - 1];
+                    const double pp = fmax(L[i] + ip * (A[oi + 1] + Mm + kp), 0.0);
+                    const double pm = fmax(L[i] + ip * (A[oi + 1] + Mm + km), 0.0);
+                    const double mp = fmax(L[i] + im * (A[oi - 1] + Mm + kp), 0.0);
+                    const double mm = fmax(L[i] + im * (A[oi - 1] + Mm + km), 0.0);
+                    const double mix = (pp - pm) - (mp - mm);
+                    inner += c.rm[upair(i, k)] * tab[s.toff[k] + s.M[k] + j[k] - 1] * mix;
+                }
+                Q *= b[k];
+                Mm += a[k] * Q;
+            }
+        }
+        if (i >= 1) {  // drift of rates 2..N-1 (eq. coef_adv), sum over rates 2..i
+            double S = 0.0;
 #pragma unroll
             for (int r = 1; r <= i; ++r) S += c.rh[ltri(i, r)] * tab[s.toff[r] + 2 * s.M[r] + j[r] - 1];
             inner += S * c.g2[i] * grad[i];
@@ -942,14 +1014,9 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
 
     // 2. H = F(G)/V^2 on the rate grid (FP64), Z from the state or zero
     for (int tr = rank; tr < s.Lr; tr += gsize) {
-        PaySrc<N> ps;
-#pragma unroll
-        for (int i = 0; i < N; ++i) ps.poff[i] = s.poff[i];
-        ps.phalf = s.phalf;
-        ps.pay = pay;
-        ps.payoff = P.payoff;
-        decode<N>(s, tr, ps.j);
-        H[tr] = (TK)stencil_acc<N, double>(s, ps.j, 0, ps, tabd, *cd);
+        int j[N];
+        decode<N>(s, tr, j);
+        H[tr] = (TK)payoff_H<N>(s, pay, P.payoff, j, tabd, *cd);
     }
     for (int t = rank; t < s.L; t += gsize) {
         const int J = s.padded(t);
@@ -1158,7 +1225,7 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
 // then moves on, so classes of uneven instances share one launch and no warp
 // waits for another.
 template <int N, bool MIXED, int KIND>
-__global__ void __launch_bounds__(KIND == kWarpGroup ? 128 : kCtaMaxThreads) solve_kernel(SolveArgs a)
+__global__ void __launch_bounds__(KIND == kWarpGroup ? 128 : kCtaMaxThreads, KIND == kWarpGroup ? 3 : (KIND == kMemGroup ? 2 : 1)) solve_kernel(SolveArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     if constexpr (KIND == kWarpGroup) {
