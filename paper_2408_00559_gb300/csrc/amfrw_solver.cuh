@@ -148,7 +148,7 @@ __device__ __forceinline__ double payoff_at(const int (&poff)[N], int phalf, con
 #pragma unroll
     for (int r = 0; r < N - 1; ++r) {
         P *= pay[phalf + poff[r] + jj[r]];
-        sum += pay[poff[r] + jj[r]] * P;
+        sum = fma(pay[poff[r] + jj[r]], P, sum);
     }
     return fmax(sum, 0.0);
 }
@@ -225,17 +225,16 @@ __device__ __forceinline__ TC stencil_acc(const Shape<N>& s, const int (&j)[N], 
 // computed once per grid in FP64.  G does not depend on V, so every term that
 // differentiates along V vanishes and is skipped; the remaining terms use the
 // same coefficients, Neumann reflections and upper-face rules as stencil_acc.
-// Neighbour values come from the centre node in O(1) each: with
-// a_r = tau_r (F_r - K), b_r = 1/(1 + tau_r F_r) and the swaption payoff
-// S = sum_r a_r prod_{l<=r} b_l, the prefix products Pp_r = prod_{l<r} b_l,
-// prefix sums L_r = sum_{l<r} a_l Pp_{l+1} and suffix sums
-// T_r = b_r (a_r + T_{r+1}) give, for a change of rate i to (a', b'),
-// S' = L_i + Pp_i b' (a' + T_{i+1}), and for rates i < k
-// S'' = L_i + Pp_i b_i' (a_i' + M + Q b_k' (a_k' + T_{k+1})) with
-// Q = prod_{i<l<k} b_l and M = sum_{i<r<k} a_r prod_{i<l<=r} b_l.
+// A neighbour differs from the centre in one or two rates, so its swaption
+// payoff sum_r a_r prod_{l<=r} b_l (a_r = tau_r (F_r - K),
+// b_r = 1/(1 + tau_r F_r)) starts from the centre's partial product and sum
+// just before the first changed rate and finishes the same forward loop as
+// payoff_at: every value is bitwise the one payoff_at gives (second
+// differences over fine axes amplify any rounding difference by 1/h^2), at a
+// fraction of the cost.
 template <int N>
 __device__ __noinline__ double payoff_H(const Shape<N>& s, const double* pay, int payoff, const int (&j)[N],
-                           const double* __restrict__ tab, const Consts<double>& c)
+                                        const double* __restrict__ tab, const Consts<double>& c)
 {
     constexpr int n = N - 1;  // rate axes
     const double* A = pay;
@@ -247,30 +246,38 @@ __device__ __noinline__ double payoff_H(const Shape<N>& s, const double* pay, in
         const double p = (j[0] == s.M[0]) ? m : fmax(A[o + 1], 0.0);
         return tab[s.toff[0] + j[0] - 1] * ((p - x0) - (x0 - m));
     }
-    double a[n], b[n], Pp[n + 1], L[n + 1], T[n + 1];
+    double a[n], b[n], P0[n], S0[n];  // P0[r], S0[r]: product and sum before rate r
+    double P = 1.0, S = 0.0;
 #pragma unroll
     for (int r = 0; r < n; ++r) {
         a[r] = A[s.poff[r] + j[r]];
         b[r] = Bv[s.poff[r] + j[r]];
+        P0[r] = P;
+        S0[r] = S;
+        P *= b[r];
+        S = fma(a[r], P, S);
     }
-    Pp[0] = 1.0;
-    L[0] = 0.0;
+    const double x0 = fmax(S, 0.0);
+    // payoff with rate i at table offset oi (and rate k > i at ok; k < 0: none)
+    auto g = [&](int i, int oi, int k, int ok) {
+        double p = P0[i] * Bv[oi];
+        double q = fma(A[oi], p, S0[i]);
 #pragma unroll
-    for (int r = 0; r < n; ++r) {
-        Pp[r + 1] = Pp[r] * b[r];
-        L[r + 1] = L[r] + a[r] * Pp[r + 1];
-    }
-    T[n] = 0.0;
-#pragma unroll
-    for (int r = n - 1; r >= 0; --r) T[r] = b[r] * (a[r] + T[r + 1]);
-    const double x0 = fmax(T[0], 0.0);
+        for (int r = 0; r < n; ++r) {
+            if (r <= i) continue;
+            const bool ch = r == k;
+            p *= ch ? Bv[ok] : b[r];
+            q = fma(ch ? A[ok] : a[r], p, q);
+        }
+        return fmax(q, 0.0);
+    };
     double lap[n], grad[n];
 #pragma unroll
     for (int i = 0; i < n; ++i) {
         const int o = s.poff[i] + j[i];
         const bool top = j[i] == s.M[i];
-        const double m = fmax(L[i] + Pp[i] * Bv[o - 1] * (A[o - 1] + T[i + 1]), 0.0);
-        const double p = top ? m : fmax(L[i] + Pp[i] * Bv[o + 1] * (A[o + 1] + T[i + 1]), 0.0);
+        const double m = g(i, o - 1, -1, 0);
+        const double p = top ? m : g(i, o + 1, -1, 0);
         const double dp = p - x0;
         const double dm = x0 - m;
         lap[i] = dp - dm;
@@ -284,31 +291,24 @@ __device__ __noinline__ double payoff_H(const Shape<N>& s, const double* pay, in
         double inner = 0.0;
         if (j[i] != s.M[i]) {
             const int oi = s.poff[i] + j[i];
-            double Q = 1.0, Mm = 0.0;
 #pragma unroll
             for (int k = i + 1; k < n; ++k) {
                 if (j[k] != s.M[k]) {
                     const int ok = s.poff[k] + j[k];
-                    const double tk = T[k + 1];
-                    const double kp = Q * Bv[ok + 1] * (A[ok + 1] + tk);
-                    const double km = Q * Bv[ok - 1] * (A[ok - 1] + tk);
-                    const double ip = Pp[i] * Bv[oi + 1], im = Pp[i] * Bv[oi - 1];
-                    const double pp = fmax(L[i] + ip * (A[oi + 1] + Mm + kp), 0.0);
-                    const double pm = fmax(L[i] + ip * (A[oi + 1] + Mm + km), 0.0);
-                    const double mp = fmax(L[i] + im * (A[oi - 1] + Mm + kp), 0.0);
-                    const double mm = fmax(L[i] + im * (A[oi - 1] + Mm + km), 0.0);
+                    const double pp = g(i, oi + 1, k, ok + 1);
+                    const double pm = g(i, oi + 1, k, ok - 1);
+                    const double mp = g(i, oi - 1, k, ok + 1);
+                    const double mm = g(i, oi - 1, k, ok - 1);
                     const double mix = (pp - pm) - (mp - mm);
                     inner += c.rm[upair(i, k)] * tab[s.toff[k] + s.M[k] + j[k] - 1] * mix;
                 }
-                Q *= b[k];
-                Mm += a[k] * Q;
             }
         }
         if (i >= 1) {  // drift of rates 2..N-1 (eq. coef_adv), sum over rates 2..i
-            double S = 0.0;
+            double Sd = 0.0;
 #pragma unroll
-            for (int r = 1; r <= i; ++r) S += c.rh[ltri(i, r)] * tab[s.toff[r] + 2 * s.M[r] + j[r] - 1];
-            inner += S * c.g2[i] * grad[i];
+            for (int r = 1; r <= i; ++r) Sd += c.rh[ltri(i, r)] * tab[s.toff[r] + 2 * s.M[r] + j[r] - 1];
+            inner += Sd * c.g2[i] * grad[i];
         }
         acc += tab[s.toff[i] + s.M[i] + j[i] - 1] * inner;
     }
