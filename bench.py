@@ -254,6 +254,29 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ sharding
+def shard_start(rank: int, per_rank: int) -> int:
+    """First instance index of a rank: ranks price disjoint, consecutive blocks
+    of seeded instances (weak scaling, no data-path collective)."""
+    return rank * per_rank
+
+
+def max_over_ranks(seconds: float, world: int, device) -> float:
+    """The job's time is its slowest rank's (one all-reduce of one scalar)."""
+    if world <= 1:
+        return seconds
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, per_rank: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput: every rank's instances over the slowest rank's time."""
+    return world * per_rank * steps / seconds
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -276,7 +299,7 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.Stream(device=dev)
     wl = WORKLOADS[args.workload]
     B = args.batch or wl["batch"]
-    insts = W.batch(args.workload, B, start=rank * B)
+    insts = W.batch(args.workload, B, start=shard_start(rank, B))
     with torch.cuda.stream(stream):
         batch = L.Batch(insts, stream=stream)
         batch.enable_timing(True)
@@ -313,12 +336,8 @@ def run_ours(args, rank, world, local_rank):
         if world > 1:
             dist.barrier()
         step_ms = [s.elapsed_time(e) for s, e in evs]
-    total_s = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = world * B * args.steps / total_s
+    total_s = max_over_ranks(sum(step_ms) / 1e3, world, dev)
+    value = job_rate(world, B, args.steps, total_s)
 
     # dominant kernel: the solver kernel, launched once per (N, grid-size)
     # class; all its launches of one batch together form its work for the batch
@@ -350,11 +369,7 @@ def run_ours(args, rank, world, local_rank):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         L._check(lib.amfrw_solve_batch(m.arr, B, L._dp(host_prices), sptr), "amfrw_solve_batch")
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
     assert np.array_equal(host_prices, prices.cpu().numpy()), "e2e prices differ from the device run"
     batch.close()
 
