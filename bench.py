@@ -79,7 +79,7 @@ def parse():
                          "c5 the surrogate with solver fallback; paper the paper-scale rows")
     ap.add_argument("--train", type=int, default=100_000, help="c5: training prices")
     ap.add_argument("--queries", type=int, default=1 << 20, help="c5: queries served")
-    ap.add_argument("--epochs", type=int, default=130, help="c5: training epochs")
+    ap.add_argument("--epochs", type=int, default=260, help="c5: training epochs")
     ap.add_argument("--budget", type=float, default=300.0, help="paper: GPU seconds to spend")
     ap.add_argument("--only", default=None,
                     help="paper: one row, TABLE:LEVEL[:STEPS] (e.g. sg_d4:12:8), for profiling")
