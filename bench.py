@@ -80,6 +80,7 @@ def parse():
     ap.add_argument("--train", type=int, default=100_000, help="c5: training prices")
     ap.add_argument("--queries", type=int, default=1 << 20, help="c5: queries served")
     ap.add_argument("--epochs", type=int, default=260, help="c5: training epochs")
+    ap.add_argument("--members", type=int, default=4, help="c5: ensemble members")
     ap.add_argument("--budget", type=float, default=300.0, help="paper: GPU seconds to spend")
     ap.add_argument("--only", default=None,
                     help="paper: one row, TABLE:LEVEL[:STEPS] (e.g. sg_d4:12:8), for profiling")
@@ -489,7 +490,7 @@ def run_surrogate(args, rank, world, local_rank):
     audit = [W.c5_instance_from(f, **kw) for f in F_audit]
     y_audit = solve_chunked(audit)
     t_data = time.perf_counter() - t0
-    s = L.Surrogate(members=4, seed=11, stream=stream)
+    s = L.Surrogate(members=args.members, seed=11, stream=stream)
     t0 = time.perf_counter()
     loss = s.fit(train, y_train, epochs=args.epochs, lr=3e-3)
     t_fit = time.perf_counter() - t0
@@ -553,7 +554,7 @@ def run_surrogate(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (network) + f32/f64 (fallback solver)",
         "data": "synthetic",
         "config": {"workload": C5_DESC, "queries_per_step": per, "train": args.train,
-                   "epochs": args.epochs, "members": 4, "rel_bound": 1e-3, "calib_quantile": 0.99,
+                   "epochs": args.epochs, "members": args.members, "rel_bound": 1e-3, "calib_quantile": 0.99,
                    "l2": "queries stream from host memory; every chunk is new data"},
         "surrogate": {"fallback_fraction": fell_total / (per * args.steps),
                       "solver_alone": solver_rate, "speedup_vs_solver": value / solver_rate,
