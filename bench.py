@@ -80,7 +80,7 @@ def parse():
     ap.add_argument("--train", type=int, default=100_000, help="c5: training prices")
     ap.add_argument("--queries", type=int, default=1 << 20, help="c5: queries served")
     ap.add_argument("--epochs", type=int, default=260, help="c5: training epochs")
-    ap.add_argument("--members", type=int, default=4, help="c5: ensemble members")
+    ap.add_argument("--members", type=int, default=8, help="c5: ensemble members")
     ap.add_argument("--budget", type=float, default=300.0, help="paper: GPU seconds to spend")
     ap.add_argument("--only", default=None,
                     help="paper: one row, TABLE:LEVEL[:STEPS] (e.g. sg_d4:12:8), for profiling")
