@@ -391,17 +391,36 @@ amfrw_params params_from(const Family& fam, const double* f, InstanceStore& st)
 
 }  // namespace
 
+// Work buffers of one forward/backward pass: the packed batch, activations,
+// pre-activations and gradients, and the stream the pass runs on.  Prediction
+// and gradient checks use one set on the caller's stream; training gives every
+// member its own set and stream, so the members' steps run concurrently.
+struct SgWork {
+    bf16 *X = nullptr, *Xt = nullptr, *H1 = nullptr, *H2 = nullptr, *H3 = nullptr, *H1t = nullptr, *H2t = nullptr;
+    bf16 *dZ1 = nullptr, *dZ2 = nullptr, *dZ3 = nullptr, *dZ1t = nullptr, *dZ2t = nullptr, *dZ3t = nullptr;
+    float *Z1 = nullptr, *Z2 = nullptr, *Z3 = nullptr, *y = nullptr, *t = nullptr, *dy = nullptr, *loss = nullptr;
+    int* idx = nullptr;  // training: the epoch's permutation of the rows
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    void release()
+    {
+        for (void* q : {(void*)X, (void*)Xt, (void*)H1, (void*)H2, (void*)H3, (void*)H1t, (void*)H2t,
+                        (void*)dZ1, (void*)dZ2, (void*)dZ3, (void*)dZ1t, (void*)dZ2t, (void*)dZ3t,
+                        (void*)Z1, (void*)Z2, (void*)Z3, (void*)y, (void*)t, (void*)dy, (void*)loss, (void*)idx})
+            cudaFree(q);
+        if (own_stream && st) cudaStreamDestroy(st);
+        *this = SgWork{};
+    }
+};
+
 struct amfrw_surrogate {
     int members = 0;
     uint64_t seed = 0;
     cudaStream_t stream = nullptr;
     std::vector<float*> P, G, Mo, Vo;
     std::vector<bf16*> W1b, W2b, W3b, W2tb, W3tb;
-    // work buffers: training batch (kTrainRows) and prediction chunk (kPredRows)
-    bf16 *X = nullptr, *Xt = nullptr, *H1 = nullptr, *H2 = nullptr, *H3 = nullptr, *H1t = nullptr, *H2t = nullptr;
-    bf16 *dZ1 = nullptr, *dZ2 = nullptr, *dZ3 = nullptr, *dZ1t = nullptr, *dZ2t = nullptr, *dZ3t = nullptr;
-    float *Z1 = nullptr, *Z2 = nullptr, *Z3 = nullptr, *y = nullptr, *t = nullptr, *dy = nullptr;
-    float *loss = nullptr, *ys = nullptr;
+    SgWork w;                  // prediction chunk (kPredRows) and gradient checks (kTrainRows)
+    float* ys = nullptr;       // prediction chunk: every member's output
     float *pmean = nullptr, *pspread = nullptr;  // prediction chunk: ensemble mean, spread
     double *pg = nullptr, *dpoly = nullptr;      // prediction chunk: target; control-variate coefficients
     int* err = nullptr;
@@ -419,15 +438,30 @@ struct amfrw_surrogate {
             for (float* q : *v) cudaFree(q);
         for (auto v : {&W1b, &W2b, &W3b, &W2tb, &W3tb})
             for (bf16* q : *v) cudaFree(q);
-        for (void* q : {(void*)X, (void*)Xt, (void*)H1, (void*)H2, (void*)H3, (void*)H1t, (void*)H2t,
-                        (void*)dZ1, (void*)dZ2, (void*)dZ3, (void*)dZ1t, (void*)dZ2t, (void*)dZ3t,
-                        (void*)Z1, (void*)Z2, (void*)Z3, (void*)y, (void*)t, (void*)dy, (void*)loss,
-                        (void*)ys, (void*)err, (void*)pmean, (void*)pspread, (void*)pg, (void*)dpoly})
-            cudaFree(q);
+        w.release();
+        for (void* q : {(void*)ys, (void*)err, (void*)pmean, (void*)pspread, (void*)pg, (void*)dpoly}) cudaFree(q);
     }
 };
 
 namespace {
+
+// Buffers of one pass set: forward rows (activations) and training rows
+// (transposes, pre-activations, gradients).
+int sg_work_alloc(SgWork& w, size_t fwd_rows, size_t train_rows)
+{
+    const size_t B2 = sizeof(bf16), F4 = sizeof(float);
+    SG_CUDA(cudaMalloc(&w.X, B2 * fwd_rows * kInPad));
+    SG_CUDA(cudaMalloc(&w.Xt, B2 * train_rows * kInPad));
+    for (bf16** q : {&w.H1, &w.H2, &w.H3}) SG_CUDA(cudaMalloc(q, B2 * fwd_rows * kW));
+    for (bf16** q : {&w.H1t, &w.H2t, &w.dZ1, &w.dZ2, &w.dZ3, &w.dZ1t, &w.dZ2t, &w.dZ3t})
+        SG_CUDA(cudaMalloc(q, B2 * train_rows * kW));
+    for (float** q : {&w.Z1, &w.Z2, &w.Z3}) SG_CUDA(cudaMalloc(q, F4 * train_rows * kW));
+    SG_CUDA(cudaMalloc(&w.y, F4 * fwd_rows));
+    SG_CUDA(cudaMalloc(&w.t, F4 * train_rows));
+    SG_CUDA(cudaMalloc(&w.dy, F4 * train_rows));
+    SG_CUDA(cudaMalloc(&w.loss, F4));
+    return AMFRW_OK;
+}
 
 int sg_alloc(amfrw_surrogate* s)
 {
@@ -449,16 +483,9 @@ int sg_alloc(amfrw_surrogate* s)
         s->W1b.push_back(w1); s->W2b.push_back(w2); s->W3b.push_back(w3);
         s->W2tb.push_back(w2t); s->W3tb.push_back(w3t);
     }
-    SG_CUDA(cudaMalloc(&s->X, B2 * PQ * kInPad));
-    SG_CUDA(cudaMalloc(&s->Xt, B2 * TR * kInPad));
-    for (bf16** q : {&s->H1, &s->H2, &s->H3}) SG_CUDA(cudaMalloc(q, B2 * PQ * kW));
-    for (bf16** q : {&s->H1t, &s->H2t, &s->dZ1, &s->dZ2, &s->dZ3, &s->dZ1t, &s->dZ2t, &s->dZ3t})
-        SG_CUDA(cudaMalloc(q, B2 * TR * kW));
-    for (float** q : {&s->Z1, &s->Z2, &s->Z3}) SG_CUDA(cudaMalloc(q, F4 * TR * kW));
-    SG_CUDA(cudaMalloc(&s->y, F4 * PQ));
-    SG_CUDA(cudaMalloc(&s->t, F4 * TR));
-    SG_CUDA(cudaMalloc(&s->dy, F4 * TR));
-    SG_CUDA(cudaMalloc(&s->loss, F4));
+    s->w.st = s->stream;
+    int st = sg_work_alloc(s->w, PQ, TR);
+    if (st != AMFRW_OK) return st;
     SG_CUDA(cudaMalloc(&s->ys, F4 * PQ * (size_t)s->members));
     SG_CUDA(cudaMalloc(&s->err, sizeof(int)));
     SG_CUDA(cudaMalloc(&s->pmean, F4 * PR));
@@ -471,60 +498,59 @@ int sg_alloc(amfrw_surrogate* s)
 }
 
 // BF16 weight copies of member m from its FP32 master weights.
-void sg_cast(amfrw_surrogate* s, int m)
+void sg_cast(amfrw_surrogate* s, int m, cudaStream_t st)
 {
-    cudaStream_t st = s->stream;
     cast_kernel<<<cdiv(kW * kInPad, 256), 256, 0, st>>>(s->P[m] + oW1, kW, kInPad, s->W1b[m], nullptr);
     cast_kernel<<<cdiv(kW * kW, 256), 256, 0, st>>>(s->P[m] + oW2, kW, kW, s->W2b[m], s->W2tb[m]);
     cast_kernel<<<cdiv(kW * kW, 256), 256, 0, st>>>(s->P[m] + oW3, kW, kW, s->W3b[m], s->W3tb[m]);
 }
 
-// Forward pass of member m on B packed rows in s->X; output into y.  With
+// Forward pass of member m on B packed rows in w.X; output into y.  With
 // train set, keeps the pre-activations and transposes the backward pass needs.
-int sg_forward(amfrw_surrogate* s, int m, int B, bool train, float* y)
+int sg_forward(amfrw_surrogate* s, int m, int B, bool train, float* y, const SgWork& w)
 {
-    cudaStream_t st = s->stream;
+    cudaStream_t st = w.st;
     tc::Epi e{};
     e.mode = 1;
     e.error = s->err;
     e.ldt = B;
-    e.bias = s->P[m] + ob1; e.Z = train ? s->Z1 : nullptr; e.H = s->H1; e.Ht = train ? s->H1t : nullptr;
-    int rc = tc::gemm(s->X, kInPad, s->W1b[m], kInPad, B, kW, kInPad, e, st);
-    e.bias = s->P[m] + ob2; e.Z = train ? s->Z2 : nullptr; e.H = s->H2; e.Ht = train ? s->H2t : nullptr;
-    if (!rc) rc = tc::gemm(s->H1, kW, s->W2b[m], kW, B, kW, kW, e, st);
-    e.bias = s->P[m] + ob3; e.Z = train ? s->Z3 : nullptr; e.H = s->H3; e.Ht = nullptr;
-    if (!rc) rc = tc::gemm(s->H2, kW, s->W3b[m], kW, B, kW, kW, e, st);
-    if (!rc) out_fwd_kernel<<<cdiv(B * 32, 256), 256, 0, st>>>(s->H3, s->P[m], y, B);
+    e.bias = s->P[m] + ob1; e.Z = train ? w.Z1 : nullptr; e.H = w.H1; e.Ht = train ? w.H1t : nullptr;
+    int rc = tc::gemm(w.X, kInPad, s->W1b[m], kInPad, B, kW, kInPad, e, st);
+    e.bias = s->P[m] + ob2; e.Z = train ? w.Z2 : nullptr; e.H = w.H2; e.Ht = train ? w.H2t : nullptr;
+    if (!rc) rc = tc::gemm(w.H1, kW, s->W2b[m], kW, B, kW, kW, e, st);
+    e.bias = s->P[m] + ob3; e.Z = train ? w.Z3 : nullptr; e.H = w.H3; e.Ht = nullptr;
+    if (!rc) rc = tc::gemm(w.H2, kW, s->W3b[m], kW, B, kW, kW, e, st);
+    if (!rc) out_fwd_kernel<<<cdiv(B * 32, 256), 256, 0, st>>>(w.H3, s->P[m], y, B);
     if (rc) return sg_fail(AMFRW_ECUDA, std::string("surrogate forward: ") + cudaGetErrorString((cudaError_t)rc));
     return AMFRW_OK;
 }
 
-// Loss gradient of member m on the packed batch (targets in s->t) into s->G[m].
-int sg_backward(amfrw_surrogate* s, int m, int B)
+// Loss gradient of member m on the packed batch (targets in w.t) into s->G[m].
+int sg_backward(amfrw_surrogate* s, int m, int B, const SgWork& w)
 {
-    cudaStream_t st = s->stream;
+    cudaStream_t st = w.st;
     float* G = s->G[m];
-    out_bwd_kernel<<<cdiv(B * kW, 256), 256, 0, st>>>(s->y, s->t, s->P[m], s->Z3, B, s->dZ3, s->dZ3t, s->dy, s->loss);
-    out_wgrad_kernel<<<cdiv(kW + 1, 128), 128, 0, st>>>(s->H3, s->dy, B, G);
+    out_bwd_kernel<<<cdiv(B * kW, 256), 256, 0, st>>>(w.y, w.t, s->P[m], w.Z3, B, w.dZ3, w.dZ3t, w.dy, w.loss);
+    out_wgrad_kernel<<<cdiv(kW + 1, 128), 128, 0, st>>>(w.H3, w.dy, B, G);
     tc::Epi e{};
     e.error = s->err;
     e.ldt = B;
     // W3, b3
     e.mode = 0; e.C = G + oW3; e.ldc = kW;
-    int rc = tc::gemm(s->dZ3t, B, s->H2t, B, kW, kW, B, e, st);
-    rowsum_kernel<<<cdiv(kW * 32, 256), 256, 0, st>>>(s->dZ3t, kW, B, G + ob3);
+    int rc = tc::gemm(w.dZ3t, B, w.H2t, B, kW, kW, B, e, st);
+    rowsum_kernel<<<cdiv(kW * 32, 256), 256, 0, st>>>(w.dZ3t, kW, B, G + ob3);
     // dZ2 = (dZ3 W3) * gelu'(Z2)
-    e.mode = 2; e.H = s->dZ2; e.Ht = s->dZ2t; e.Zprev = s->Z2;
-    if (!rc) rc = tc::gemm(s->dZ3, kW, s->W3tb[m], kW, B, kW, kW, e, st);
+    e.mode = 2; e.H = w.dZ2; e.Ht = w.dZ2t; e.Zprev = w.Z2;
+    if (!rc) rc = tc::gemm(w.dZ3, kW, s->W3tb[m], kW, B, kW, kW, e, st);
     e.mode = 0; e.C = G + oW2; e.ldc = kW;
-    if (!rc) rc = tc::gemm(s->dZ2t, B, s->H1t, B, kW, kW, B, e, st);
-    rowsum_kernel<<<cdiv(kW * 32, 256), 256, 0, st>>>(s->dZ2t, kW, B, G + ob2);
+    if (!rc) rc = tc::gemm(w.dZ2t, B, w.H1t, B, kW, kW, B, e, st);
+    rowsum_kernel<<<cdiv(kW * 32, 256), 256, 0, st>>>(w.dZ2t, kW, B, G + ob2);
     // dZ1 = (dZ2 W2) * gelu'(Z1)
-    e.mode = 2; e.H = s->dZ1; e.Ht = s->dZ1t; e.Zprev = s->Z1;
-    if (!rc) rc = tc::gemm(s->dZ2, kW, s->W2tb[m], kW, B, kW, kW, e, st);
+    e.mode = 2; e.H = w.dZ1; e.Ht = w.dZ1t; e.Zprev = w.Z1;
+    if (!rc) rc = tc::gemm(w.dZ2, kW, s->W2tb[m], kW, B, kW, kW, e, st);
     e.mode = 0; e.C = G + oW1; e.ldc = kInPad;
-    if (!rc) rc = tc::gemm(s->dZ1t, B, s->Xt, B, kW, kInPad, B, e, st);
-    rowsum_kernel<<<cdiv(kW * 32, 256), 256, 0, st>>>(s->dZ1t, kW, B, G + ob1);
+    if (!rc) rc = tc::gemm(w.dZ1t, B, w.Xt, B, kW, kInPad, B, e, st);
+    rowsum_kernel<<<cdiv(kW * 32, 256), 256, 0, st>>>(w.dZ1t, kW, B, G + ob1);
     if (rc) return sg_fail(AMFRW_ECUDA, std::string("surrogate backward: ") + cudaGetErrorString((cudaError_t)rc));
     return AMFRW_OK;
 }
@@ -632,9 +658,9 @@ int sg_predict_dev(amfrw_surrogate* s, const float* d_feats, int64_t n, std::vec
     for (int64_t r0 = 0; r0 < n; r0 += kPredRows) {
         const int B = (int)std::min<int64_t>(kPredRows, n - r0);
         const float* z = d_feats + (size_t)r0 * kIn;
-        pack_kernel<<<cdiv(B * kInPad, 256), 256, 0, st>>>(z, nullptr, nullptr, 0, B, s->X, nullptr, nullptr);
+        pack_kernel<<<cdiv(B * kInPad, 256), 256, 0, st>>>(z, nullptr, nullptr, 0, B, s->w.X, nullptr, nullptr);
         for (int m = 0; m < s->members; ++m) {
-            const int rc = sg_forward(s, m, B, false, s->ys + (size_t)m * B);
+            const int rc = sg_forward(s, m, B, false, s->ys + (size_t)m * B, s->w);
             if (rc != AMFRW_OK) return rc;
         }
         ensemble_kernel<<<cdiv(B, 256), 256, 0, st>>>(s->ys, s->members, B, s->pmean, s->pspread);
@@ -757,7 +783,7 @@ int amfrw_surrogate_create(int32_t n_members, uint64_t seed, void* cuda_stream, 
         cudaMemcpyAsync(s->P[m], h.data(), sizeof(float) * kParams, cudaMemcpyHostToDevice, s->stream);
         cudaMemsetAsync(s->Mo[m], 0, sizeof(float) * kParams, s->stream);
         cudaMemsetAsync(s->Vo[m], 0, sizeof(float) * kParams, s->stream);
-        sg_cast(s, m);
+        sg_cast(s, m, s->stream);
     }
     if (cudaStreamSynchronize(s->stream) != cudaSuccess) {
         delete s;
@@ -817,51 +843,90 @@ int amfrw_surrogate_fit(amfrw_surrogate* s, const amfrw_params* ps, const double
     SG_CUDA(cudaMemcpyAsync(s->dpoly, s->poly, sizeof(double) * kPolyTerms, cudaMemcpyHostToDevice, s->stream));
     cudaStream_t st = s->stream;
     float *d_feats = nullptr, *d_targ = nullptr;
-    int* d_idx = nullptr;
     SG_CUDA(cudaMalloc(&d_feats, sizeof(float) * feats.size()));
     SG_CUDA(cudaMalloc(&d_targ, sizeof(float) * n));
-    SG_CUDA(cudaMalloc(&d_idx, sizeof(int) * n));
     cudaMemcpyAsync(d_feats, feats.data(), sizeof(float) * feats.size(), cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(d_targ, targ.data(), sizeof(float) * n, cudaMemcpyHostToDevice, st);
     const int B = kTrainRows;
     const int64_t steps_per_epoch = n / B;
     const int64_t total = steps_per_epoch * epochs;
-    std::vector<int> perm((size_t)n);
+    // every member trains on its own stream with its own work buffers; the
+    // members' steps are issued in turn, so their small kernels overlap
+    const int M = s->members;
+    std::vector<SgWork> tw((size_t)M);
+    std::vector<std::mt19937_64> rng;
+    std::vector<std::vector<int>> perm((size_t)M, std::vector<int>((size_t)n));
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> done((size_t)M, nullptr);
     int rc = AMFRW_OK;
+    if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess) rc = sg_fail(AMFRW_ECUDA, "event");
+    if (rc == AMFRW_OK) cudaEventRecord(fork, st);
+    for (int m = 0; m < M; ++m) {
+        rng.emplace_back(s->seed * 7919ull + 17ull * (uint64_t)m + 1ull);
+        if (rc != AMFRW_OK) continue;
+        if (cudaStreamCreateWithFlags(&tw[(size_t)m].st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&done[(size_t)m], cudaEventDisableTiming) != cudaSuccess) {
+            rc = sg_fail(AMFRW_ECUDA, "training streams");
+            continue;
+        }
+        tw[(size_t)m].own_stream = true;
+        rc = sg_work_alloc(tw[(size_t)m], B, B);
+        if (rc == AMFRW_OK && cudaMalloc(&tw[(size_t)m].idx, sizeof(int) * n) != cudaSuccess)
+            rc = sg_fail(AMFRW_ENOMEM, "training permutation");
+        if (rc == AMFRW_OK) cudaStreamWaitEvent(tw[(size_t)m].st, fork, 0);  // after the uploads
+    }
     float last = 0.0f;
-    for (int m = 0; m < s->members && rc == AMFRW_OK; ++m) {
-        std::mt19937_64 rng(s->seed * 7919ull + 17ull * (uint64_t)m + 1ull);
-        int64_t step = 0;
-        for (int ep = 0; ep < epochs && rc == AMFRW_OK; ++ep) {
-            for (int64_t i = 0; i < n; ++i) perm[(size_t)i] = (int)i;
-            std::shuffle(perm.begin(), perm.end(), rng);
-            cudaMemcpyAsync(d_idx, perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st);
-            cudaMemsetAsync(s->loss, 0, sizeof(float), st);
-            for (int64_t k = 0; k < steps_per_epoch && rc == AMFRW_OK; ++k, ++step) {
-                pack_kernel<<<cdiv(B * kInPad, 256), 256, 0, st>>>(d_feats, d_targ, d_idx + k * B, 0, B, s->X,
-                                                                  s->Xt, s->t);
-                rc = sg_forward(s, m, B, true, s->y);
-                if (rc == AMFRW_OK) rc = sg_backward(s, m, B);
-                // Adam with cosine decay to 1% of lr
-                const double frac = (double)step / (double)std::max<int64_t>(1, total - 1);
-                const float lr_t = (float)(lr * (0.01 + 0.99 * 0.5 * (1.0 + std::cos(M_PI * frac))));
-                const int t = (int)step + 1;
-                const float bc1 = 1.0f - std::pow(0.9f, (float)t), bc2 = 1.0f - std::pow(0.999f, (float)t);
-                adam_kernel<<<cdiv(kParams, 256), 256, 0, st>>>(s->P[m], s->G[m], s->Mo[m], s->Vo[m], kParams,
-                                                               lr_t, 0.9f, 0.999f, 1e-8f, bc1, bc2);
-                sg_cast(s, m);
+    for (int ep = 0; ep < epochs && rc == AMFRW_OK; ++ep) {
+        for (int m = 0; m < M; ++m) {
+            SgWork& w = tw[(size_t)m];
+            std::vector<int>& pm = perm[(size_t)m];
+            for (int64_t i = 0; i < n; ++i) pm[(size_t)i] = (int)i;
+            std::shuffle(pm.begin(), pm.end(), rng[(size_t)m]);
+            cudaMemcpyAsync(w.idx, pm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, w.st);
+            cudaMemsetAsync(w.loss, 0, sizeof(float), w.st);
+        }
+        for (int64_t k = 0; k < steps_per_epoch && rc == AMFRW_OK; ++k) {
+            const int64_t step = (int64_t)ep * steps_per_epoch + k;
+            // Adam with cosine decay to 1% of lr
+            const double frac = (double)step / (double)std::max<int64_t>(1, total - 1);
+            const float lr_t = (float)(lr * (0.01 + 0.99 * 0.5 * (1.0 + std::cos(M_PI * frac))));
+            const int t = (int)step + 1;
+            const float bc1 = 1.0f - std::pow(0.9f, (float)t), bc2 = 1.0f - std::pow(0.999f, (float)t);
+            for (int m = 0; m < M && rc == AMFRW_OK; ++m) {
+                const SgWork& w = tw[(size_t)m];
+                pack_kernel<<<cdiv(B * kInPad, 256), 256, 0, w.st>>>(d_feats, d_targ, w.idx + k * B, 0, B, w.X,
+                                                                    w.Xt, w.t);
+                rc = sg_forward(s, m, B, true, w.y, w);
+                if (rc == AMFRW_OK) rc = sg_backward(s, m, B, w);
+                adam_kernel<<<cdiv(kParams, 256), 256, 0, w.st>>>(s->P[m], s->G[m], s->Mo[m], s->Vo[m], kParams,
+                                                                 lr_t, 0.9f, 0.999f, 1e-8f, bc1, bc2);
+                sg_cast(s, m, w.st);
             }
-            if (rc == AMFRW_OK && ep == epochs - 1) {
+        }
+        if (rc == AMFRW_OK && ep == epochs - 1) {
+            for (int m = 0; m < M; ++m) {
                 float hl = 0.0f;
-                cudaMemcpyAsync(&hl, s->loss, sizeof(float), cudaMemcpyDeviceToHost, st);
-                cudaStreamSynchronize(st);
-                last += hl / (float)steps_per_epoch / (float)s->members;
+                cudaMemcpyAsync(&hl, tw[(size_t)m].loss, sizeof(float), cudaMemcpyDeviceToHost, tw[(size_t)m].st);
+                cudaStreamSynchronize(tw[(size_t)m].st);
+                last += hl / (float)steps_per_epoch / (float)M;
             }
         }
     }
+    // join: the caller's stream waits for every member
+    for (int m = 0; m < M; ++m) {
+        if (tw[(size_t)m].st && done[(size_t)m]) {
+            cudaEventRecord(done[(size_t)m], tw[(size_t)m].st);
+            cudaStreamWaitEvent(st, done[(size_t)m], 0);
+        }
+    }
+    cudaStreamSynchronize(st);
+    for (int m = 0; m < M; ++m) {
+        tw[(size_t)m].release();
+        if (done[(size_t)m]) cudaEventDestroy(done[(size_t)m]);
+    }
+    if (fork) cudaEventDestroy(fork);
     cudaFree(d_feats);
     cudaFree(d_targ);
-    cudaFree(d_idx);
     if (rc != AMFRW_OK) return rc;
     rc = sg_check_err(s);
     if (rc != AMFRW_OK) return rc;
@@ -1015,7 +1080,7 @@ int amfrw_surrogate_load(const char* path, void* cuda_stream, amfrw_surrogate** 
     for (int m = 0; ok && m < members; ++m) {
         ok = fread(h.data(), sizeof(float), kParams, f) == (size_t)kParams;
         ok = ok && cudaMemcpy(s->P[m], h.data(), sizeof(float) * kParams, cudaMemcpyHostToDevice) == cudaSuccess;
-        if (ok) sg_cast(s, m);
+        if (ok) sg_cast(s, m, s->stream);
     }
     fclose(f);
     if (!ok) {
@@ -1038,7 +1103,7 @@ int amfrw_surrogate_params(amfrw_surrogate* s, int32_t member, float* params_out
     if (!s || member < 0 || member >= s->members) return sg_fail(AMFRW_EINVAL, "bad member");
     if (params_in) {
         SG_CUDA(cudaMemcpy(s->P[member], params_in, sizeof(float) * kParams, cudaMemcpyHostToDevice));
-        sg_cast(s, member);
+        sg_cast(s, member, s->stream);
         SG_CUDA(cudaStreamSynchronize(s->stream));
     }
     if (params_out) SG_CUDA(cudaMemcpy(params_out, s->P[member], sizeof(float) * kParams, cudaMemcpyDeviceToHost));
@@ -1057,14 +1122,14 @@ int amfrw_surrogate_grad(amfrw_surrogate* s, int32_t member, const float* x_norm
     SG_CUDA(cudaMalloc(&d_t, sizeof(float) * rows));
     cudaMemcpyAsync(d_x, x_norm, sizeof(float) * rows * kIn, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(d_t, targets, sizeof(float) * rows, cudaMemcpyHostToDevice, st);
-    cudaMemsetAsync(s->loss, 0, sizeof(float), st);
+    cudaMemsetAsync(s->w.loss, 0, sizeof(float), st);
     cudaMemsetAsync(s->G[member], 0, sizeof(float) * kParams, st);
-    pack_kernel<<<cdiv(rows * kInPad, 256), 256, 0, st>>>(d_x, d_t, nullptr, 0, rows, s->X, s->Xt, s->t);
-    int rc = sg_forward(s, member, rows, true, s->y);
-    if (rc == AMFRW_OK) rc = sg_backward(s, member, rows);
+    pack_kernel<<<cdiv(rows * kInPad, 256), 256, 0, st>>>(d_x, d_t, nullptr, 0, rows, s->w.X, s->w.Xt, s->w.t);
+    int rc = sg_forward(s, member, rows, true, s->w.y, s->w);
+    if (rc == AMFRW_OK) rc = sg_backward(s, member, rows, s->w);
     if (rc == AMFRW_OK) {
         cudaMemcpyAsync(grad_out, s->G[member], sizeof(float) * kParams, cudaMemcpyDeviceToHost, st);
-        if (loss_out) cudaMemcpyAsync(loss_out, s->loss, sizeof(float), cudaMemcpyDeviceToHost, st);
+        if (loss_out) cudaMemcpyAsync(loss_out, s->w.loss, sizeof(float), cudaMemcpyDeviceToHost, st);
         cudaStreamSynchronize(st);
     }
     cudaFree(d_x);
