@@ -83,7 +83,7 @@ def parse():
     ap.add_argument("--members", type=int, default=8, help="c5: ensemble members")
     ap.add_argument("--budget", type=float, default=300.0, help="paper: GPU seconds to spend")
     ap.add_argument("--only", default=None,
-                    help="paper: one row, TABLE:LEVEL[:STEPS] (e.g. sg_d4:12:8), for profiling")
+                    help="paper: one row, TABLE:LEVEL[:STEPS] (e.g. sg_d4:12:8, d4:level:12), for profiling")
     return ap.parse_args()
 
 
@@ -631,10 +631,15 @@ def run_paper(args, local_rank):
     rows = []
     todo = PAPER_ROWS
     if args.only:
+        # TABLE:LEVEL[:STEPS]; table names may contain ':' themselves (d4:level)
         parts = args.only.split(":")
-        todo = [(t, nr, psi, st, fm, [r for r in lv if r[0] == int(parts[1])])
+        nums = []
+        while parts and parts[-1].isdigit() and len(nums) < 2:
+            nums.insert(0, int(parts.pop()))
+        table = ":".join(parts)
+        todo = [(t, nr, psi, st, fm, [r for r in lv if r[0] == nums[0]])
                 for t, nr, psi, st, fm, lv in PAPER_ROWS
-                if t == parts[0] and (len(parts) < 3 or st == int(parts[2]))][:1]
+                if t == table and (len(nums) < 2 or st == nums[1])][:1]
     for table, nr, psi, steps, fmax, levels in todo:
         left = args.budget / len(todo)  # each table gets its share
         prev = None
