@@ -250,7 +250,8 @@ int amfrw_tc_gemm_bf16(const void *dA, int32_t lda, const void *dB, int32_t ldb,
  *              in the normalised features (165 monomials) is the control
  *              variate; every member learns the standardised residual of g
  *              (Adam, cosine-decayed learning rate, batches of 1024, mean
- *              squared error).  *final_loss_out (may be NULL) = mean loss of
+ *              squared error); the members train concurrently, each on a
+ *              stream of its own, joined to cuda_stream before returning.  *final_loss_out (may be NULL) = mean loss of
  *              the last epoch, in standardised units.
  *   calibrate  on an audit sample judged by the solver: the factor is the
  *              `quantile` of |error| / spread; stores rel_bound.
