@@ -242,7 +242,7 @@ struct LaunchClass {
 // Global-memory groups: at most this much scratch per launch class (it bounds
 // the number of resident blocks, each holding one grid's state).
 constexpr int64_t kMemScratchBudget = int64_t(8) << 30;
-constexpr int kMemBlock = kMemThreads;
+constexpr int kMemBlock = 256;
 
 struct Plan {
     int device = 0;

@@ -12,7 +12,6 @@ namespace amfrw {
 
 constexpr int kMaxDim = 8;
 constexpr int kCtaMaxThreads = 256;  // CTA work groups (grids of more than 64 Inner nodes)
-constexpr int kMemThreads = 512;    // global-memory work groups (one large grid per CTA)
 
 // Per-instance parameters on the device (one per pricing problem).
 struct InstDev {

@@ -1225,8 +1225,7 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
 // then moves on, so classes of uneven instances share one launch and no warp
 // waits for another.
 template <int N, bool MIXED, int KIND>
-__global__ void __launch_bounds__(KIND == kWarpGroup ? 128 : (KIND == kMemGroup ? kMemThreads : kCtaMaxThreads),
-                                    KIND == kWarpGroup ? 3 : 1) solve_kernel(SolveArgs a)
+__global__ void __launch_bounds__(KIND == kWarpGroup ? 128 : kCtaMaxThreads, KIND == kWarpGroup ? 3 : (KIND == kMemGroup ? 2 : 1)) solve_kernel(SolveArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     if constexpr (KIND == kWarpGroup) {
