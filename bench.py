@@ -81,6 +81,8 @@ def parse():
     ap.add_argument("--queries", type=int, default=1 << 20, help="c5: queries served")
     ap.add_argument("--epochs", type=int, default=260, help="c5: training epochs")
     ap.add_argument("--members", type=int, default=8, help="c5: ensemble members")
+    ap.add_argument("--global-grids", action="store_true",
+                    help="c2/c3/c4: keep every component grid in global memory (for comparisons)")
     ap.add_argument("--budget", type=float, default=300.0, help="paper: GPU seconds to spend")
     ap.add_argument("--only", default=None,
                     help="paper: one row, TABLE:LEVEL[:STEPS] (e.g. sg_d4:12:8, d4:level:12), for profiling")
@@ -301,6 +303,8 @@ def run_ours(args, rank, world, local_rank):
     wl = WORKLOADS[args.workload]
     B = args.batch or wl["batch"]
     insts = W.batch(args.workload, B, start=shard_start(rank, B))
+    if args.global_grids:
+        insts = [dict(x, global_grids=True) for x in insts]
     with torch.cuda.stream(stream):
         batch = L.Batch(insts, stream=stream)
         batch.enable_timing(True)
