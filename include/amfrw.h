@@ -196,15 +196,22 @@ int amfrw_batch_enable_timing(amfrw_batch *b, int32_t on);
 int amfrw_batch_kernel_times(amfrw_batch *b, float *ms_out, double *node_steps_out,
                              int32_t *dims_out, int32_t cap, int32_t *n_out);
 
-/* Autotuning of the launch strategy (the paper has no counterpart; its CPU
- * code schedules grids with OpenMP's dynamic schedule).  Times, on this
- * batch and device, per-class launches against one persistent multi-class
- * launch for the warp-solved grids (`trials` solves each after a warm-up),
- * keeps the faster, and caches the choice in-process under the batch's class
- * signature (and, if the environment variable AMFRW_TUNE_CACHE names a file,
- * appends it there), so later batches with the same classes start with it.
- * *use_multi_out (may be NULL) receives the choice.  Synchronises. */
+/* Autotuning of the launch strategy and of where grid states live (the
+ * paper has no counterpart; its CPU code schedules grids with OpenMP's
+ * dynamic schedule).  Times, on this batch and device (`trials` solves each
+ * after a warm-up): (1) per-class launches against one persistent
+ * multi-class launch for the warp-solved grids; (2) for every CTA class
+ * (grids in shared memory) its launch with the grid states in shared memory
+ * against in global memory, class by class.  Keeps the faster choices and
+ * caches them in-process under the batch's class signature (and, if the
+ * environment variable AMFRW_TUNE_CACHE names a file, appends them there),
+ * so later batches with the same classes start with them.  *use_multi_out
+ * (may be NULL) receives choice (1).  Prices change by rounding only.
+ * Synchronises. */
 int amfrw_batch_autotune(amfrw_batch *b, int32_t trials, int32_t *use_multi_out);
+/* Launch classes of a batch by work-group kind: warp groups, CTA groups
+ * (grids in shared memory), global-memory groups.  Any pointer may be NULL. */
+int amfrw_batch_classes(const amfrw_batch *b, int32_t *n_warp, int32_t *n_cta, int32_t *n_global);
 
 /* Bytes one amfrw_solve_batch call of this problem set copies host->device
  * (instance records, grid list, coefficients) and device->host (prices and

@@ -28,7 +28,7 @@ EXPORTS = [
     "amfrw_problem_destroy", "amfrw_solve_batch", "amfrw_batch_create", "amfrw_batch_run",
     "amfrw_batch_launches", "amfrw_batch_destroy", "amfrw_status_string", "amfrw_last_error",
     "amfrw_batch_enable_timing", "amfrw_batch_kernel_times", "amfrw_batch_io_bytes",
-    "amfrw_solve_noalloc", "amfrw_batch_autotune", "amfrw_tc_gemm_bf16",
+    "amfrw_solve_noalloc", "amfrw_batch_autotune", "amfrw_batch_classes", "amfrw_tc_gemm_bf16",
     "amfrw_surrogate_create", "amfrw_surrogate_fit", "amfrw_surrogate_calibrate",
     "amfrw_surrogate_predict", "amfrw_surrogate_predict_features", "amfrw_surrogate_eval",
     "amfrw_surrogate_eval_features",
@@ -93,6 +93,7 @@ def lib():
         L.amfrw_batch_io_bytes.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         L.amfrw_solve_noalloc.argtypes = [pp, C.c_int32, vp, vp]
         L.amfrw_batch_autotune.argtypes = [vp, C.c_int32, C.POINTER(C.c_int32)]
+        L.amfrw_batch_classes.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
         i32 = C.c_int32
         L.amfrw_tc_gemm_bf16.argtypes = [vp, i32, vp, i32, vp, i32, i32, i32, i32, vp]
         i64, u8p, fp = C.c_int64, C.POINTER(C.c_uint8), C.POINTER(C.c_float)
@@ -274,11 +275,18 @@ class Batch:
         return [(dims[i], ms[i], ns[i]) for i in range(n.value)]
 
     def autotune(self, trials: int = 2) -> bool:
-        """Pick the faster launch strategy on this device; True = one persistent
-        multi-class launch for the warp-solved grids."""
+        """Pick the faster launch strategy and grid-state placement on this
+        device; True = one persistent multi-class launch for the warp-solved
+        grids."""
         m = C.c_int32()
         _check(lib().amfrw_batch_autotune(self.h, int(trials), C.byref(m)), "amfrw_batch_autotune")
         return bool(m.value)
+
+    def classes(self):
+        """Launch classes by kind: (warp groups, CTA groups, global-memory groups)."""
+        w, c, g = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(lib().amfrw_batch_classes(self.h, C.byref(w), C.byref(c), C.byref(g)), "amfrw_batch_classes")
+        return w.value, c.value, g.value
 
     def io_bytes(self):
         h2d, d2h = C.c_int64(), C.c_int64()

@@ -687,6 +687,48 @@ int run_combine(Plan& P, double* d_out)
     return AMFRW_OK;
 }
 
+// Move CTA class c (grids in shared memory) to a global-memory class: same
+// grids, each block's state in its slice of the plan's scratch array.
+int class_to_global(Plan& P, int c)
+{
+    LaunchClass& L = P.classes[(size_t)c];
+    if (L.kind != kCtaGroup) return AMFRW_OK;
+    int64_t lumax = 0;
+    for (int q = L.item_begin; q < L.item_begin + L.item_count; ++q) {
+        const Layout lay = make_layout(L.N, P.items[(size_t)q].lv, L.mixed, kMemGroup, log2i(kMemBlock));
+        lumax = std::max<int64_t>(lumax, lay.total);
+    }
+    const int per_sm = occ_for(L.N)(L.mixed, kMemGroup, kMemBlock, 0);
+    if (per_sm < 1) return fail(AMFRW_ETOOBIG, "no resident block possible for a global-memory class");
+    L.kind = kMemGroup;
+    L.block = kMemBlock;
+    L.smem = 0;
+    L.lu_stride = (lumax + 255) & ~(int64_t)255;
+    L.grid = std::max(1, std::min(L.item_count, per_sm * num_sms()));
+    if (L.lu_stride > 0)
+        L.grid = (int)std::max<int64_t>(1, std::min<int64_t>(L.grid, kMemScratchBudget / L.lu_stride));
+    return AMFRW_OK;
+}
+
+// Reassign every class's part of the scratch array and reallocate it when
+// its length changes.
+int relayout_scratch(Plan& P)
+{
+    int64_t off = 0;
+    for (LaunchClass& c : P.classes) {
+        c.lu_offset = off;
+        off += c.lu_stride * c.grid;
+    }
+    if (off != P.lu_scratch_len) {
+        CUDA_TRY(cudaStreamSynchronize(P.stream));
+        cudaFree(P.d_lu);
+        P.d_lu = nullptr;
+        P.lu_scratch_len = off;
+        if (off > 0) CUDA_TRY(cudaMalloc(&P.d_lu, (size_t)off));
+    }
+    return AMFRW_OK;
+}
+
 int all_same_steps(const Plan& P)
 {
     int s = P.insts[0].n_steps;
@@ -719,9 +761,11 @@ struct amfrw_batch {
 
 namespace {
 
-// Launch-strategy cache of the autotuner: class signature -> multi on/off.
+// Cache of the autotuner: class signature -> choice bits (bit 0: one
+// persistent multi-class launch for the warp groups; bit 1 + k: the k-th CTA
+// class keeps its grids in global memory instead of shared memory).
 std::mutex g_tune_mutex;
-std::map<std::string, bool> g_tune_cache;
+std::map<std::string, int> g_tune_cache;
 
 std::string class_signature(const Plan& P)
 {
@@ -748,19 +792,43 @@ void load_tune_file()
         char* sp = strrchr(line, ' ');
         if (!sp) continue;
         *sp = 0;
-        g_tune_cache[line] = atoi(sp + 1) != 0;
+        g_tune_cache[line] = atoi(sp + 1);
     }
     fclose(f);
 }
 
-void save_tune_entry(const std::string& sig, bool multi)
+void save_tune_entry(const std::string& sig, int choice)
 {
     const char* path = getenv("AMFRW_TUNE_CACHE");
     if (!path) return;
     FILE* f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%s %d\n", sig.c_str(), multi ? 1 : 0);
+    fprintf(f, "%s %d\n", sig.c_str(), choice);
     fclose(f);
+}
+
+// Apply cached choice bits to a freshly planned batch.
+int apply_choice(Plan& P, int choice)
+{
+    int st = AMFRW_OK;
+    int k = 0;
+    bool moved = false;
+    for (size_t c = 0; c < P.classes.size() && st == AMFRW_OK; ++c) {
+        if (P.classes[c].kind != kCtaGroup) continue;
+        if ((choice >> (1 + k)) & 1) {
+            st = class_to_global(P, (int)c);
+            moved = true;
+        }
+        ++k;
+    }
+    if (st == AMFRW_OK && moved) st = relayout_scratch(P);
+    const bool multi = (choice & 1) != 0;
+    if (st == AMFRW_OK && multi != P.use_multi) {
+        P.use_multi = multi;
+        st = build_warp_launches(P);
+        if (st == AMFRW_OK) st = upload_warp_launches(P);
+    }
+    return st;
 }
 
 // Capture solve + combination into a CUDA graph on the batch's private stream.
@@ -938,10 +1006,8 @@ int amfrw_batch_create(const amfrw_params* ps, int32_t n, void* cuda_stream, amf
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         load_tune_file();
         auto it = g_tune_cache.find(class_signature(b->plan));
-        if (it != g_tune_cache.end() && it->second != b->plan.use_multi) {
-            b->plan.use_multi = it->second;
-            st = build_warp_launches(b->plan);
-            if (st == AMFRW_OK) st = upload_warp_launches(b->plan);
+        if (it != g_tune_cache.end()) {
+            st = apply_choice(b->plan, it->second);
             if (st != AMFRW_OK) {
                 delete b;
                 return st;
@@ -973,8 +1039,33 @@ int amfrw_batch_autotune(amfrw_batch* b, int32_t trials, int32_t* use_multi_out)
     if (!b) return fail(AMFRW_EINVAL, "NULL argument");
     Plan& P = b->plan;
     if (trials < 1) trials = 1;
+    const int steps = P.insts[0].n_steps;
+    const std::string sig = class_signature(P);  // of the plan as built, before any move
+    const std::vector<LaunchClass> base = P.classes;
+    // time `trials` solves (after a warm-up); per-record times if rec != nullptr
+    auto timed = [&](float& total, std::vector<float>* rec) -> int {
+        const size_t nrec = launch_records(P).size();
+        std::vector<cudaEvent_t> ev(2 * nrec, nullptr);
+        for (cudaEvent_t& e : ev) CUDA_TRY(cudaEventCreate(&e));
+        int st = run_solve(P, steps, 0);
+        total = 0.f;
+        if (rec) rec->assign(nrec, 0.f);
+        for (int k = 0; k < trials && st == AMFRW_OK; ++k) {
+            st = run_solve(P, steps, 0, ev.data());
+            if (st == AMFRW_OK && cudaEventSynchronize(ev.back()) != cudaSuccess) st = fail(AMFRW_ECUDA, "timing");
+            for (size_t r = 0; r < nrec && st == AMFRW_OK; ++r) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ev[2 * r], ev[2 * r + 1]);
+                total += ms;
+                if (rec) (*rec)[r] += ms;
+            }
+        }
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        return st;
+    };
+    int st = AMFRW_OK;
+    // 1. warp groups: per-class launches against one persistent multi-class launch
     bool best = P.use_multi;
-    // the strategies differ only if some (N, precision) has several warp classes
     bool differs = false;
     for (size_t c = 0; c < P.classes.size(); ++c)
         for (size_t d = c + 1; d < P.classes.size(); ++d)
@@ -982,41 +1073,74 @@ int amfrw_batch_autotune(amfrw_batch* b, int32_t trials, int32_t* use_multi_out)
                 P.classes[c].mixed == P.classes[d].mixed)
                 differs = true;
     if (differs) {
-        cudaEvent_t e0, e1;
-        CUDA_TRY(cudaEventCreate(&e0));
-        CUDA_TRY(cudaEventCreate(&e1));
         float t[2] = {0.f, 0.f};
-        int st = AMFRW_OK;
         for (int m = 0; m < 2 && st == AMFRW_OK; ++m) {
             P.use_multi = m == 1;
             st = build_warp_launches(P);
             if (st == AMFRW_OK) st = upload_warp_launches(P);
-            if (st == AMFRW_OK) st = run_solve(P, P.insts[0].n_steps, 0);  // warm-up
-            if (st != AMFRW_OK) break;
-            cudaEventRecord(e0, P.stream);
-            for (int k = 0; k < trials && st == AMFRW_OK; ++k) st = run_solve(P, P.insts[0].n_steps, 0);
-            cudaEventRecord(e1, P.stream);
-            cudaEventSynchronize(e1);
-            cudaEventElapsedTime(&t[m], e0, e1);
+            if (st == AMFRW_OK) st = timed(t[m], nullptr);
         }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
         if (st != AMFRW_OK) return st;
         best = t[1] <= t[0];
         P.use_multi = best;
         st = build_warp_launches(P);
         if (st == AMFRW_OK) st = upload_warp_launches(P);
         if (st != AMFRW_OK) return st;
-        std::lock_guard<std::mutex> lock(g_tune_mutex);
-        const std::string sig = class_signature(P);
-        g_tune_cache[sig] = best;
-        save_tune_entry(sig, best);
-        if (b->exec) {
-            cudaGraphExecDestroy(b->exec);
-            b->exec = nullptr;
+    }
+    // 2. CTA classes: grid state in shared memory against global memory, class by class
+    int choice = best ? 1 : 0;
+    std::vector<int> cta;
+    for (size_t c = 0; c < P.classes.size(); ++c)
+        if (P.classes[c].kind == kCtaGroup) cta.push_back((int)c);
+    if (!cta.empty()) {
+        // launch record of each CTA class
+        std::vector<size_t> at;
+        {
+            const std::vector<std::pair<int, int>> recs = launch_records(P);
+            for (int c : cta)
+                for (size_t r = 0; r < recs.size(); ++r)
+                    if (recs[r].second == c) at.push_back(r);
         }
+        float tot[2];
+        std::vector<float> rec[2];
+        st = timed(tot[0], &rec[0]);
+        for (int c : cta)
+            if (st == AMFRW_OK) st = class_to_global(P, c);
+        if (st == AMFRW_OK) st = relayout_scratch(P);
+        if (st == AMFRW_OK) st = timed(tot[1], &rec[1]);
+        if (st != AMFRW_OK) return st;
+        P.classes = base;  // back to shared memory, then move the classes that were faster
+        for (size_t k = 0; k < cta.size(); ++k) {
+            if (rec[1][at[k]] < rec[0][at[k]]) {
+                choice |= 1 << (1 + (int)k);
+                st = class_to_global(P, cta[k]);
+                if (st != AMFRW_OK) return st;
+            }
+        }
+        st = relayout_scratch(P);
+        if (st != AMFRW_OK) return st;
+    }
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tune_cache[sig] = choice;
+        save_tune_entry(sig, choice);
+    }
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
     }
     if (use_multi_out) *use_multi_out = best ? 1 : 0;
+    return AMFRW_OK;
+}
+
+int amfrw_batch_classes(const amfrw_batch* b, int32_t* n_warp, int32_t* n_cta, int32_t* n_global)
+{
+    if (!b) return fail(AMFRW_EINVAL, "NULL argument");
+    int32_t c[3] = {0, 0, 0};
+    for (const LaunchClass& L : b->plan.classes) ++c[L.kind];
+    if (n_warp) *n_warp = c[kWarpGroup];
+    if (n_cta) *n_cta = c[kCtaGroup];
+    if (n_global) *n_global = c[kMemGroup];
     return AMFRW_OK;
 }
 

@@ -88,3 +88,29 @@ def test_c3_mixed_price_within_1e5_of_fp64():
     p_mix = B.solve_batch([inst])[0]
     p_64 = B.solve_batch([dict(inst, precision="fp64")])[0]
     assert abs(p_mix - p_64) <= 1e-5 * abs(p_64), (p_mix, p_64)
+
+
+def test_autotuned_grid_placement_keeps_prices():
+    # a d=6 modified batch has CTA classes (grids of up to 1024 Inner nodes);
+    # the autotuner may move them to global memory, which changes prices by
+    # rounding only, and a new batch with the same classes starts with it
+    import torch
+    insts = [W.small_instance(6, 3, psi=1, steps=4, seed=s) for s in range(4)]
+    b = B.Batch(insts)
+    w0, c0, g0 = b.classes()
+    assert c0 >= 1
+    out = torch.zeros(len(insts), dtype=torch.float64, device="cuda")
+    b.run(out.data_ptr())
+    torch.cuda.synchronize()
+    before = out.cpu().numpy().copy()
+    b.autotune(2)
+    w1, c1, g1 = b.classes()
+    assert w1 == w0 and c1 + g1 == c0 + g0
+    b.run(out.data_ptr())
+    torch.cuda.synchronize()
+    after = out.cpu().numpy()
+    assert np.allclose(after, before, rtol=1e-12, atol=0), (after, before)
+    b.close()
+    b2 = B.Batch(insts)
+    assert b2.classes() == (w1, c1, g1)
+    b2.close()
