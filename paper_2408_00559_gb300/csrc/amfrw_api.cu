@@ -652,10 +652,14 @@ int run_solve(Plan& P, int steps, int flags, cudaEvent_t* ev = nullptr)
 {
     CUDA_TRY(cudaMemsetAsync(P.d_queue, 0, sizeof(int32_t) * P.classes.size(), P.stream));
     const std::vector<std::pair<int, int>> recs = launch_records(P);
+    // inside a graph capture the records are external, so that they also
+    // record when the graph is replayed; outside they are plain records
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (ev) CUDA_TRY(cudaStreamIsCapturing(P.stream, &cap));
+    const unsigned rec_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
     for (size_t r = 0; r < recs.size(); ++r) {
         int rc = 0;
-        // external records so that they also record when replayed from a graph
-        if (ev) CUDA_TRY(cudaEventRecordWithFlags(ev[2 * r], P.stream, cudaEventRecordExternal));
+        if (ev) CUDA_TRY(cudaEventRecordWithFlags(ev[2 * r], P.stream, rec_flags));
         if (recs[r].first >= 0) {
             const Plan::WarpLaunch& w = P.wl[recs[r].first];
             SolveArgs a = class_args(P, P.classes[w.covers[0]], 0, steps, flags);
@@ -671,7 +675,7 @@ int run_solve(Plan& P, int steps, int flags, cudaEvent_t* ev = nullptr)
             rc = launch_for(L.N)(class_args(P, L, c, steps, flags), L.mixed, L.kind, L.block, L.grid,
                                  L.smem, P.stream);
         }
-        if (ev) CUDA_TRY(cudaEventRecordWithFlags(ev[2 * r + 1], P.stream, cudaEventRecordExternal));
+        if (ev) CUDA_TRY(cudaEventRecordWithFlags(ev[2 * r + 1], P.stream, rec_flags));
         if (rc != 0) return fail(AMFRW_ECUDA, std::string("solver launch: ") + cudaGetErrorString((cudaError_t)rc));
     }
     return AMFRW_OK;
