@@ -54,6 +54,11 @@ UNIT = "instances/s"
 WORKLOAD = ("c2: d=4 (3 forward rates + V) SABR-LMM swaption, standard combination level 5 "
             "(121 component grids, 15149 nodes), 40 AMFR-W2 steps, T=2, FP64")
 FP64_PEAK = 152 * 2 * 2 * 2070e6  # SMs x DFMA/clk x FLOP/FMA x max SM clock
+# DRAM bytes (read + write) of the C2 FP64 solver launch per instance: one ncu
+# capture of this kernel on a 256-instance launch (dram__bytes_read.sum
+# 1 030 144 + dram__bytes_write.sum 7 424).  The traffic is the parameter
+# records and the grid list, so it grows with the instances of a launch.
+C2_DRAM_BYTES_PER_INSTANCE = (1030144 + 7424) / 256
 FP32_PEAK = 152 * 128 * 2 * 2070e6  # SMs x FFMA/clk x FLOP/FMA x max SM clock
 WORKLOADS = {
     "c2": dict(desc=WORKLOAD, d=4, n=5, psi=0, dtype="f64", batch=4096),
@@ -438,7 +443,9 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "alu", "pipe": "fp64" if fp64 else "fp32",
                      "kernel": "solve_kernel (all per-class launches of a batch)",
                      "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": (C2_DRAM_BYTES_PER_INSTANCE * B
+                                 if args.workload == "c2" and not args.global_grids else None),
                      "kernel_ms_per_batch": avg_ms, "solver_launches_per_batch": launches_per_batch,
                      "flops_per_batch": flops_batch,
                      "peak_source": ("derived: 152 SMs x 2 DFMA/clk x 2 FLOP x 2070 MHz" if fp64 else
