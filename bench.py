@@ -91,6 +91,7 @@ def parse():
     ap.add_argument("--budget", type=float, default=300.0, help="paper: GPU seconds to spend")
     ap.add_argument("--only", default=None,
                     help="paper: one row, TABLE:LEVEL[:STEPS] (e.g. sg_d4:12:8, d4:level:12), for profiling")
+    ap.add_argument("--psi", type=int, default=None, help="paper: with --only, the table's psi")
     return ap.parse_args()
 
 
@@ -651,7 +652,7 @@ def run_paper(args, local_rank):
         table = ":".join(parts)
         todo = [(t, nr, psi, st, fm, [r for r in lv if r[0] == nums[0]])
                 for t, nr, psi, st, fm, lv in PAPER_ROWS
-                if t == table and (len(nums) < 2 or st == nums[1])][:1]
+                if t == table and (len(nums) < 2 or st == nums[1]) and (args.psi is None or psi == args.psi)][:1]
     for table, nr, psi, steps, fmax, levels in todo:
         left = args.budget / len(todo)  # each table gets its share
         prev = None

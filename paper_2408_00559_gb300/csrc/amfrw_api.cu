@@ -347,9 +347,9 @@ int plan_host(const amfrw_params* ps, int n, bool keep_state, Plan& P)
                     llog += g.lv[a];
                     maxlv = std::max(maxlv, (int)g.lv[a]);
                 }
-                if (llog > 20)
+                if (llog > 22)
                     return fail(AMFRW_ETOOBIG, "instance " + std::to_string(i) +
-                                                   ": a component grid has more than 2^20 Inner nodes");
+                                                   ": a component grid has more than 2^22 Inner nodes");
                 const bool warp = (1 << llog) <= kWarpMaxL && !force_mem;
                 // warp groups: one lane per node up to 32 nodes (at least 8 lanes), so
                 // small grids share a warp

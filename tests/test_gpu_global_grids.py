@@ -7,7 +7,8 @@ solves streamed from memory.
   shared-memory path agree with the oracle node by node to 1e-12 (FP64) and
   in price to 1e-5 (mixed).
 - Large grids take it by themselves: full grids of 129^2 and 257^2 nodes,
-  a d=3 combination with 512-row lines, against the oracle node by node.
+  a d=3 full grid of 2^21 Inner nodes, a d=3 combination with 512-row lines,
+  against the oracle node by node.
 - Every caplet value the paper prints (Tables fg_sigma0, fg_2d, d2_1,
   d1_sg_sigma, d1:Level; the oracle reproduces all of them) is reproduced on
   the GPU, including the rows that need this path.
@@ -81,6 +82,12 @@ def test_forced_global_path_mixed(case):
 @pytest.mark.parametrize("level,steps", [(7, 6), (8, 3)])
 def test_large_full_grids(level, steps):
     inst = dict(W.c1_instance(), level=level, n_steps=steps)
+    check_problem(inst, TOL64, TOL64)
+
+
+def test_grid_of_two_million_inner_nodes():
+    # d=3 full grid of level 7: 128^3 = 2^21 Inner nodes (above 2^20)
+    inst = W.small_instance(3, 7, steps=2, seed=21, full=True, payoff="swaption")
     check_problem(inst, TOL64, TOL64)
 
 
