@@ -824,18 +824,31 @@ __device__ __forceinline__ void sweep_mem(const Shape<N>& s, int axis, const T* 
     }
 }
 
+// One out-of-line copy of the register sweep per epilogue type.
+template <int N, typename T, int RMAX, class Epi>
+__device__ __noinline__ void sweep_outlined(const Shape<N>& s, int axis, const T* __restrict__ lu,
+                                            const T* src, T* dst, int rank, int gsize, unsigned gm,
+                                            Epi epi)
+{
+    sweep<N, T, RMAX>(s, axis, lu, src, dst, rank, gsize, gm, epi);
+}
+
 // Line sweep of a work-group kind: rows in registers (warp and CTA groups)
-// or streamed from memory (global-memory groups).
+// or streamed from memory (global-memory groups).  For N <= 4 the register
+// sweep is called out of line (one copy instead of one per call site), which
+// measured faster there; for larger N inlining measured faster.
 template <int N, typename T, int KIND, class Epi>
 __device__ __forceinline__ void lsweep(const Shape<N>& s, int axis, const T* __restrict__ lu,
                                        const T* src, T* dst, int rank, int gsize, unsigned gm,
                                        Epi epi)
 {
+    constexpr int RM = 1 << (KIND == kWarpGroup ? kRowsLogWarp : kRowsLogCta);
     if constexpr (KIND == kMemGroup)
         sweep_mem<N, T>(s, axis, lu, src, dst, rank, gsize, gm, epi);
+    else if constexpr (N <= 4)
+        sweep_outlined<N, T, RM>(s, axis, lu, src, dst, rank, gsize, gm, epi);
     else
-        sweep<N, T, 1 << (KIND == kWarpGroup ? kRowsLogWarp : kRowsLogCta)>(s, axis, lu, src, dst, rank,
-                                                                            gsize, gm, epi);
+        sweep<N, T, RM>(s, axis, lu, src, dst, rank, gsize, gm, epi);
 }
 
 template <bool WARP>
