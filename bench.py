@@ -56,9 +56,9 @@ WORKLOAD = ("c2: d=4 (3 forward rates + V) SABR-LMM swaption, standard combinati
 FP64_PEAK = 152 * 2 * 2 * 2070e6  # SMs x DFMA/clk x FLOP/FMA x max SM clock
 # DRAM bytes (read + write) of the C2 FP64 solver launch per instance: one ncu
 # capture of this kernel on a 256-instance launch (dram__bytes_read.sum
-# 1 030 144 + dram__bytes_write.sum 7 424).  The traffic is the parameter
-# records and the grid list, so it grows with the instances of a launch.
-C2_DRAM_BYTES_PER_INSTANCE = (1030144 + 7424) / 256
+# 814 848 + dram__bytes_write.sum 512).  The traffic is the parameter records
+# and the grid list, so it grows with the instances of a launch.
+C2_DRAM_BYTES_PER_INSTANCE = (814848 + 512) / 256
 FP32_PEAK = 152 * 128 * 2 * 2070e6  # SMs x FFMA/clk x FLOP/FMA x max SM clock
 WORKLOADS = {
     "c2": dict(desc=WORKLOAD, d=4, n=5, psi=0, dtype="f64", batch=4096),
