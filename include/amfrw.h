@@ -54,7 +54,7 @@ enum amfrw_status {
     AMFRW_ECUDA = 4,      /* a CUDA runtime call failed                       */
     AMFRW_ETIMEOUT = 5,   /* reserved: a bounded device wait gave up          */
     AMFRW_ENONFINITE = 6, /* a computed price is NaN or infinite              */
-    AMFRW_ETOOBIG = 7     /* a component grid exceeds the on-chip capacity    */
+    AMFRW_ETOOBIG = 7     /* a grid or a problem exceeds the supported size   */
 };
 
 enum amfrw_payoff {
@@ -131,7 +131,7 @@ typedef struct amfrw_batch amfrw_batch;
 
 /* Validate *p, enumerate its component grids, copy the parameters to the
  * device and set every grid to the payoff (eq. icNd).  No time step is taken.
- * Errors: EINVAL, ENOTPSD, ETOOBIG (a grid does not fit the on-chip solver),
+ * Errors: EINVAL, ENOTPSD, ETOOBIG (a grid has more than 2^22 Inner nodes),
  * ENOMEM, ECUDA. */
 int amfrw_problem_create(const amfrw_params *p, void *cuda_stream, amfrw_problem **out);
 
