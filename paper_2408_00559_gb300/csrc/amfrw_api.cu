@@ -38,9 +38,24 @@ int fail(int status, const std::string& msg)
             return fail(AMFRW_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
-constexpr int kWarpMaxL = 64;          // grids up to this many Inner nodes: one warp each
+constexpr int kWarpMaxL = 64;          // grids up to this many Inner nodes: warp groups
 constexpr int kWarpsPerBlock = 4;
-constexpr int kMinGroupLog = 3;        // warp groups have at least 8 lanes (at most 4 grids per warp)
+
+// Warp groups have at least 4 lanes for FP64 (at most 8 grids per warp) and
+// at least 8 for mixed precision, where smaller groups measured slower.
+constexpr int kMinGroupLogF64 = 2;
+constexpr int kMinGroupLogMixed = 3;
+
+// Lanes (as log2) of the warp group that solves a grid of 2^llog Inner
+// nodes: two nodes per lane (the most a lane's line-solve registers take), so
+// that a line solve runs one PCR level fewer than with one node per lane and
+// twice as many grids share a warp; at most 32 lanes.  Each PCR level costs
+// two FP64 FMAs per row, which is what bounds the warp kernels, so the fewer
+// levels outweigh the lower occupancy of the larger per-warp shared memory.
+int warp_group_log(int llog, bool mixed)
+{
+    return std::max(std::min(llog - kRowsLogWarp, 5), mixed ? kMinGroupLogMixed : kMinGroupLogF64);
+}
 
 bool finite(double x) { return std::isfinite(x); }
 
@@ -351,11 +366,10 @@ int plan_host(const amfrw_params* ps, int n, bool keep_state, Plan& P)
                     return fail(AMFRW_ETOOBIG, "instance " + std::to_string(i) +
                                                    ": a component grid has more than 2^22 Inner nodes");
                 const bool warp = (1 << llog) <= kWarpMaxL && !force_mem;
-                // warp groups: one lane per node up to 32 nodes (at least 8 lanes), so
-                // small grids share a warp
+                // warp groups: two nodes per lane, so small grids share a warp
                 int kind = warp ? kWarpGroup : kCtaGroup;
                 Layout lay = make_layout(N, g.lv, mixed, kind,
-                                         warp ? std::max(std::min(llog, 5), kMinGroupLog) : 5);
+                                         warp ? warp_group_log(llog, mixed) : 5);
                 // grids beyond shared memory, or with lines longer than the register
                 // sweeps take, keep their state in global memory
                 if (force_mem || lay.total > smem_cap || (!warp && maxlv > 5 + kRowsLogCta)) {
@@ -460,7 +474,7 @@ int plan_host(const amfrw_params* ps, int n, bool keep_state, Plan& P)
         c.smem_group = gmax;
         int64_t lumax = 0;
         if (c.warp) {
-            c.glog = std::max(log2i(std::min(lmax, 32)), kMinGroupLog);
+            c.glog = warp_group_log(log2i(lmax), c.mixed);
             const int gpw = 32 >> c.glog;  // groups per warp
             int wpb = std::min(kWarpsPerBlock, std::max(1, smem_cap / (gmax * gpw)));
             if ((size_t)gmax * gpw > (size_t)smem_cap)

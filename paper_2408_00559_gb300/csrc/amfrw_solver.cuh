@@ -602,12 +602,14 @@ __device__ __forceinline__ void sweep(const Shape<N>& s, int axis, const T* __re
                 }
             }
         }
+        // forward elimination; the lane's first row has no predecessor, so its
+        // lower factor drops out (x - l * 0 = x)
         T y = T(0);
 #pragma unroll
         for (int q = 0; q < RMAX; ++q) {
             if (q < R) {
                 const T* row = tb + q * PS + 2 * plog;
-                y = (x[q] - row[0] * y) * row[1];
+                y = (q == 0) ? x[q] * row[1] : (x[q] - row[0] * y) * row[1];
                 x[q] = y;
             }
         }
@@ -793,10 +795,13 @@ __device__ __forceinline__ void sweep_mem(const Shape<N>& s, int axis, const T* 
         }
         if (act) {
             const T* th = tb + 2 * plog;  // Thomas factors (lower, 1/pivot, upper/pivot) of row q at q PS
-            T y = T(0);
-            T x = in[J0], lo = th[0], iv = th[1];
-            T x1 = R > 1 ? in[J0 + PSp] : T(0);
-            for (int q = 0; q < R; ++q) {
+            // the first row has no predecessor: its lower factor drops out
+            T y = in[J0] * th[1];
+            dst[J0] = y;
+            T x = R > 1 ? in[J0 + PSp] : T(0);
+            T lo = R > 1 ? th[PS] : T(0), iv = R > 1 ? th[PS + 1] : T(0);
+            T x1 = R > 2 ? in[J0 + 2 * PSp] : T(0);
+            for (int q = 1; q < R; ++q) {
                 const T x2 = q + 2 < R ? in[J0 + (q + 2) * PSp] : T(0);
                 const T lo_n = q + 1 < R ? th[(q + 1) * PS] : T(0);
                 const T iv_n = q + 1 < R ? th[(q + 1) * PS + 1] : T(0);
@@ -1313,8 +1318,22 @@ int occupancy_impl(bool mixed, int kind, int block, size_t smem)
 {
     int nb = 0;
     const void* f = kernel_for<N>(mixed, kind);
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // The limit is an attribute of the kernel, shared by all its launches, and
+    // launches of one kernel request different amounts: past the default
+    // 48 KB, allow the device's opt-in maximum (less the kernel's static
+    // shared memory), so that no launch depends on which query came last.
+    if (smem > 48 * 1024) {
+        int dev = 0, optin = 0;
+        cudaFuncAttributes fa{};
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+            cudaFuncGetAttributes(&fa, f) != cudaSuccess)
+            return 0;
+        const int lim = optin - (int)fa.sharedSizeBytes;
+        if ((size_t)lim < smem ||
+            cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess)
+            return 0;
+    }
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, block, smem) != cudaSuccess) return 0;
     return nb;
 }
