@@ -142,7 +142,7 @@ AMFRW_HD Layout make_layout(int N, const int8_t* lv, bool mixed, int kind, int t
     y.tabf = o; o = align16(o + (mixed ? 4 * y.ntab : 0));
     y.pay = o;  o = align16(o + 8 * y.npay);
     y.lu = o;   o = align16(o + (lu_in ? sk * y.nlu : 0));
-    y.Z = o;    o = align16(o + (mixed ? 0 : 8 * y.Lp));
+    y.Z = o;    o = align16(o + 8 * y.Lp);
     y.ZZ = o;   o = align16(o + (mixed ? 8 * y.Lp : 0));
     y.H = o;    o = align16(o + sk * y.Lr);
     y.FY = o;   o = align16(o + (mixed ? 4 * y.Lp : 0));

@@ -27,11 +27,10 @@
 // nothing else.
 //
 // Precision.  FP64 mode: every operation in double.  Mixed mode: the stencil
-// and the line solves run in FP32 on the increments K; Z is accumulated
-// (Y_{n+1} = Y_n + b1 K1 + b2 K2) as an unevaluated pair of floats
-// (hi + lo, ~48 bits), which the stencil of F(Y_n) reads, so its differences
-// keep ~48 bits; F(G) (through H), the interpolation and the combination sum
-// are FP64.  The
+// and the line solves run in FP32 on the increments K; Z is accumulated in
+// FP64 (Y_{n+1} = Y_n + b1 K1 + b2 K2) and the stencil of F(Y_n) reads Z as
+// an unevaluated pair of floats (hi + lo), so its differences keep ~48 bits;
+// F(G) (through H), the interpolation and the combination sum are FP64.  The
 // stage-2 argument uses linearity, F(Y_n + a21 K1) = F(Y_n) + a21 F_0(K1), so
 // that F is applied to Y only once per step.
 #pragma once
@@ -940,14 +939,12 @@ __device__ void convert_consts(const Consts<double>& a, Consts<T>* b)
     }
 }
 
-// Mixed mode holds Z as the unevaluated pair hi + lo of floats (a 48-bit
-// significand), which the stencil of F(Y_n) reads.  Each step adds the two
+// Mixed mode keeps, beside the FP64 accumulation of Z, the unevaluated pair
+// hi + lo that the stencil of F(Y_n) reads.  It is advanced with the same two
 // increments by error-free transformations in FP32 (Knuth's TwoSum; the
-// product error c*x - fl(c*x) by one FMA), so the accumulation loses about
-// 2^-48 of |Z| per step, far below the FP32 error of the increments, without
-// any FP64 operation (FP64 runs at 1/64 of the FP32 rate on this part).  The
-// _rn intrinsics keep the compiler from contracting the products into the
-// sums.
+// product error c*x - fl(c*x) by one FMA), so it follows Z to the pair's
+// precision without converting Z every step.  The _rn intrinsics keep the
+// compiler from contracting the products into the sums.
 __device__ __forceinline__ float2 ff_axpy(float2 z, float c, float x)
 {
     const float p = __fmul_rn(c, x);
@@ -1047,8 +1044,8 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
             decode<N>(s, t, j);
             z = a.state[it.state_off + t] - payoff_at<N>(s, pay, P.payoff, j);
         }
+        Z[J] = z;
         if constexpr (MIXED) ZZ[J] = split_df(z);
-        else Z[J] = z;
     }
     gsync<WARP>(gm);
     if constexpr (DIFF) {
@@ -1178,10 +1175,10 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
         for (int ax = 0; ax < N; ++ax) {
             if (ax == N - 1) {
                 lsweep<N, TK, KIND>(s, ax, luc, K0, K0, rank, gsize, gm, [=](int J, TK x) {
+                    const double z = fma(kB2, (double)x, fma(kB1, (double)K1[J], Z[J]));
+                    Z[J] = z;
                     if constexpr (MIXED)
                         ZZ[J] = ff_axpy(ff_axpy(ZZ[J], (float)kB1, (float)K1[J]), (float)kB2, (float)x);
-                    else
-                        Z[J] = fma(kB2, (double)x, fma(kB1, (double)K1[J], Z[J]));
                 });
             } else {
                 lsweep<N, TK, KIND>(s, ax, luc, K0, K0, rank, gsize, gm, NoEpi());
@@ -1190,17 +1187,12 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
         }
     }
 
-    // Z at a node in FP64 (mixed: the value of the pair hi + lo)
-    auto zval = [&](int J) -> double {
-        if constexpr (MIXED) return (double)ZZ[J].x + (double)ZZ[J].y;
-        else return Z[J];
-    };
     // 3. keep the state (Y on Inner nodes) if asked
     if (a.flags & kStoreState) {
         for (int t = rank; t < s.L; t += gsize) {
             int j[N];
             decode<N>(s, t, j);
-            a.state[it.state_off + t] = payoff_at<N>(s, pay, P.payoff, j) + zval(s.padded(t));
+            a.state[it.state_off + t] = payoff_at<N>(s, pay, P.payoff, j) + Z[s.padded(t)];
         }
     }
     // 4. multilinear interpolation at the spot x* = (F_1(0), ..., V0)
@@ -1235,7 +1227,7 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
                 int t = 0;
 #pragma unroll
                 for (int i = 0; i < N; ++i) t += (jj[i] - 1) << s.sh[i];
-                zv = zval(s.padded(t));
+                zv = Z[s.padded(t)];
             }
             u += wt * (payoff_at<N>(s, pay, P.payoff, jj) + zv);
         }
