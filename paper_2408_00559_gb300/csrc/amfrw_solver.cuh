@@ -320,7 +320,9 @@ __device__ __noinline__ double payoff_H(const Shape<N>& s, const double* pay, in
 // axis k, the central difference D_k = X(J+E_k) - X(J-E_k) (zero on Outer
 // nodes and, by the ghost node Y_{J+E_k} = Y_{J-E_k}, zero on the upper face
 // of axis k).  Pass 2 combines, with per-node coefficients computed once per
-// grid (every coefficient of eqs. coef_diff/mix/adv carries V^2, folded in):
+// grid (every coefficient of eqs. coef_diff/mix/adv carries V^2, folded in,
+// and so is the time step, so that pass 2 gives dt F_0 and can start from the
+// stage's other terms):
 //   F_0(X)_J = sum_i d_i/h_i^2 (X+_i + X-_i) - 2 sum_i d_i/h_i^2 X_J
 //            + sum_{i<k} m_ik/(4 h_i h_k) (D_k(J+E_i) - D_k(J-E_i))
 //            + sum_i a_i/(2 h_i) D_i(J)
@@ -347,7 +349,7 @@ __device__ void build_node_coefs(const Shape<N>& s, const double* tabd, const Co
         int j[N];
         decode<N>(s, t, j);
         const int J = s.padded(t);
-        const double v2 = tabd[s.toff[N - 1] + j[N - 1] - 1];
+        const double v2 = tabd[s.toff[N - 1] + j[N - 1] - 1] * c.dt;  // dt V^2
         double sum = 0.0;
 #pragma unroll
         for (int i = 0; i < N - 1; ++i) {
@@ -375,10 +377,13 @@ __device__ void build_node_coefs(const Shape<N>& s, const double* tabd, const Co
                 C[(I::drift + i - 1) * Lp + J] = pwi * S * c.g2[i] * v2;
             }
         }
-        C[I::fg * Lp + J] = c.dt * v2 * H[t & (s.Lr - 1)];
+        C[I::fg * Lp + J] = v2 * H[t & (s.Lr - 1)];
     }
 }
 
+// Central differences D_k = X[J + E_k] - X[J - E_k] for axes k >= 1: the
+// cross terms read D_k for k > i >= 0 and the drift terms D_i for i >= 1, so
+// axis 0 is never read.
 template <int N>
 __device__ __forceinline__ void diff_pass(const Shape<N>& s, const double* X, double* D, int Lp,
                                           int rank, int gsize)
@@ -388,7 +393,7 @@ __device__ __forceinline__ void diff_pass(const Shape<N>& s, const double* X, do
         decode<N>(s, t, j);
         const int J = s.padded(t);
 #pragma unroll
-        for (int k = 0; k < N; ++k) {
+        for (int k = 1; k < N; ++k) {
             const bool top = j[k] == s.M[k];
             const double xm = (j[k] > 1) ? X[J - s.Sp[k]] : 0.0;
             D[k * Lp + J] = top ? 0.0 : X[J + s.Sp[k]] - xm;
@@ -398,10 +403,11 @@ __device__ __forceinline__ void diff_pass(const Shape<N>& s, const double* X, do
 
 template <int N>
 __device__ __forceinline__ double diff_F(const Shape<N>& s, const int (&j)[N], int J,
-                                         const double* X, const double* D, const double* C, int Lp)
+                                         const double* X, const double* D, const double* C, int Lp,
+                                         double init)
 {
     using I = CIdx<N>;
-    double f = C[I::ctr * Lp + J] * X[J];
+    double f = fma(C[I::ctr * Lp + J], X[J], init);
 #pragma unroll
     for (int i = 0; i < N; ++i) {
         const double xm = (j[i] > 1) ? X[J - s.Sp[i]] : 0.0;
@@ -1056,6 +1062,7 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
     const int Lr1 = s.Lr - 1;
     const TK* v2 = tabk + s.toff[N - 1] - 1;  // v2[j_V], 1-based
     const TK* luc = lu;
+    const double theta = P.theta;
 
     using CI = CIdx<N>;
     for (int n = 0; n < a.steps; ++n) {
@@ -1067,7 +1074,7 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
                 int j[N];
                 decode<N>(s, t, j);
                 const int J = s.padded(t);
-                K0[J] = (TK)(Cc[CI::fg * Lp + J] + cd->dt * diff_F<N>(s, j, J, Z, Dd, Cc, Lp));
+                K0[J] = (TK)diff_F<N>(s, j, J, Z, Dd, Cc, Lp, Cc[CI::fg * Lp + J]);
             }
         } else for (int t = rank; t < s.L; t += gsize) {
             int j[N];
@@ -1097,8 +1104,8 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
                 int j[N];
                 decode<N>(s, t, j);
                 const int J = s.padded(t);
-                const double f = diff_F<N>(s, j, J, (const double*)Kw, Dd, Cc, Lp);
-                K0[J] = (TK)(2.0 * (double)K0[J] - (double)Kw[J] + cd->thdt * f);
+                const double f = diff_F<N>(s, j, J, (const double*)Kw, Dd, Cc, Lp, 0.0);
+                K0[J] = (TK)(2.0 * (double)K0[J] - (double)Kw[J] + theta * f);
             }
         } else for (int t = rank; t < s.L; t += gsize) {
             int j[N];
@@ -1129,8 +1136,8 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
                 int j[N];
                 decode<N>(s, t, j);
                 const int J = s.padded(t);
-                const double f = diff_F<N>(s, j, J, (const double*)Kw, Dd, Cc, Lp);
-                K0[J] = (TK)(Cc[CI::fg * Lp + J] + cd->dt * f + kQ21 * (double)K1[J]);
+                K0[J] = (TK)diff_F<N>(s, j, J, (const double*)Kw, Dd, Cc, Lp,
+                                      fma(kQ21, (double)K1[J], Cc[CI::fg * Lp + J]));
             }
         } else for (int t = rank; t < s.L; t += gsize) {
             int j[N];
@@ -1160,8 +1167,8 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
                 int j[N];
                 decode<N>(s, t, j);
                 const int J = s.padded(t);
-                const double f = diff_F<N>(s, j, J, (const double*)Kw, Dd, Cc, Lp);
-                K0[J] = (TK)(2.0 * (double)K0[J] - (double)Kw[J] + cd->thdt * f);
+                const double f = diff_F<N>(s, j, J, (const double*)Kw, Dd, Cc, Lp, 0.0);
+                K0[J] = (TK)(2.0 * (double)K0[J] - (double)Kw[J] + theta * f);
             }
         } else for (int t = rank; t < s.L; t += gsize) {
             int j[N];
