@@ -191,8 +191,9 @@ __device__ __forceinline__ TC stencil_acc(const Shape<N>& s, const int (&j)[N], 
     for (int i = 0; i < N - 1; ++i) acc += tab[s.toff[i] + j[i] - 1] * lap[i];
 #pragma unroll
     for (int i = 0; i < N - 1; ++i) {
-        TC inner = TC(0);
+        // cross and drift terms of rate i: zero on its upper face
         if (j[i] != s.M[i]) {
+            TC inner = TC(0);
             const bool li = j[i] > 1;
 #pragma unroll
             for (int k = i + 1; k < N; ++k) {
@@ -208,14 +209,14 @@ __device__ __forceinline__ TC stencil_acc(const Shape<N>& s, const int (&j)[N], 
                     inner += ck * mix;
                 }
             }
-        }
-        if (i >= 1) {  // drift of rates 2..N-1 (eq. coef_adv), sum over rates 2..i
-            TC S = TC(0);
+            if (i >= 1) {  // drift of rates 2..N-1 (eq. coef_adv), sum over rates 2..i
+                TC S = TC(0);
 #pragma unroll
-            for (int r = 1; r <= i; ++r) S += c.rh[ltri(i, r)] * tab[s.toff[r] + 2 * s.M[r] + j[r] - 1];
-            inner += S * c.g2[i] * grad[i];
+                for (int r = 1; r <= i; ++r) S += c.rh[ltri(i, r)] * tab[s.toff[r] + 2 * s.M[r] + j[r] - 1];
+                inner += S * c.g2[i] * grad[i];
+            }
+            acc += tab[s.toff[i] + s.M[i] + j[i] - 1] * inner;
         }
-        acc += tab[s.toff[i] + s.M[i] + j[i] - 1] * inner;
     }
     return acc;
 }
@@ -381,9 +382,12 @@ __device__ void build_node_coefs(const Shape<N>& s, const double* tabd, const Co
     }
 }
 
-// Central differences D_k = X[J + E_k] - X[J - E_k] for axes k >= 1: the
-// cross terms read D_k for k > i >= 0 and the drift terms D_i for i >= 1, so
-// axis 0 is never read.
+// Central differences D_k = X[J + E_k] - X[J - E_k] for axes k >= 1, off
+// the upper face of axis k.  The cross terms read D_k for k > i >= 0 and the
+// drift terms D_i for i >= 1, both only off that face (where Sketch 1 sets
+// them to zero), so axis 0 and the upper-face entries are never read.  On an
+// axis with a single Inner row (M_k = 1) every node is on the upper face, and
+// the whole pass along it is skipped alike by every lane of the grid.
 template <int N>
 __device__ __forceinline__ void diff_pass(const Shape<N>& s, const double* X, double* D, int Lp,
                                           int rank, int gsize)
@@ -394,13 +398,18 @@ __device__ __forceinline__ void diff_pass(const Shape<N>& s, const double* X, do
         const int J = s.padded(t);
 #pragma unroll
         for (int k = 1; k < N; ++k) {
-            const bool top = j[k] == s.M[k];
-            const double xm = (j[k] > 1) ? X[J - s.Sp[k]] : 0.0;
-            D[k * Lp + J] = top ? 0.0 : X[J + s.Sp[k]] - xm;
+            if (j[k] != s.M[k]) {
+                const double xm = (j[k] > 1) ? X[J - s.Sp[k]] : 0.0;
+                D[k * Lp + J] = X[J + s.Sp[k]] - xm;
+            }
         }
     }
 }
 
+// dt F_0(X) at the Inner node J, plus init.  Terms that vanish are skipped:
+// the neighbour sum along an axis with one Inner row (both neighbours are
+// zero: an Outer node and its ghost reflection; the centre term keeps its
+// part), and the cross and drift terms on the upper face of their axes.
 template <int N>
 __device__ __forceinline__ double diff_F(const Shape<N>& s, const int (&j)[N], int J,
                                          const double* X, const double* D, const double* C, int Lp,
@@ -410,9 +419,11 @@ __device__ __forceinline__ double diff_F(const Shape<N>& s, const int (&j)[N], i
     double f = fma(C[I::ctr * Lp + J], X[J], init);
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-        const double xm = (j[i] > 1) ? X[J - s.Sp[i]] : 0.0;
-        const double xp = (j[i] == s.M[i]) ? xm : X[J + s.Sp[i]];
-        f += C[(I::diag + i) * Lp + J] * (xp + xm);
+        if (s.M[i] > 1) {
+            const double xm = (j[i] > 1) ? X[J - s.Sp[i]] : 0.0;
+            const double xp = (j[i] == s.M[i]) ? xm : X[J + s.Sp[i]];
+            f += C[(I::diag + i) * Lp + J] * (xp + xm);
+        }
     }
 #pragma unroll
     for (int i = 0; i < N - 1; ++i) {
@@ -420,14 +431,17 @@ __device__ __forceinline__ double diff_F(const Shape<N>& s, const int (&j)[N], i
             const bool li = j[i] > 1;
 #pragma unroll
             for (int k = i + 1; k < N; ++k) {
-                const double dp = D[k * Lp + J + s.Sp[i]];
-                const double dm = li ? D[k * Lp + J - s.Sp[i]] : 0.0;
-                f += C[I::pair(i, k) * Lp + J] * (dp - dm);
+                if (j[k] != s.M[k]) {
+                    const double dp = D[k * Lp + J + s.Sp[i]];
+                    const double dm = li ? D[k * Lp + J - s.Sp[i]] : 0.0;
+                    f += C[I::pair(i, k) * Lp + J] * (dp - dm);
+                }
             }
         }
     }
 #pragma unroll
-    for (int i = 1; i < N - 1; ++i) f += C[(I::drift + i - 1) * Lp + J] * D[i * Lp + J];
+    for (int i = 1; i < N - 1; ++i)
+        if (j[i] != s.M[i]) f += C[(I::drift + i - 1) * Lp + J] * D[i * Lp + J];
     return f;
 }
 
