@@ -57,11 +57,12 @@ struct Shape {
     int plog[N];   // log2 lanes per line in the directional solves
     int luS[N];    // factor values per matrix row (2 plog + 3)
     int L, Lr, pad, phalf;
+    int skip;      // rate axes with one Inner row whose solves are folded into the V solve
     __device__ __forceinline__ int padded(int t) const { return t + pad * (t >> lv[0]); }
 };
 
 template <int N>
-__device__ __forceinline__ void make_shape(Shape<N>& s, const int8_t* lv, int tlog, int rlog)
+__device__ __forceinline__ void make_shape(Shape<N>& s, const int8_t* lv, int tlog, int rlog, bool fold)
 {
     int sh = 0;
 #pragma unroll
@@ -99,6 +100,10 @@ __device__ __forceinline__ void make_shape(Shape<N>& s, const int8_t* lv, int tl
         s.luoff[i] = lo;
         lo += ((i < N - 1 ? s.M[N - 1] : 1) << s.lv[i]) * s.luS[i];
     }
+    s.skip = 0;
+#pragma unroll
+    for (int i = 0; i < N - 1; ++i)
+        if (fold && s.M[i] == 1) s.skip |= 1 << i;
 }
 
 template <int N>
@@ -487,6 +492,25 @@ __device__ __forceinline__ void matrix_row(const Shape<N>& s, const double* tabd
     a = (r == 0) ? 0.0 : ((r < M - 1) ? -nd : -2.0 * nd);
 }
 
+// A rate axis with one Inner row (M_i = 1) has the 1x1 directional matrix
+// b_i = 1 + 2 nu dt delta_i, which depends on the V index only: its solve is
+// the scaling by 1/b_i(j_V).  These scalings commute with the solves along
+// the other rate axes (which keep j_V), so they are applied together inside
+// the V solve instead: solving (I - nu dt A_V) x = S g with S = prod 1/b_i is
+// solving (S^-1 (I - nu dt A_V)) x = g, whose row r is the V matrix row times
+// prod_i b_i(r).  This returns that product for V row r (1 when none is
+// folded).
+template <int N>
+__device__ __forceinline__ double fold_scale(const Shape<N>& s, const double* tabd,
+                                             const Consts<double>& c, int r)
+{
+    double f = 1.0;
+#pragma unroll
+    for (int i = 0; i < N - 1; ++i)
+        if ((s.skip >> i) & 1) f *= 1.0 + 2.0 * (c.nudt * (tabd[s.toff[i]] * tabd[s.toff[N - 1] + r]));
+    return f;
+}
+
 // The PCR multipliers and Thomas factors of every line class: the same
 // reduction as the solve, applied to the matrix coefficients (FP64).  Rows
 // are updated in ascending order; each lane keeps the pre-update values of
@@ -512,8 +536,17 @@ __device__ void pcr_setup(const Shape<N>& s, const double* tabd, const Consts<do
             T* tb = lu + s.luoff[axis] + (cl * M + p) * S;
             double a[RMAX], b[RMAX], u[RMAX];
 #pragma unroll
-            for (int q = 0; q < RMAX; ++q)
-                if (q < R) matrix_row<N>(s, tabd, c, axis, cl, p + P * q, a[q], b[q], u[q]);
+            for (int q = 0; q < RMAX; ++q) {
+                if (q < R) {
+                    matrix_row<N>(s, tabd, c, axis, cl, p + P * q, a[q], b[q], u[q]);
+                    if (axis == N - 1 && s.skip) {  // the folded single-row rate solves
+                        const double f = fold_scale<N>(s, tabd, c, p + P * q);
+                        a[q] *= f;
+                        b[q] *= f;
+                        u[q] *= f;
+                    }
+                }
+            }
             for (int k = 0; k < plog; ++k) {
                 const int d = 1 << k;
                 const int sm = (p - d) & (P - 1), sp = (p + d) & (P - 1);
@@ -989,11 +1022,13 @@ __device__ __forceinline__ void sweeps_into(const Shape<N>& s, const TK* lu, con
                                             int rank, int gsize, unsigned gm)
 {
     constexpr bool WARP = KIND == kWarpGroup;
-    lsweep<N, TK, KIND>(s, 0, lu, from, to, rank, gsize, gm, NoEpi());
-    gsync<WARP>(gm);
-    for (int ax = 1; ax < N; ++ax) {
-        lsweep<N, TK, KIND>(s, ax, lu, to, to, rank, gsize, gm, NoEpi());
+    const TK* src = from;
+#pragma unroll
+    for (int ax = 0; ax < N; ++ax) {
+        if ((s.skip >> ax) & 1) continue;  // folded into the V solve
+        lsweep<N, TK, KIND>(s, ax, lu, src, to, rank, gsize, gm, NoEpi());
         gsync<WARP>(gm);
+        src = to;
     }
 }
 
@@ -1009,7 +1044,7 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
     const int tlog = 31 - __clz(gsize);
     const unsigned gm = WARP ? group_mask(tlog) : 0xffffffffu;
     Shape<N> s;
-    make_shape<N>(s, it.lv, tlog, rows_log(KIND));
+    make_shape<N>(s, it.lv, tlog, rows_log(KIND), KIND != kMemGroup);
     const Layout lay = make_layout(N, it.lv, MIXED, KIND, tlog);
     Consts<double>* cd = reinterpret_cast<Consts<double>*>(base + lay.cd);
     Consts<TK>* ck = MIXED ? reinterpret_cast<Consts<TK>*>(base + lay.cf)
@@ -1129,18 +1164,22 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
             K0[J] = TK(2) * K0[J] - Kw[J] + ck->thdt * v2[j[N - 1]] * acc;
         }
         gsync<WARP>(gm);
-        // N solves into K1; the last one also forms the stage-2 argument
-        lsweep<N, TK, KIND>(s, 0, luc, K0, K1, rank, gsize, gm, NoEpi());
-        gsync<WARP>(gm);
-        for (int ax = 1; ax < N; ++ax) {
-            if (!MIXED && ax == N - 1) {  // FP64: Kw = Z + a21 K1
-                lsweep<N, TK, KIND>(s, ax, luc, K1, K1, rank, gsize, gm, [=](int J, TK x) {
-                    Kw[J] = (TK)(Z[J] + kA21 * (double)x);
-                });
-            } else {
-                lsweep<N, TK, KIND>(s, ax, luc, K1, K1, rank, gsize, gm, NoEpi());
+        // N solves into K1 (single-row rate axes folded into the V solve); the
+        // last one also forms the stage-2 argument
+        {
+            const TK* src = K0;
+            for (int ax = 0; ax < N; ++ax) {
+                if ((s.skip >> ax) & 1) continue;
+                if (!MIXED && ax == N - 1) {  // FP64: Kw = Z + a21 K1
+                    lsweep<N, TK, KIND>(s, ax, luc, src, K1, rank, gsize, gm, [=](int J, TK x) {
+                        Kw[J] = (TK)(Z[J] + kA21 * (double)x);
+                    });
+                } else {
+                    lsweep<N, TK, KIND>(s, ax, luc, src, K1, rank, gsize, gm, NoEpi());
+                }
+                gsync<WARP>(gm);
+                src = K1;
             }
-            gsync<WARP>(gm);
         }
         // ---- stage 2: K^(0) = dt F(Y_n + a21 K1) + q21 K1
         if constexpr (DIFF) {
@@ -1194,6 +1233,7 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
         gsync<WARP>(gm);
         // N solves in place; the last one accumulates Y_{n+1} = Y_n + b1 K1 + b2 K2
         for (int ax = 0; ax < N; ++ax) {
+            if ((s.skip >> ax) & 1) continue;
             if (ax == N - 1) {
                 lsweep<N, TK, KIND>(s, ax, luc, K0, K0, rank, gsize, gm, [=](int J, TK x) {
                     const double z = fma(kB2, (double)x, fma(kB1, (double)K1[J], Z[J]));
