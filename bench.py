@@ -107,8 +107,10 @@ def node_flops(levels, steps):
     2i+3 when not on its upper face, 2 per rate axis for the outer
     coefficient FMA and 2(N-1)+1 for the diagonal coefficients; 4 F
     evaluations per step plus 4 (stage-argument) and 5 (refinement) per
-    node for the fused stage algebra, 5 per row of each of the 4N Thomas
-    sweeps, and 6 for the two fused updates."""
+    node for the fused stage algebra, 5M - 4 per line of M rows for each of
+    the 4N Thomas solves with precomputed factors (a forward multiply-add and
+    a backward multiply-add and multiply per row; a single row is one
+    multiply), and 6 for the two fused updates."""
     N = len(levels)
     M = [1 << int(l) for l in levels]
     axes = [np.arange(1, m + 1) for m in M]
@@ -122,7 +124,8 @@ def node_flops(levels, steps):
         for k in range(i + 1, N):
             both = nt[i] & nt[k]
             f += both * (3 + (3 if k < N - 1 else 2))
-    per_step = 4 * f.sum() + f.size * (2 * 4 + 2 * 5 + 20 * N + 6)
+    thomas = sum(4 * (5 - 4 / m) for m in M)  # per node: 4 solves along each axis
+    per_step = 4 * f.sum() + f.size * (2 * 4 + 2 * 5 + thomas + 6)
     return float(per_step) * steps
 
 
