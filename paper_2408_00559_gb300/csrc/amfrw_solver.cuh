@@ -57,12 +57,14 @@ struct Shape {
     int plog[N];   // log2 lanes per line in the directional solves
     int luS[N];    // factor values per matrix row (2 plog + 3)
     int L, Lr, pad, phalf;
-    int skip;      // rate axes with one Inner row whose solves are folded into the V solve
+    int skip;      // axes whose single-row solves are folded into the solve along `last`
+    int last;      // the last axis solved in a stage (carries the stage's epilogue)
     __device__ __forceinline__ int padded(int t) const { return t + pad * (t >> lv[0]); }
 };
 
 template <int N>
-__device__ __forceinline__ void make_shape(Shape<N>& s, const int8_t* lv, int tlog, int rlog, bool fold)
+__device__ __forceinline__ void make_shape(Shape<N>& s, const int8_t* lv, int tlog, int rlog, bool fold,
+                                           bool fold_v)
 {
     int sh = 0;
 #pragma unroll
@@ -101,9 +103,17 @@ __device__ __forceinline__ void make_shape(Shape<N>& s, const int8_t* lv, int tl
         lo += ((i < N - 1 ? s.M[N - 1] : 1) << s.lv[i]) * s.luS[i];
     }
     s.skip = 0;
+    s.last = N - 1;
+    int lastr = -1;  // the last rate axis with more than one row
 #pragma unroll
-    for (int i = 0; i < N - 1; ++i)
+    for (int i = 0; i < N - 1; ++i) {
         if (fold && s.M[i] == 1) s.skip |= 1 << i;
+        if (s.M[i] > 1) lastr = i;
+    }
+    if (fold && fold_v && s.M[N - 1] == 1 && lastr >= 0) {
+        s.skip |= 1 << (N - 1);
+        s.last = lastr;
+    }
 }
 
 template <int N>
@@ -492,22 +502,26 @@ __device__ __forceinline__ void matrix_row(const Shape<N>& s, const double* tabd
     a = (r == 0) ? 0.0 : ((r < M - 1) ? -nd : -2.0 * nd);
 }
 
-// A rate axis with one Inner row (M_i = 1) has the 1x1 directional matrix
-// b_i = 1 + 2 nu dt delta_i, which depends on the V index only: its solve is
-// the scaling by 1/b_i(j_V).  These scalings commute with the solves along
-// the other rate axes (which keep j_V), so they are applied together inside
-// the V solve instead: solving (I - nu dt A_V) x = S g with S = prod 1/b_i is
-// solving (S^-1 (I - nu dt A_V)) x = g, whose row r is the V matrix row times
-// prod_i b_i(r).  This returns that product for V row r (1 when none is
-// folded).
+// An axis with one Inner row (M_i = 1) has a 1x1 directional matrix
+// b_i = 1 + 2 nu dt delta_i, which for a rate axis depends on the V index
+// only, so its solve is the scaling by 1/b_i(j_V).  These scalings commute
+// with the solves along the other rate axes (which keep j_V), so they are
+// applied together inside one other solve: solving (I - nu dt A_a) x = S g
+// with S = prod 1/b_i is solving (S^-1 (I - nu dt A_a)) x = g, whose matrix
+// rows are those of axis a times prod_i b_i.  The target a (`last`) is the V
+// axis, or, when V has one row too (then every b_i is a constant), the last
+// rate axis with more than one row.  This returns that product for row r of
+// line class cls of the target axis.
 template <int N>
 __device__ __forceinline__ double fold_scale(const Shape<N>& s, const double* tabd,
-                                             const Consts<double>& c, int r)
+                                             const Consts<double>& c, int axis, int cls, int r)
 {
+    const int v = (axis == N - 1) ? r : cls;  // V index of the row
     double f = 1.0;
 #pragma unroll
     for (int i = 0; i < N - 1; ++i)
-        if ((s.skip >> i) & 1) f *= 1.0 + 2.0 * (c.nudt * (tabd[s.toff[i]] * tabd[s.toff[N - 1] + r]));
+        if ((s.skip >> i) & 1) f *= 1.0 + 2.0 * (c.nudt * (tabd[s.toff[i]] * tabd[s.toff[N - 1] + v]));
+    if ((s.skip >> (N - 1)) & 1) f *= 1.0 + 2.0 * (c.nudt * (c.cV * tabd[s.toff[N - 1]]));
     return f;
 }
 
@@ -539,8 +553,8 @@ __device__ void pcr_setup(const Shape<N>& s, const double* tabd, const Consts<do
             for (int q = 0; q < RMAX; ++q) {
                 if (q < R) {
                     matrix_row<N>(s, tabd, c, axis, cl, p + P * q, a[q], b[q], u[q]);
-                    if (axis == N - 1 && s.skip) {  // the folded single-row rate solves
-                        const double f = fold_scale<N>(s, tabd, c, p + P * q);
+                    if (axis == s.last && s.skip) {  // the folded single-row solves
+                        const double f = fold_scale<N>(s, tabd, c, axis, cl, p + P * q);
                         a[q] *= f;
                         b[q] *= f;
                         u[q] *= f;
@@ -1025,7 +1039,7 @@ __device__ __forceinline__ void sweeps_into(const Shape<N>& s, const TK* lu, con
     const TK* src = from;
 #pragma unroll
     for (int ax = 0; ax < N; ++ax) {
-        if ((s.skip >> ax) & 1) continue;  // folded into the V solve
+        if ((s.skip >> ax) & 1) continue;  // folded into the solve along s.last
         lsweep<N, TK, KIND>(s, ax, lu, src, to, rank, gsize, gm, NoEpi());
         gsync<WARP>(gm);
         src = to;
@@ -1044,7 +1058,12 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
     const int tlog = 31 - __clz(gsize);
     const unsigned gm = WARP ? group_mask(tlog) : 0xffffffffu;
     Shape<N> s;
-    make_shape<N>(s, it.lv, tlog, rows_log(KIND), KIND != kMemGroup);
+    // single-row solves are folded into another solve (not for global-memory
+    // groups); into a rate-axis solve only where the register sweep is called
+    // out of line (N <= 4), since the epilogue then moves to a runtime axis
+    constexpr bool kFoldV = N <= 4 && KIND != kMemGroup;
+    make_shape<N>(s, it.lv, tlog, rows_log(KIND), KIND != kMemGroup, kFoldV);
+    const int last = kFoldV ? s.last : N - 1;  // the axis whose solve carries the epilogues
     const Layout lay = make_layout(N, it.lv, MIXED, KIND, tlog);
     Consts<double>* cd = reinterpret_cast<Consts<double>*>(base + lay.cd);
     Consts<TK>* ck = MIXED ? reinterpret_cast<Consts<TK>*>(base + lay.cf)
@@ -1164,13 +1183,13 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
             K0[J] = TK(2) * K0[J] - Kw[J] + ck->thdt * v2[j[N - 1]] * acc;
         }
         gsync<WARP>(gm);
-        // N solves into K1 (single-row rate axes folded into the V solve); the
-        // last one also forms the stage-2 argument
+        // N solves into K1 (single-row axes folded into the solve along
+        // `last`); the last one also forms the stage-2 argument
         {
             const TK* src = K0;
             for (int ax = 0; ax < N; ++ax) {
                 if ((s.skip >> ax) & 1) continue;
-                if (!MIXED && ax == N - 1) {  // FP64: Kw = Z + a21 K1
+                if (!MIXED && ax == last) {  // FP64: Kw = Z + a21 K1
                     lsweep<N, TK, KIND>(s, ax, luc, src, K1, rank, gsize, gm, [=](int J, TK x) {
                         Kw[J] = (TK)(Z[J] + kA21 * (double)x);
                     });
@@ -1234,7 +1253,7 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
         // N solves in place; the last one accumulates Y_{n+1} = Y_n + b1 K1 + b2 K2
         for (int ax = 0; ax < N; ++ax) {
             if ((s.skip >> ax) & 1) continue;
-            if (ax == N - 1) {
+            if (ax == last) {
                 lsweep<N, TK, KIND>(s, ax, luc, K0, K0, rank, gsize, gm, [=](int J, TK x) {
                     const double z = fma(kB2, (double)x, fma(kB1, (double)K1[J], Z[J]));
                     Z[J] = z;
