@@ -95,6 +95,7 @@ CASES = [
     (8, 4, 0, False, "swaption", 2),
     (8, 1, 0, False, "swaption", 3),      # level below d-1: only q <= 1 grids
     (4, 0, 0, False, "swaption", 2),      # all axes degenerate (M_i = 1)
+    (4, 7, 0, False, "swaption", 2),      # CTA groups (128 nodes) with single-row axes: folded solves
 ]
 
 
@@ -177,8 +178,8 @@ def test_c2_batch_sampled_against_oracle():
 
 
 # ------------------------------------------------------------------ mixed
-@pytest.mark.parametrize("case", [(4, 3, 0), (6, 2, 1), (8, 3, 0), (3, 4, 1)],
-                         ids=["N4_n3", "N6_n2_psi1", "N8_n3", "N3_n4_psi1"])
+@pytest.mark.parametrize("case", [(4, 3, 0), (6, 2, 1), (8, 3, 0), (3, 4, 1), (4, 7, 0)],
+                         ids=["N4_n3", "N6_n2_psi1", "N8_n3", "N3_n4_psi1", "N4_n7_cta"])
 def test_mixed_precision_price(case):
     N, n, psi = case
     inst = W.small_instance(N, n, psi=psi, steps=10, seed=500 + N, precision="mixed")
