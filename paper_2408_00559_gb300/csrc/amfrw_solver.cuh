@@ -1275,8 +1275,12 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
             a.state[it.state_off + t] = payoff_at<N>(s, pay, P.payoff, j) + Z[s.padded(t)];
         }
     }
-    // 4. multilinear interpolation at the spot x* = (F_1(0), ..., V0)
-    if (rank == 0) {
+    // 4. multilinear interpolation at the spot x* = (F_1(0), ..., V0).  The
+    // 2^N corners of the containing cell are shared among up to 32 lanes of
+    // the group (a whole warp group, or the first warp of a CTA), which sum
+    // them by a shuffle reduction; corners of weight zero are skipped.
+    const int il = gsize < 32 ? gsize : 32;
+    if (rank < il) {
         int c[N];
         double w[N];
 #pragma unroll
@@ -1291,7 +1295,7 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
             w[i] = sx - (double)ci;
         }
         double u = 0.0;
-        for (int corner = 0; corner < (1 << N); ++corner) {
+        for (int corner = rank; corner < (1 << N); corner += il) {
             double wt = 1.0;
             int jj[N];
             bool outer = false;
@@ -1302,6 +1306,7 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
                 jj[i] = c[i] + bit;
                 outer |= jj[i] == 0;
             }
+            if (wt == 0.0) continue;
             double zv = 0.0;
             if (!outer) {
                 int t = 0;
@@ -1311,7 +1316,9 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
             }
             u += wt * (payoff_at<N>(s, pay, P.payoff, jj) + zv);
         }
-        a.u_out[it.out_idx] = u;
+        const unsigned im = WARP ? gm : 0xffffffffu;
+        for (int off = il >> 1; off > 0; off >>= 1) u += __shfl_xor_sync(im, u, off, il);
+        if (rank == 0) a.u_out[it.out_idx] = u;
     }
     gsync<WARP>(gm);  // the group's shared memory is reused by its next grid
 }
