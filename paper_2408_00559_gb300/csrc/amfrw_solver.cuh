@@ -945,8 +945,11 @@ __device__ void build_tables(const Shape<N>& s, const InstDev& P, double* tabd, 
         const double raa = P.rho[a * kMaxDim + a];
         for (int jj = 1 + rank; jj <= M; jj += gsize) {
             const double F = (double)jj * h;
-            const double Fb = pow(F, beta);
-            tabd[s.toff[a] + jj - 1] = 0.5 * al * al * raa * pow(F, 2.0 * beta) / (h * h);
+            // F^beta and F^(2 beta); beta = 1/2 (the usual SABR choice) by a square root
+            const bool half = beta == 0.5;
+            const double Fb = half ? sqrt(F) : pow(F, beta);
+            const double F2b = half ? F : pow(F, 2.0 * beta);
+            tabd[s.toff[a] + jj - 1] = 0.5 * al * al * raa * F2b / (h * h);
             tabd[s.toff[a] + M + jj - 1] = al * Fb;
             tabd[s.toff[a] + 2 * M + jj - 1] = al * ta * Fb / (1.0 + ta * F);
         }
@@ -964,29 +967,41 @@ __device__ void build_tables(const Shape<N>& s, const InstDev& P, double* tabd, 
             tabd[s.toff[N - 1] + jj - 1] = V * V;
         }
     }
-    if (rank == 0) {
-        double h[kMaxDim];
-#pragma unroll
-        for (int i = 0; i < kMaxDim; ++i) h[i] = (i < N) ? P.Fmax[i] / (double)s.M[i < N ? i : 0] : 1.0;
-        const double hV = h[N - 1];
-        cd->cV = 0.5 * P.sigma * P.sigma / (hV * hV);
-        cd->dt = P.dt;
-        cd->thdt = P.theta * P.dt;
-        cd->nudt = P.nu * P.dt;
-#pragma unroll
-        for (int i = 0; i < kMaxDim; ++i) {
-#pragma unroll
-            for (int k = i + 1; k < kMaxDim; ++k) {
-                const bool ok = i < N - 1 && k < N - 1;
-                cd->rm[upair(i, k)] = ok ? P.rho[i * kMaxDim + k] / (4.0 * h[i] * h[k]) : 0.0;
+    // the constants, one entry per lane at a time (each entry divides once)
+    constexpr int kPairs = kMaxDim * (kMaxDim - 1) / 2, kTri = kMaxDim * (kMaxDim + 1) / 2;
+    constexpr int kConsts = 1 + kPairs + kTri + 2 * kMaxDim;
+    auto hh = [&](int i) {  // h_i = Fmax_i / M_i, by an exact power of two
+        return P.Fmax[i] * __longlong_as_double((long long)(1023 - s.lv[i]) << 52);
+    };
+    for (int q = rank; q < kConsts; q += gsize) {
+        if (q == 0) {
+            const double hV = hh(N - 1);
+            cd->cV = 0.5 * P.sigma * P.sigma / (hV * hV);
+            cd->dt = P.dt;
+            cd->thdt = P.theta * P.dt;
+            cd->nudt = P.nu * P.dt;
+        } else if (q <= kPairs) {  // rm[upair(i, k)], i < k
+            int i = 0, r = q - 1;
+            while (r >= kMaxDim - 1 - i) {
+                r -= kMaxDim - 1 - i;
+                ++i;
             }
-#pragma unroll
-            for (int r = 0; r <= i; ++r) {
-                const bool ok = i < N - 1;
-                cd->rh[ltri(i, r)] = ok ? P.rho[i * kMaxDim + r] : 0.0;
+            const int k = i + 1 + r;
+            const bool ok = i < N - 1 && k < N - 1;
+            cd->rm[upair(i, k)] = ok ? P.rho[i * kMaxDim + k] / (4.0 * hh(i) * hh(k)) : 0.0;
+        } else if (q <= kPairs + kTri) {  // rh[ltri(i, r)], r <= i
+            int i = 0, r = q - 1 - kPairs;
+            while (r > i) {
+                r -= i + 1;
+                ++i;
             }
-            cd->sm[i] = (i < N - 1) ? P.sigma * P.phi[i] / (4.0 * h[i] * hV) : 0.0;
-            cd->g2[i] = (i < N) ? 1.0 / (2.0 * h[i]) : 0.0;
+            cd->rh[ltri(i, r)] = (i < N - 1) ? P.rho[i * kMaxDim + r] : 0.0;
+        } else if (q <= kPairs + kTri + kMaxDim) {
+            const int i = q - 1 - kPairs - kTri;
+            cd->sm[i] = (i < N - 1) ? P.sigma * P.phi[i] / (4.0 * hh(i) * hh(N - 1)) : 0.0;
+        } else {
+            const int i = q - 1 - kPairs - kTri - kMaxDim;
+            cd->g2[i] = (i < N) ? 1.0 / (2.0 * hh(i)) : 0.0;
         }
     }
 }
