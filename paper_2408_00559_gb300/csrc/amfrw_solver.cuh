@@ -567,7 +567,12 @@ __device__ void pcr_setup(const Shape<N>& s, const double* tabd, const Consts<do
                 const bool wm = p < d, wp = p + d >= P;      // this lane receives across a wrap
                 const bool send_prev = p >= P - d;          // my receiver (p + d) wraps
                 const bool send_next = p < d;               // my receiver (p - d) wraps
-                double pa = 0.0, pb = 1.0, pu = 0.0;         // pre-update values of row q-1
+                // reciprocals of this level's diagonals (one division per row;
+                // the neighbours' reciprocals arrive by shuffle)
+                double rb[RMAX];
+#pragma unroll
+                for (int q = 0; q < RMAX; ++q) rb[q] = (q < R) ? 1.0 / b[q] : 1.0;
+                double pa = 0.0, prb = 1.0, pu = 0.0;        // pre-update values of row q-1
 #pragma unroll
                 for (int q = 0; q < RMAX; ++q) {
                     if (q < R) {
@@ -575,21 +580,21 @@ __device__ void pcr_setup(const Shape<N>& s, const double* tabd, const Consts<do
                         const bool nx = q + 1 < R;
                         // to the lane above (p + d): my row q, or my row q-1 across the wrap
                         const double a_m = shfl(send_prev ? pa : a[q], sm, P, gm);
-                        const double b_m = shfl(send_prev ? pb : b[q], sm, P, gm);
+                        const double rb_m = shfl(send_prev ? prb : rb[q], sm, P, gm);
                         const double u_m = shfl(send_prev ? pu : u[q], sm, P, gm);
                         // to the lane below (p - d): my row q, or my row q+1 across the wrap
                         const double a_p = shfl(send_next ? (nx ? a[qn] : 0.0) : a[q], sp, P, gm);
-                        const double b_p = shfl(send_next ? (nx ? b[qn] : 1.0) : b[q], sp, P, gm);
+                        const double rb_p = shfl(send_next ? (nx ? rb[qn] : 1.0) : rb[q], sp, P, gm);
                         const double u_p = shfl(send_next ? (nx ? u[qn] : 0.0) : u[q], sp, P, gm);
                         const bool hm = !wm || q >= 1;
-                        const double al = hm ? a[q] / b_m : 0.0;
-                        const double ga = u[q] / b_p;  // identity row sent past the end
+                        const double al = hm ? a[q] * rb_m : 0.0;
+                        const double ga = u[q] * rb_p;  // identity row sent past the end
                         if (act) {
                             tb[q * P * S + 2 * k] = (T)al;
                             tb[q * P * S + 2 * k + 1] = (T)(wp && !nx ? 0.0 : ga);
                         }
                         pa = a[q];
-                        pb = b[q];
+                        prb = rb[q];
                         pu = u[q];
                         const double gg = (wp && !nx) ? 0.0 : ga;
                         b[q] = b[q] - al * u_m - gg * a_p;
@@ -942,21 +947,21 @@ __device__ void build_tables(const Shape<N>& s, const InstDev& P, double* tabd, 
         const int M = s.M[a];
         const double h = P.Fmax[a] / (double)M;
         const double al = P.alpha[a], ta = P.tau[a];
-        const double raa = P.rho[a * kMaxDim + a];
-        for (int jj = 1 + rank; jj <= M; jj += gsize) {
-            const double F = (double)jj * h;
-            // F^beta and F^(2 beta); beta = 1/2 (the usual SABR choice) by a square root
-            const bool half = beta == 0.5;
-            const double Fb = half ? sqrt(F) : pow(F, beta);
-            const double F2b = half ? F : pow(F, 2.0 * beta);
-            tabd[s.toff[a] + jj - 1] = 0.5 * al * al * raa * F2b / (h * h);
-            tabd[s.toff[a] + M + jj - 1] = al * Fb;
-            tabd[s.toff[a] + 2 * M + jj - 1] = al * ta * Fb / (1.0 + ta * F);
-        }
+        const double dcoef = 0.5 * al * al * P.rho[a * kMaxDim + a] / (h * h);
         for (int jj = rank; jj <= M; jj += gsize) {
             const double F = (double)jj * h;
+            const double bF = 1.0 / (1.0 + ta * F);  // discount factor of the accrual period
             pay[s.poff[a] + jj] = (P.payoff == 0) ? (F - P.K) : ta * (F - P.K);
-            pay[s.phalf + s.poff[a] + jj] = 1.0 / (1.0 + ta * F);
+            pay[s.phalf + s.poff[a] + jj] = bF;
+            if (jj >= 1) {
+                // F^beta and F^(2 beta); beta = 1/2 (the usual SABR choice) by a square root
+                const bool half = beta == 0.5;
+                const double Fb = half ? sqrt(F) : pow(F, beta);
+                const double F2b = half ? F : pow(F, 2.0 * beta);
+                tabd[s.toff[a] + jj - 1] = dcoef * F2b;
+                tabd[s.toff[a] + M + jj - 1] = al * Fb;
+                tabd[s.toff[a] + 2 * M + jj - 1] = al * ta * Fb * bF;
+            }
         }
     }
     {
@@ -1301,8 +1306,7 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
 #pragma unroll
         for (int i = 0; i < N; ++i) {
             const double x = (i < N - 1) ? P.F0[i] : P.V0;
-            const double h = P.Fmax[i] / (double)s.M[i];
-            const double sx = x / h;
+            const double sx = x / P.Fmax[i] * (double)s.M[i];  // x / h_i, h_i = Fmax_i / M_i
             int ci = (int)floor(sx);
             ci = ci > s.M[i] - 1 ? s.M[i] - 1 : ci;
             ci = ci < 0 ? 0 : ci;
