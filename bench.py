@@ -56,10 +56,10 @@ WORKLOAD = ("c2: d=4 (3 forward rates + V) SABR-LMM swaption, standard combinati
 FP64_PEAK = 152 * 2 * 2 * 2070e6  # SMs x DFMA/clk x FLOP/FMA x max SM clock
 # DRAM bytes (read + write) of the C2 FP64 solver launches of one batch, per
 # instance: one ncu capture of the four per-class launches of a 256-instance
-# batch (dram__bytes_read.sum 833 536 + 733 184 + 545 280 + 451 584,
-# dram__bytes_write.sum 0).  The traffic is the parameter records and the grid
-# list, so it grows with the instances of a batch.
-C2_DRAM_BYTES_PER_INSTANCE = (833536 + 733184 + 545280 + 451584) / 256
+# batch (dram__bytes_read.sum 824 064 + 642 816 + 510 208 + 469 248,
+# dram__bytes_write.sum 768 + 0 + 0 + 0).  The traffic is the parameter records
+# and the grid list, so it grows with the instances of a batch.
+C2_DRAM_BYTES_PER_INSTANCE = (824064 + 642816 + 510208 + 469248 + 768) / 256
 FP32_PEAK = 152 * 128 * 2 * 2070e6  # SMs x FFMA/clk x FLOP/FMA x max SM clock
 WORKLOADS = {
     "c2": dict(desc=WORKLOAD, d=4, n=5, psi=0, dtype="f64", batch=4096),
