@@ -85,3 +85,16 @@ def test_rejects_null_arguments(L):
     out = C.c_void_p(1)
     assert L.amfrw_problem_create(None, None, C.byref(out)) == 1
     assert out.value is None
+
+
+def test_rejects_empty_and_negative_batches(L):
+    # an empty problem set is an argument error, reported before any CUDA call
+    m = B._Marshal([W.small_instance(3, 3)])
+    prices = np.zeros(1)
+    out = C.c_void_p(1)
+    for n in (0, -1):
+        assert L.amfrw_solve_batch(m.arr, n, B._dp(prices), None) == 1
+        assert L.amfrw_solve_noalloc(m.arr, n, C.c_void_p(1), None) == 1
+        assert L.amfrw_batch_create(m.arr, n, None, C.byref(out)) == 1
+        assert out.value is None
+        assert "at least one instance" in L.amfrw_last_error().decode()
