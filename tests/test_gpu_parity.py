@@ -212,3 +212,32 @@ def test_c3_full_size_sampled_grids():
         assert np.max(np.abs(Yg - Yo)) <= 1e-6 * np.max(np.abs(Yo)), lv[g]
         assert abs(u[g] - u_o) <= 1e-6 * np.max(np.abs(Yo))
     assert np.isfinite(prob.combine())
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_c4_full_size_d8_sampled_grids(precision):
+    """The largest shape of the batched workload, d=8 standard level 6 (3003
+    grids of 256..8320 nodes, 40 steps), taken from the 256-instance batch:
+    sampled component grids against the oracle one by one (the largest, the
+    smallest, and the one with the most refined axes, which has the most
+    active cross and drift terms), node by node."""
+    inst = dict(W.batch("c4", 2)[1], precision=precision)
+    assert inst["N"] == 8 and inst["level"] == 6
+    tol = TOL64 if precision == "fp64" else 1e-6
+    prob = B.Problem(inst)
+    prob.step(inst["n_steps"])
+    lv, cf = prob.grid_info()
+    u = prob.grid_values()
+    assert len(lv) == 3003
+    sizes = np.array([np.prod([(1 << int(x)) + 1 for x in l]) for l in lv])  # with Outer nodes
+    spread = np.array([np.count_nonzero(l) for l in lv])
+    pick = [int(np.argmax(sizes)), int(np.argmin(sizes)), int(np.argmax(spread))]
+    for g in pick:
+        u_o, Yf = O.solve_grid(inst, lv[g], want_Y=True)
+        Yo = inner(Yf, lv[g])
+        Yg = prob.read_grid(g, lv[g])
+        scale = np.max(np.abs(Yo))
+        assert np.max(np.abs(Yg - Yo)) <= tol * scale, (lv[g], np.max(np.abs(Yg - Yo)) / scale)
+        assert abs(u[g] - u_o) <= tol * scale, (lv[g], u[g], u_o)
+    assert np.isfinite(prob.combine())
+    prob.close()
