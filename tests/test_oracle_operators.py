@@ -167,3 +167,44 @@ def test_line_solve_equals_dense_solve(N, levels):
         assert np.max(np.abs(K - Kd)) <= 1e-13 * max(1.0, np.max(np.abs(Kd)))
         res = K - nu_dt * O.apply_Fi(inst, levels, axis, K) - G
         assert np.max(np.abs(res)) <= 1e-12 * max(1.0, np.max(np.abs(G)))
+
+
+# ---------------------------------------------------------- spatial order 2
+def _caplet_on_nodes(sigma, phi, beta, alpha, steps=64):
+    # strike K = 0.01 and spot F0 = 0.0125 are nodes of every grid of level
+    # >= 4 on [0, 0.04] (the payoff kink sits on a node), V0 = 1 is a node on
+    # [0, 2]; 64 steps of the third-order scheme leave the time error far
+    # below the spatial one
+    return dict(N=2, payoff="caplet", n_steps=steps, alpha=[alpha], phi=[phi], tau=[0.5],
+                F0=[0.0125], Fmax=[0.04], Vmax=2.0, rho=[[1.0]], sigma=sigma, beta=beta, V0=1.0,
+                K=0.01, T=0.5, theta=(3 + math.sqrt(3)) / 6, nu=(3 + math.sqrt(3)) / 6,
+                discount=1.0)
+
+
+def test_full_grid_price_converges_at_second_order_to_black():
+    """Sec. 3 discretises with second-order central differences.  With sigma
+    = 0 and beta = 1 the model is Black's lognormal one, whose caplet value
+    (F N(d1) - K N(d2), volatility alpha V0) is exact; the error of the
+    full-grid price falls by a factor tending to 4 per level (observed order
+    2; the domain truncation at F^max, eight standard deviations away, is far
+    below the errors measured here)."""
+    F, K, vol, T = 0.0125, 0.01, 0.2, 0.5
+    d1 = (math.log(F / K) + 0.5 * vol * vol * T) / (vol * math.sqrt(T))
+    Nc = lambda x: 0.5 * (1.0 + math.erf(x / math.sqrt(2.0)))
+    black = F * Nc(d1) - K * Nc(d1 - vol * math.sqrt(T))
+    inst = _caplet_on_nodes(0.0, 0.0, 1.0, vol)
+    err = [O.price(inst, lev, full=True) - black for lev in (6, 7, 8)]
+    assert abs(err[2]) < 2e-5 * black  # 1.6e-5 relative at level 8 (257 x 257 nodes)
+    r67, r78 = err[0] / err[1], err[1] / err[2]
+    assert 3.0 < r67 < r78 < 4.3, (r67, r78)
+
+
+def test_full_grid_self_convergence_with_stochastic_volatility():
+    """The same on the SABR problem (sigma > 0, correlated, beta = 1/2),
+    which has no closed form: the level-to-level price differences shrink by
+    a factor that grows towards 4."""
+    inst = _caplet_on_nodes(0.3, -0.3, 0.5, 0.02)
+    p = [O.price(inst, lev, full=True) for lev in (5, 6, 7, 8)]
+    d = [p[i] - p[i + 1] for i in range(3)]
+    r1, r2 = d[0] / d[1], d[1] / d[2]
+    assert 1.2 < r1 < r2 < 4.3 and r2 > 3.0, (r1, r2)
