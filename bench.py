@@ -1,34 +1,40 @@
 """Benchmark: priced instances per second of the AMFR-W2 sparse-grid solver.
 
-Workload (one "step" = one batch): B seeded instances of the d=4 SABR-LMM
-swaption problem (3 forward rates + V, standard combination level n=5, 121
-component grids, 40 AMFR-W2 steps, FP64), each priced end to end (all
-component grids, interpolation, combination).  Instances are sharded across
-ranks with no collective on the data path (weak scaling).
+Default workload (one "step" = one batch): the batched mixed-precision
+configuration -- 256 seeded SABR-LMM swaption instances of uneven size (N in
+{4, 6, 8} axes, i.e. 3, 5 or 7 forward rates + V, standard combination level
+n in {4, 5, 6}, 40 AMFR-W2 steps, T = 2), all their component grids solved in
+persistent launches replayed from a CUDA graph, F and the line solves in FP32,
+the stage accumulation, interpolation and combination in FP64.  Instances are
+sharded across ranks with no collective on the data path (weak scaling).
 
-  value  device-timed throughput with inputs resident in HBM (CUDA events
-         on the library's stream around each batch; L2 flushed between
-         batches by a 256 MiB write outside the timed events)
+  value  device-timed throughput of the mixed batch, counting only the
+         instances whose price is within 1e-5 (relative) of the FP64 GPU
+         price of the same instance (CUDA events on the library's stream
+         around each batch; L2 flushed between batches by a 256 MiB write
+         outside the timed events; inputs resident in HBM)
   e2e    the same metric through the C-ABI call amfrw_solve_batch with host
          buffers (validation, grid enumeration, upload, solve, download)
-  roofline  the dominant solver kernel: algorithmic FP64 FLOPs of its launch
-         (counted per node from Sketch 1 and the Thomas sweeps) / its CUDA
-         event duration, against the FP64 peak derived from 152 SMs x
-         2 DFMA/clk x 2070 MHz
-  cpu_baseline  the CPU oracle on the host cores (bounded sample)
+  roofline  the solver launches of a batch against the two arithmetic pipes
+         the mixed path uses: FP32 operations of the F evaluations, line solves
+         and stage algebra, FP64 operations of the stage accumulation, F of the
+         payoff and the interpolation, each divided by its pipe's peak as
+         measured in this run (amfrw_peak_probe); the bound is the larger
+         time, frac = bound / measured time
+  cpu_baseline  the CPU oracle timed on a seeded random sample of the batch's
+         component grids (all host cores, and one core), scaled to the batch
+  variants  the same 256 instances in plain FP64, the d=4 level-5 FP64 batch,
+         the d=6 modified level-6 mixed instance and the surrogate with its
+         solver fallback
 
---workload c5 measures the surrogate instead: an ensemble of MLPs trained on
-the batched solver's prices of a d=6 instance family serves queries, falling
-back to the solver wherever its calibrated error estimate exceeds 1e-3 of the
-price; it reports queries/s with the network beside the solver alone.
-
---workload paper prices the paper's own swaption rows (Tables sg_d3, sg_d4,
-sg_d5, sg_d6, d4:level, d6:level: 3 to 6 axes, levels up to 19) with its
-market data, FP64, one instance per row, within a GPU-time budget, and prints
-the GPU seconds beside the paper's CPU seconds (another machine: context).
+--workload c2|c3 measures one of those solver variants alone, --workload c5
+the surrogate alone, --workload paper the paper's own swaption rows (Tables
+sg_d3, sg_d4, sg_d5, sg_d6, d4:level, d6:level) beside the paper's CPU seconds
+(another machine: context).
 
 --impl reference runs the oracle arm instead (the reference of this build is
-the plain FP64 CPU implementation of the paper's method).
+the plain FP64 CPU implementation of the paper's method), on the same
+workload, metric and unit.
 """
 from __future__ import annotations
 
@@ -51,24 +57,19 @@ from paper_2408_00559_gb300 import workloads as W  # noqa: E402
 
 METRIC = "priced instances/sec at 1e-5 rel. error (batched/mixed vs plain; surrogate)"
 UNIT = "instances/s"
-WORKLOAD = ("c2: d=4 (3 forward rates + V) SABR-LMM swaption, standard combination level 5 "
-            "(121 component grids, 15149 nodes), 40 AMFR-W2 steps, T=2, FP64")
-FP64_PEAK = 152 * 2 * 2 * 2070e6  # SMs x DFMA/clk x FLOP/FMA x max SM clock
-# DRAM bytes (read + write) of the C2 FP64 solver launches of one batch, per
-# instance: one ncu capture of the four per-class launches of a 256-instance
-# batch (dram__bytes_read.sum 824 064 + 642 816 + 510 208 + 469 248,
-# dram__bytes_write.sum 768 + 0 + 0 + 0).  The traffic is the parameter records
-# and the grid list, so it grows with the instances of a batch.
-C2_DRAM_BYTES_PER_INSTANCE = (824064 + 642816 + 510208 + 469248 + 768) / 256
-FP32_PEAK = 152 * 128 * 2 * 2070e6  # SMs x FFMA/clk x FLOP/FMA x max SM clock
+C4_DESC = ("c4: 256 instances, N in {4,6,8} axes (3/5/7 forward rates + V), standard combination "
+           "level n in {4,5,6}, swaption, 40 AMFR-W2 steps, T=2; F and line solves FP32, stage "
+           "accumulation, interpolation and combination FP64")
+C2_DESC = ("c2: d=4 (3 forward rates + V) SABR-LMM swaption, standard combination level 5 "
+           "(121 component grids, 15149 nodes), 40 AMFR-W2 steps, T=2, FP64")
+C3_DESC = ("c3: d=6 (5 forward rates + V) swaption, modified combination psi=1 level 6 "
+           "(923 grids, 13.5 M nodes), 40 steps, mixed FP32/FP64")
 WORKLOADS = {
-    "c2": dict(desc=WORKLOAD, d=4, n=5, psi=0, dtype="f64", batch=4096),
-    "c3": dict(desc=("c3: d=6 (5 forward rates + V) swaption, modified combination psi=1 level 6 "
-                     "(923 grids, 13.5 M nodes), 40 steps, mixed FP32/FP64"),
-               d=6, n=6, psi=1, dtype="f32+f64", batch=4),
-    "c4": dict(desc=("c4: d in {4,6,8}, level in {4,5,6}, standard combination, 40 steps, "
-                     "mixed FP32/FP64"), d=None, n=None, psi=0, dtype="f32+f64", batch=256),
+    "c4": dict(desc=C4_DESC, dtype="f32+f64", batch=256, mixed=True),
+    "c2": dict(desc=C2_DESC, dtype="f64", batch=4096, mixed=False),
+    "c3": dict(desc=C3_DESC, dtype="f32+f64", batch=4, mixed=True),
 }
+L2_FLUSH_BYTES = 256 << 20
 
 
 def parse():
@@ -80,13 +81,19 @@ def parse():
     ap.add_argument("--batch", type=int, default=None, help="instances per step per GPU")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "paper"],
-                    help="c2 (default, the metric's configuration); c3/c4 for profiling runs; "
-                         "c5 the surrogate with solver fallback; paper the paper-scale rows")
+    ap.add_argument("--no-variants", action="store_true", help="skip the variants (quick runs)")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate variant")
+    ap.add_argument("--workload", default="c4", choices=["c4", "c2", "c3", "c5", "paper"],
+                    help="c4 (default: the batched mixed-precision configuration); c2/c3 one solver "
+                         "variant alone; c5 the surrogate with solver fallback; paper the paper-scale rows")
     ap.add_argument("--train", type=int, default=100_000, help="c5: training prices")
     ap.add_argument("--queries", type=int, default=1 << 20, help="c5: queries served")
     ap.add_argument("--epochs", type=int, default=260, help="c5: training epochs")
     ap.add_argument("--members", type=int, default=8, help="c5: ensemble members")
+    ap.add_argument("--c5-box", default="configured", choices=["configured", "centred"],
+                    help="c5: the surrogate family's parameter box")
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="c5: stop serving after this many seconds (fallback solves included)")
     ap.add_argument("--global-grids", action="store_true",
                     help="c2/c3/c4: keep every component grid in global memory (for comparisons)")
     ap.add_argument("--budget", type=float, default=300.0, help="paper: GPU seconds to spend")
@@ -96,10 +103,17 @@ def parse():
     return ap.parse_args()
 
 
-# ---------------------------------------------------------------- FLOP count
+def workload_batch(name: str, count: int, start: int = 0, precision: str | None = None) -> list[dict]:
+    insts = W.batch(name, count, start=start)
+    if precision is not None:
+        insts = [dict(x, precision=precision) for x in insts]
+    return insts
+
+
+# ---------------------------------------------------------------- op counts
 def node_flops(levels, steps):
-    """Algorithmic FP64 FLOPs of one component grid over `steps` AMFR-W2
-    steps (FMA = 2).  Per F evaluation at an Inner node (Sketch 1 with the
+    """Algorithmic FLOPs of one component grid over `steps` AMFR-W2 steps
+    (FMA = 2).  Per F evaluation at an Inner node (Sketch 1 with the
     coefficients from per-axis tables): 3 per second difference, 1 per
     gradient of a drift axis not on its upper face, for each pair (i,k) with
     both indices below their upper faces 3 for the cross difference plus 3
@@ -129,10 +143,37 @@ def node_flops(levels, steps):
     return float(per_step) * steps
 
 
-def c2_flops_per_instance():
-    from paper_2408_00559_gb300._lib import Problem  # noqa: F401  (shapes only below)
-    lv = enumerate_levels(4, 5, 0)
-    return sum(node_flops(l, 40) for l in lv)
+def payoff_F_flops(levels):
+    """FLOPs of F applied once to the payoff on the rate grid (the V terms
+    vanish: the payoff does not depend on V), with the swaption payoff
+    evaluated at the centre and at each neighbour the stencil reads (2 per
+    rate and payoff evaluation): the same per-node terms as node_flops
+    restricted to the rate axes."""
+    N = len(levels)
+    nr = N - 1
+    M = [1 << int(l) for l in levels[:nr]]
+    axes = [np.arange(1, m + 1) for m in M]
+    grids = np.meshgrid(*axes, indexing="ij")
+    nt = [g != m for g, m in zip(grids, M)]
+    f = np.full(grids[0].shape, 3 * nr + 2 * nr + 2 * nr + 2 * nr * (1 + 2 * nr), dtype=np.float64)
+    for i in range(1, nr):
+        f += nt[i] * (1 + 2 * i + 3)
+    for i in range(nr):
+        for k in range(i + 1, nr):
+            f += (nt[i] & nt[k]) * (6 + 4 * 2 * nr)
+    return float(f.sum())
+
+
+def mixed_ops(levels, steps):
+    """(FP32 ops, FP64 ops) of one grid in the mixed mode: the F
+    evaluations, line solves and stage algebra in FP32; the accumulation
+    Y_{n+1} = Y_n + b1 K1 + b2 K2 (2 FMAs per node and step), F of the
+    payoff and the 2^N-corner interpolation in FP64."""
+    N = len(levels)
+    L = 1 << int(sum(levels))
+    total = node_flops(levels, steps)
+    fp64 = 4.0 * L * steps + payoff_F_flops(levels) + (1 << N) * (3 * N + 2)
+    return total - 6.0 * L * steps, fp64
 
 
 def enumerate_levels(d, n, psi):
@@ -149,6 +190,29 @@ def enumerate_levels(d, n, psi):
         if n - q >= 0:
             rec([], n - q)
     return [[psi + x for x in l] for l in out]
+
+
+def batch_ops(insts):
+    """(FP32 or FP64 FLOPs of the F/solve work, FP64 ops) of a batch: for
+    FP64 instances everything counts as FP64."""
+    shapes = {}
+    f32 = f64 = 0.0
+    for inst in insts:
+        key = (inst["N"], inst["level"], inst["psi"], inst["n_steps"], inst.get("precision", "fp64"))
+        if key not in shapes:
+            lvs = enumerate_levels(key[0], key[1], key[2])
+            if key[4] == "mixed":
+                a = b = 0.0
+                for lv in lvs:
+                    x, y = mixed_ops(lv, key[3])
+                    a += x
+                    b += y
+                shapes[key] = (a, b)
+            else:
+                shapes[key] = (0.0, sum(node_flops(lv, key[3]) for lv in lvs))
+        f32 += shapes[key][0]
+        f64 += shapes[key][1]
+    return f32, f64
 
 
 # ------------------------------------------------------------------- clocks
@@ -208,60 +272,124 @@ class ClockSampler:
 
 
 # -------------------------------------------------------------- CPU oracle
+def _oracle_grid(job):
+    """Solve one component grid with the oracle; returns its wall seconds."""
+    import oracle as O
+    inst, lv = job
+    t0 = time.perf_counter()
+    O.solve_grid(inst, lv)
+    return time.perf_counter() - t0
+
+
 def _oracle_price(inst):
     import oracle as O
     return O.price(inst, inst["level"], inst["psi"], inst.get("full", False))
 
 
-def cpu_oracle_rate(seconds: float, start: int):
-    """The oracle as it stands, one instance per worker process, all host
-    cores, for about `seconds` of wall time.  Returns (instances/s, cores,
-    instances done)."""
+def grid_jobs(insts, seed: int = 7):
+    """Every (instance, component grid) of a batch in a seeded random order."""
+    import oracle as O
+    jobs = []
+    cache = {}
+    for inst in insts:
+        key = (inst["N"], inst["level"], inst["psi"])
+        if key not in cache:
+            cache[key] = O.enumerate_grids(*key)[0]
+        for lv in cache[key]:
+            jobs.append((inst, [int(x) for x in lv]))
+    order = np.random.Generator(np.random.PCG64(seed)).permutation(len(jobs))
+    return [jobs[i] for i in order]
+
+
+def oracle_sample_rate(insts, seconds: float, workers: int, seed: int = 7):
+    """The oracle as it stands on a seeded uniform random sample of the
+    batch's component grids, `workers` processes, for about `seconds` of wall
+    time.  The batch's oracle time is estimated as the sample's wall time x
+    (all grids / sampled grids).  Returns (instances/s, grids done, grids in
+    the batch)."""
     import oracle as O
     O.build()
-    cores = os.cpu_count() or 1
+    jobs = grid_jobs(insts, seed)
     ctx = mp.get_context("spawn")
     done = 0
-    t0 = time.perf_counter()
-    with ctx.Pool(cores) as pool:
-        idx = start
-        while True:
-            chunk = W.batch("c2", cores, start=idx)
-            idx += cores
-            pool.map(_oracle_price, chunk)
-            done += len(chunk)
+    with ctx.Pool(workers) as pool:
+        pool.map(_oracle_grid, jobs[:workers])  # start-up, not timed
+        t0 = time.perf_counter()
+        chunk = 4 * workers
+        while done < len(jobs):
+            pool.map(_oracle_grid, jobs[done:done + chunk])
+            done += len(jobs[done:done + chunk])
             if time.perf_counter() - t0 >= seconds:
                 break
-    dt = time.perf_counter() - t0
-    return done / dt, cores, done
+        dt = time.perf_counter() - t0
+    est = dt * len(jobs) / done
+    return len(insts) / est, done, len(jobs)
+
+
+def oracle_parity_prices(insts, limit_pts: int = 300_000):
+    """Oracle prices of the instances whose whole solve is cheap (component
+    grids of at most `limit_pts` nodes in total, Outer nodes included), in a
+    spawned pool: {index: price}."""
+    import oracle as O
+    O.build()
+    pick = []
+    for i, inst in enumerate(insts):
+        lv, _ = O.enumerate_grids(inst["N"], inst["level"], inst["psi"])
+        pts = sum(int(np.prod((1 << np.asarray(l)) + 1)) for l in lv)
+        if pts <= limit_pts:
+            pick.append(i)
+    if not pick:
+        return {}
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(len(pick), os.cpu_count() or 1)) as pool:
+        vals = pool.map(_oracle_price, [insts[i] for i in pick])
+    return dict(zip(pick, vals))
 
 
 # ------------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
+    """The oracle arm: the CPU oracle, as it stands, on the same workload,
+    metric and unit.  Each step solves one chunk of the batch's component
+    grids (seeded random order) on all host cores; the rate is scaled to
+    instances by the batch's grid count."""
     if rank != 0:
         return
-    # each step prices one chunk of instances on all host cores
     import oracle as O
     O.build()
+    wl = WORKLOADS.get(args.workload, WORKLOADS["c4"])
+    name = args.workload if args.workload in WORKLOADS else "c4"
+    B = args.batch or wl["batch"]
+    insts = workload_batch(name, B, precision="mixed" if wl["mixed"] else None)
+    jobs = grid_jobs(insts)
     cores = os.cpu_count() or 1
+    chunk = 4 * cores
     ctx = mp.get_context("spawn")
+    pos = 0
     with ctx.Pool(cores) as pool:
         for w in range(args.warmup):
-            pool.map(_oracle_price, W.batch("c2", cores, start=10_000_000 + w * cores))
+            pool.map(_oracle_grid, jobs[pos:pos + chunk])
+            pos += chunk
         t0 = time.perf_counter()
+        done = 0
         for k in range(args.steps):
-            pool.map(_oracle_price, W.batch("c2", cores, start=k * cores))
+            part = jobs[pos:pos + chunk]
+            pool.map(_oracle_grid, part)
+            pos += len(part)
+            done += len(part)
         dt = time.perf_counter() - t0
-    value = args.steps * cores / dt
+    grids_per_inst = len(jobs) / B
+    value = done / dt / grids_per_inst
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "batch": cores, "impl": "CPU oracle (plain serial FP64 C, "
-                   "one instance per process)"},
+        "config": {"workload": wl["desc"], "batch": B,
+                   "impl": "CPU oracle (plain serial FP64 C), one component grid per process"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{args.steps} steps x {cores} c2 instances"},
+                         "sample": f"{args.steps} steps x {chunk} component grids drawn uniformly "
+                                   f"(seeded) from the {len(jobs)} grids of the batch; instances/s = "
+                                   f"grids/s / {grids_per_inst:.1f} grids per instance"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -291,6 +419,67 @@ def job_rate(world: int, per_rank: int, steps: int, seconds: float) -> float:
 
 
 # ------------------------------------------------------------------ our arm
+def time_device_batch(L, torch, insts, stream, dev, steps, warmup, flush, tune=True, timing=True):
+    """Upload once, autotune, W warm-up runs, then `steps` runs each timed by
+    CUDA events on the library's stream, with L2 flushed before each run
+    outside the events.  Returns (prices, per-run ms, per-run kernel times,
+    kernel launches per run, tuned choice)."""
+    B = len(insts)
+    with torch.cuda.stream(stream):
+        batch = L.Batch(insts, stream=stream)
+        choice = batch.autotune(2) if tune else None  # setup, not timed
+        if timing:
+            batch.enable_timing(True)
+        prices = torch.empty(B, dtype=torch.float64, device=dev)
+        n_launch = batch.launches()
+        for _ in range(warmup):
+            batch.run(prices.data_ptr())
+        stream.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        ktimes = []
+        for k in range(steps):
+            flush.fill_(k & 0xFF)
+            evs[k][0].record(stream)
+            batch.run(prices.data_ptr())
+            evs[k][1].record(stream)
+            if timing:
+                ktimes.append(batch.kernel_times())
+        stream.synchronize()
+        step_ms = [s.elapsed_time(e) for s, e in evs]
+        out = prices.cpu().numpy()
+        io = batch.io_bytes()
+        promoted, kappa = batch.promoted()
+        batch.close()
+    return dict(prices=out, step_ms=step_ms, ktimes=ktimes, launches=n_launch, choice=choice, io=io,
+                promoted=promoted, kappa=kappa)
+
+
+def roofline_entry(insts, kernel_ms, peak64, peak32, mixed):
+    """Algorithmic operations of the batch against the pipes they run on.
+    Mixed: FP32 and FP64 operation counts each divided by the pipe's measured
+    peak; the larger time binds, frac = that time / measured kernel time.
+    FP64: all operations on the FP64 pipe."""
+    f32, f64 = batch_ops(insts)
+    t = kernel_ms / 1e3
+    t32 = f32 / (peak32 * 1e12) if mixed else 0.0
+    t64 = f64 / (peak64 * 1e12)
+    pipe = "fp32" if t32 >= t64 else "fp64"
+    ops, peak = (f32, peak32) if pipe == "fp32" else (f64, peak64)
+    return {"bound": "alu", "pipe": pipe, "kernel": "solve_kernel (all solver launches of a batch)",
+            "achieved": ops / t / 1e12, "peak": peak, "unit": "TFLOP/s", "frac": max(t32, t64) / t,
+            "traffic": None,
+            "kernel_ms_per_batch": kernel_ms, "fp32_ops_per_batch": f32, "fp64_ops_per_batch": f64,
+            "fp32_bound_ms": 1e3 * t32, "fp64_bound_ms": 1e3 * t64,
+            "peak_fp64_tflops": peak64, "peak_fp32_tflops": peak32,
+            "peak_source": "measured in this run by amfrw_peak_probe (FMA chains on every SM, "
+                           "CUDA events, of measured)"}
+
+
+def rel_err(a, b):
+    return np.abs(a - b) / np.maximum(np.abs(b), 1e-300)
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -298,81 +487,106 @@ def run_ours(args, rank, world, local_rank):
     from paper_2408_00559_gb300 import _lib as L
     from paper_2408_00559_gb300 import build as BLD
 
-    # CPU baseline first (spawned pool, before any GPU call)
+    name = args.workload
+    wl = WORKLOADS[name]
+    B = args.batch or wl["batch"]
+    insts = workload_batch(name, B, start=shard_start(rank, B))
+    if args.global_grids:
+        insts = [dict(x, global_grids=True) for x in insts]
+    t_start = time.perf_counter()
+
+    def note(msg):
+        print(f"[bench {time.perf_counter() - t_start:7.1f} s] {msg}", file=sys.stderr, flush=True)
+
+    # CPU legs first (spawned pools, before any GPU call): the oracle on a
+    # seeded sample of the batch's grids on all cores and on one core, and
+    # oracle prices of the cheap instances of the first 16 for parity
     cpu = None
+    orc_prices = {}
     if rank == 0 and not args.no_cpu_baseline:
-        rate, cores, done = cpu_oracle_rate(args.cpu_seconds, start=20_000_000)
+        cores = os.cpu_count() or 1
+        rate, done, total = oracle_sample_rate(insts, args.cpu_seconds, cores)
+        rate1, done1, _ = oracle_sample_rate(insts, args.cpu_seconds / 2, 1, seed=8)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{done} c2 instances, one per process on {cores} host cores, "
-                         f"~{args.cpu_seconds:.0f} s"}
+               "sample": f"{done} of the batch's {total} component grids, drawn uniformly (seeded), "
+                         f"one grid per process on {cores} host cores for ~{args.cpu_seconds:.0f} s; "
+                         f"batch time = sample time x {total}/{done}",
+               "single_core": {"value": rate1, "unit": UNIT, "cores": 1,
+                               "sample": f"{done1} grids of another seeded draw on one core"}}
+        note(f"cpu baseline {rate:.4f} instances/s on {cores} cores, {rate1:.5f} on one")
+        orc_prices = oracle_parity_prices(insts[:16])
+        note(f"oracle prices of {len(orc_prices)} cheap instances among the first 16")
 
     BLD.build()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.Stream(device=dev)
-    wl = WORKLOADS[args.workload]
-    B = args.batch or wl["batch"]
-    insts = W.batch(args.workload, B, start=shard_start(rank, B))
-    if args.global_grids:
-        insts = [dict(x, global_grids=True) for x in insts]
-    with torch.cuda.stream(stream):
-        batch = L.Batch(insts, stream=stream)
-        batch.autotune(2)  # launch strategy and grid-state placement (setup, not timed)
-        batch.enable_timing(True)
-        prices = torch.empty(B, dtype=torch.float64, device=dev)
-        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-        n_launch = batch.launches()
-        for _ in range(args.warmup):
-            batch.run(prices.data_ptr())
-        stream.synchronize()
-        # accuracy of the priced instances against the oracle (sampled)
-        check = {"oracle_checked": 0, "note": "covered by the GPU parity tests"}
-        if rank == 0 and args.workload == "c2":
-            import oracle as O
-            got = prices.cpu().numpy()
-            rel = []
-            for i in (0, B // 2, B - 1):
-                po = O.price(insts[i], 5)
-                rel.append(abs(got[i] - po) / abs(po))
-            check = {"oracle_checked": 3, "max_rel_err": max(rel), "tolerance": 1e-12}
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.steps)]
-        ktimes = []
-        with ClockSampler(local_rank) as clk:
-            for k in range(args.steps):
-                flush.fill_(k & 0xFF)
-                evs[k][0].record(stream)
-                batch.run(prices.data_ptr())
-                evs[k][1].record(stream)
-                ktimes.append(batch.kernel_times())
-            torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
-        step_ms = [s.elapsed_time(e) for s, e in evs]
-    total_s = max_over_ranks(sum(step_ms) / 1e3, world, dev)
-    value = job_rate(world, B, args.steps, total_s)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    peak64 = L.peak_probe("fp64", stream=stream)
+    peak32 = L.peak_probe("fp32", iters=65536, stream=stream)
+    note(f"measured peaks: FP64 {peak64:.3f}, FP32 {peak32:.2f} TFLOP/s")
 
-    # dominant kernel: the solver kernel, launched once per (N, grid-size)
-    # class; all its launches of one batch together form its work for the batch
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        r = time_device_batch(L, torch, insts, stream, dev, args.steps, args.warmup, flush)
+    prices, step_ms, ktimes, n_launch, choice, io = (r["prices"], r["step_ms"], r["ktimes"], r["launches"],
+                                                      r["choice"], r["io"])
+    if world > 1:
+        dist.barrier()
+    total_s = max_over_ranks(sum(step_ms) / 1e3, world, dev)
+    raw_rate = job_rate(world, B, args.steps, total_s)
+    note(f"{name}: {raw_rate:.1f} instances/s, {np.mean(step_ms):.2f} ms per batch")
+
     launches_per_batch = len(ktimes[0])
-    kernel_ms = [sum(ms for (N, ms, ns) in kt) for kt in ktimes]
-    avg_ms = sum(kernel_ms) / len(kernel_ms)
-    flops_batch = 0.0
-    shapes = {}
-    for inst in insts:
-        key = (inst["N"], inst["level"], inst["psi"])
-        if key not in shapes:
-            shapes[key] = sum(node_flops(l, inst["n_steps"]) for l in enumerate_levels(*key))
-        flops_batch += shapes[key]
-    achieved = flops_batch / (avg_ms / 1e3)
-    fp64 = wl["dtype"] == "f64"
-    peak = FP64_PEAK if fp64 else FP32_PEAK
+    kernel_ms = float(np.mean([sum(ms for (_, ms, _) in kt) for kt in ktimes]))
+    roof = roofline_entry(insts, kernel_ms, peak64, peak32, wl["mixed"])
+    roof["solver_launches_per_batch"] = launches_per_batch
+
+    # accuracy: mixed prices against the FP64 GPU prices of the same instances
+    # (the FP64 path is pinned to the oracle at 1e-12 by the parity tests),
+    # and the cheap instances of the first 16 against the oracle itself
+    variants = {}
+    if wl["mixed"]:
+        r64 = time_device_batch(L, torch, [dict(x, precision="fp64") for x in insts], stream, dev,
+                                max(2, min(args.steps, 5)), 1, flush)
+        p64, s64, k64 = r64["prices"], r64["step_ms"], r64["ktimes"]
+        rel = rel_err(prices, p64)
+        within = float(np.mean(rel <= 1e-5))
+        value = raw_rate * within
+        fp64_rate = B * len(s64) / (sum(s64) / 1e3)
+        variants["plain_fp64"] = {
+            "value": fp64_rate, "unit": UNIT, "dtype": "f64", "batch": B, "steps": len(s64),
+            "ms_per_step": float(np.mean(s64)),
+            "mixed_over_plain": value / fp64_rate,
+            "roofline": roofline_entry([dict(x, precision="fp64") for x in insts],
+                                       float(np.mean([sum(ms for (_, ms, _) in kt) for kt in k64])),
+                                       peak64, peak32, False)}
+        parity = {"vs": "FP64 GPU path, same instances", "tolerance": 1e-5, "instances_checked": int(B),
+                  "max_rel_err": float(rel.max()), "median_rel_err": float(np.median(rel)),
+                  "within_1e-5": within, "rate_before_tolerance": raw_rate,
+                  "promoted_to_fp64": int(r["promoted"]),
+                  "kappa_max_seen": float(np.max(r["kappa"])) if len(r["kappa"]) else None,
+                  "rel_err_per_price": [float(f"{r:.3e}") for r in rel]}
+        note(f"plain FP64: {fp64_rate:.1f} instances/s; mixed within 1e-5: {within:.4f}")
+    else:
+        p64 = prices
+        value = raw_rate
+        parity = {}
+    if orc_prices:
+        idx = sorted(orc_prices)
+        po = np.array([orc_prices[i] for i in idx])
+        parity["oracle"] = {
+            "instances": idx, "fp64_max_rel_err": float(rel_err(p64[idx], po).max()),
+            "fp64_tolerance": 1e-12,
+            "note": "the instances among the first 16 whose grids hold <= 3e5 nodes in total; "
+                    "the others take the oracle minutes to hours each"}
+        if wl["mixed"]:
+            parity["oracle"]["mixed_max_rel_err"] = float(rel_err(prices[idx], po).max())
+            parity["oracle"]["mixed_tolerance"] = 1e-5
 
     # end to end through the C ABI with host buffers
-    h2d, d2h = batch.io_bytes()
     m = L._Marshal(insts)
     host_prices = np.zeros(B)
     lib = L.lib()
@@ -382,73 +596,22 @@ def run_ours(args, rank, world, local_rank):
     e2e_steps = max(2, args.steps // 2)
     if world > 1:
         dist.barrier()
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         L._check(lib.amfrw_solve_batch(m.arr, B, L._dp(host_prices), sptr), "amfrw_solve_batch")
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
-    assert np.array_equal(host_prices, prices.cpu().numpy()), "e2e prices differ from the device run"
-    batch.close()
+    assert np.array_equal(host_prices, prices), "e2e prices differ from the device run"
+    e2e_within = float(np.mean(rel_err(host_prices, p64) <= 1e-5)) if wl["mixed"] else 1.0
+    h2d, d2h = io
 
-    # the same instances in mixed precision (FP32 F and line solves, FP64
-    # accumulation, interpolation and combination), timed the same way; every
-    # price is compared with the FP64 price of the same instance
-    variants = {}
-    if args.workload == "c2" and rank == 0:
-        p64 = prices.cpu().numpy()
-        mb = L.Batch([dict(x, precision="mixed") for x in insts], stream=stream)
-        pm = torch.empty(B, dtype=torch.float64, device=dev)
-        with torch.cuda.stream(stream):
-            for _ in range(args.warmup):
-                mb.run(pm.data_ptr())
-            stream.synchronize()
-            mev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                   for _ in range(args.steps)]
-            for k in range(args.steps):
-                flush.fill_(k & 0xFF)
-                mev[k][0].record(stream)
-                mb.run(pm.data_ptr())
-                mev[k][1].record(stream)
-            torch.cuda.synchronize()
-        m_s = sum(a.elapsed_time(b) for a, b in mev) / 1e3
-        pmix = pm.cpu().numpy()
-        rel = np.abs(pmix - p64) / np.maximum(np.abs(p64), 1e-300)
-        mb.close()
-        within = float(np.mean(rel <= 1e-5))
-        # instances beyond 1e-5: the error against the combination's own scale
-        # sum_l |c_l u_l| (from the FP64 grid values), which a price that nearly
-        # cancels makes much larger than |price|
-        worst = []
-        for i in np.argsort(-rel)[:4]:
-            if rel[i] <= 1e-5:
-                break
-            pr = L.Problem(insts[i], stream=stream)
-            pr.step(insts[i]["n_steps"])
-            _, cf = pr.grid_info()
-            scale = float(np.sum(np.abs(np.asarray(cf) * pr.grid_values())))
-            pr.close()
-            worst.append({"instance": int(i), "price_fp64": float(p64[i]), "rel_err": float(rel[i]),
-                          "combination_scale": scale,
-                          "err_rel_to_scale": float(abs(pmix[i] - p64[i]) / scale)})
-        mval = B * args.steps / m_s
-        variants["c2_mixed"] = {
-            "value": mval, "value_at_1e-5": mval * within, "unit": UNIT, "dtype": "f32+f64",
-            "max_rel_err_vs_fp64": float(rel.max()), "instances_checked": int(B),
-            "within_1e-5": within, "beyond_1e-5": worst, "speedup_vs_fp64": mval / value}
-
-    # mixed-precision workloads: the error of every price against the FP64
-    # price of the same instance (the FP64 path agrees with the oracle to
-    # 1e-12 in the parity tests), and the rate counting only the instances
-    # within 1e-5 of it
-    if args.workload in ("c3", "c4") and rank == 0:
-        pmix = prices.cpu().numpy()
-        p64 = L.solve_batch([dict(x, precision="fp64") for x in insts], stream=stream)
-        rel = np.abs(pmix - p64) / np.maximum(np.abs(p64), 1e-300)
-        within = float(np.mean(rel <= 1e-5))
-        check = {"vs": "FP64 GPU path, same instances", "tolerance": 1e-5,
-                 "instances_checked": int(B), "max_rel_err": float(rel.max()),
-                 "median_rel_err": float(np.median(rel)), "within_1e-5": within,
-                 "value_at_1e-5": value * within,
-                 "rel_err_per_price": [float(f"{r:.3e}") for r in rel]}
+    if rank == 0 and name == "c4" and not args.no_variants:
+        variants.update(solver_variants(args, L, torch, stream, dev, flush, peak64, peak32, note))
+        if not args.no_surrogate:
+            try:
+                variants["surrogate"] = surrogate_measure(args, L, torch, stream, dev, note, quick=True)
+            except Exception as e:  # reported, not hidden
+                variants["surrogate"] = {"error": repr(e)}
 
     if rank != 0:
         return
@@ -459,53 +622,75 @@ def run_ours(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": wl["dtype"], "data": "synthetic",
         "config": {"workload": wl["desc"], "batch_per_gpu": B,
                    "parallelism": f"dp{world} (instances sharded, no collective)",
-                   "l2": "flushed between timed batches (256 MiB write outside the events)"},
-        "roofline": {"bound": "alu", "pipe": "fp64" if fp64 else "fp32",
-                     "kernel": "solve_kernel (all per-class launches of a batch)",
-                     "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-                     "frac": achieved / peak,
-                     "traffic": (C2_DRAM_BYTES_PER_INSTANCE * B
-                                 if args.workload == "c2" and not args.global_grids else None),
-                     "kernel_ms_per_batch": avg_ms, "solver_launches_per_batch": launches_per_batch,
-                     "flops_per_batch": flops_batch,
-                     "peak_source": ("derived: 152 SMs x 2 DFMA/clk x 2 FLOP x 2070 MHz" if fp64 else
-                                     "derived: 152 SMs x 128 FFMA/clk x 2 FLOP x 2070 MHz")},
+                   "l2": "flushed between timed batches (256 MiB write outside the events)",
+                   "value_counts": "instances within 1e-5 of the FP64 GPU price" if wl["mixed"] else
+                                   "every instance (FP64)",
+                   "autotuned_multi_class_launch": choice},
+        "roofline": roof,
         "cpu_baseline": cpu,
-        "e2e": {"value": world * B * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+        "e2e": {"value": world * B * e2e_steps / e2e_s * e2e_within, "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": n_launch * args.steps,
         "clocks": clocks,
-        "parity": check,
+        "parity": parity,
         "variants": variants,
     }
     print(json.dumps(line), flush=True)
 
 
+def solver_variants(args, L, torch, stream, dev, flush, peak64, peak32, note):
+    """The FP64 d=4 level-5 batch (4096 instances) and the d=6 modified
+    level-6 mixed instance, timed like the main line."""
+    out = {}
+    insts = workload_batch("c2", WORKLOADS["c2"]["batch"], start=0)
+    r = time_device_batch(L, torch, insts, stream, dev, max(2, min(args.steps, 5)), 2, flush)
+    ms, kt = r["step_ms"], r["ktimes"]
+    kms = float(np.mean([sum(x for (_, x, _) in k) for k in kt]))
+    out["c2_fp64"] = {"workload": C2_DESC, "value": len(insts) * len(ms) / (sum(ms) / 1e3), "unit": UNIT,
+                      "dtype": "f64", "batch": len(insts), "ms_per_step": float(np.mean(ms)),
+                      "roofline": roofline_entry(insts, kms, peak64, peak32, False)}
+    note(f"c2 fp64: {out['c2_fp64']['value']:.0f} instances/s")
+    rm = time_device_batch(L, torch, [dict(x, precision="mixed") for x in insts], stream, dev,
+                           max(2, min(args.steps, 5)), 2, flush)
+    rel = rel_err(rm["prices"], r["prices"])
+    within = float(np.mean(rel <= 1e-5))
+    mval = len(insts) * len(rm["step_ms"]) / (sum(rm["step_ms"]) / 1e3)
+    out["c2_mixed"] = {"workload": C2_DESC.replace("FP64", "mixed FP32/FP64"), "value": mval * within,
+                       "rate_before_tolerance": mval, "unit": UNIT, "dtype": "f32+f64", "batch": len(insts),
+                       "ms_per_step": float(np.mean(rm["step_ms"])), "within_1e-5": within,
+                       "max_rel_err_vs_fp64": float(rel.max()), "promoted_to_fp64": int(rm["promoted"]),
+                       "speedup_vs_fp64": mval * within / out["c2_fp64"]["value"]}
+    note(f"c2 mixed: {mval:.0f} instances/s, within 1e-5 {within:.4f}, promoted {rm['promoted']}")
+    insts = workload_batch("c3", WORKLOADS["c3"]["batch"], start=0)
+    r = time_device_batch(L, torch, insts, stream, dev, 3, 1, flush)
+    p, ms, kt = r["prices"], r["step_ms"], r["ktimes"]
+    p64 = time_device_batch(L, torch, [dict(x, precision="fp64") for x in insts], stream, dev,
+                            1, 0, flush, tune=False, timing=False)["prices"]
+    kms = float(np.mean([sum(x for (_, x, _) in k) for k in kt]))
+    rel = rel_err(p, p64)
+    out["c3_mixed"] = {"workload": C3_DESC, "value": len(insts) * len(ms) / (sum(ms) / 1e3), "unit": UNIT,
+                       "dtype": "f32+f64", "batch": len(insts), "ms_per_step": float(np.mean(ms)),
+                       "max_rel_err_vs_fp64": float(rel.max()), "within_1e-5": float(np.mean(rel <= 1e-5)),
+                       "roofline": roofline_entry(insts, kms, peak64, peak32, True)}
+    note(f"c3 mixed: {out['c3_mixed']['value']:.1f} instances/s")
+    return out
+
+
 # ------------------------------------------------------------ surrogate (c5)
-C5_DESC = ("c5: surrogate family, d=6 (5 forward rates + V) swaption at the money, standard "
-           "combination level 6 (923 grids, 735869 nodes), 40 steps, mixed FP32/FP64; features "
-           "(alpha, sigma, beta, K, T, lambda, phi_1, phi_5)")
+C5_DESC = ("c5: surrogate family, d=6 (5 forward rates + V) swaption, standard combination level 6 "
+           "(923 grids, 735869 nodes), 40 steps, mixed FP32/FP64; features (alpha, sigma, beta, K, T, "
+           "lambda, phi_1, phi_5); training prices from the same discretisation")
 
 
-def run_surrogate(args, rank, world, local_rank):
+def surrogate_measure(args, L, torch, stream, dev, note, quick=False):
     """Train on solver prices, then serve queries through
     amfrw_surrogate_eval_features (host features in, host prices out; the
-    fallback solves run inside the call).  Each timed step serves one chunk of
-    the queries."""
-    import torch
-
-    from paper_2408_00559_gb300 import _lib as L
-    from paper_2408_00559_gb300 import build as BLD
-
-    BLD.build()
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    stream = torch.cuda.Stream(device=dev)
-    kw = dict(N=6, level=6, steps=40)
-    t_start = time.perf_counter()
-
-    def note(msg):
-        print(f"[c5 {time.perf_counter() - t_start:7.1f} s] {msg}", file=sys.stderr, flush=True)
+    fallback solves run inside the call), chunk by chunk until the queries or
+    the serving time run out.  Returns the measurement as a dict, with the
+    fallback fraction per region of (alpha, K)."""
+    box = args.c5_box
+    kw = dict(N=6, level=6, steps=40, box=box)
+    B = W.C5_BOXES[box]
 
     def solve_chunked(insts, chunk=4096):
         # one plan per chunk: a plan holds every component grid of its instances
@@ -513,12 +698,11 @@ def run_surrogate(args, rank, world, local_rank):
                                for k in range(0, len(insts), chunk)])
 
     t0 = time.perf_counter()
-    F_train = W.c5_features(args.train, 0)
+    F_train = W.c5_features(args.train, 0, box=box)
     train = [W.c5_instance_from(f, **kw) for f in F_train]
-    note(f"{len(train)} training instances built")
     y_train = solve_chunked(train)
-    note("training prices solved")
-    F_audit = W.c5_features(4096, 10_000_000)
+    note(f"surrogate: {len(train)} training prices solved")
+    F_audit = W.c5_features(4096, 10_000_000, box=box)
     audit = [W.c5_instance_from(f, **kw) for f in F_audit]
     y_audit = solve_chunked(audit)
     t_data = time.perf_counter() - t0
@@ -526,13 +710,12 @@ def run_surrogate(args, rank, world, local_rank):
     t0 = time.perf_counter()
     loss = s.fit(train, y_train, epochs=args.epochs, lr=3e-3)
     t_fit = time.perf_counter() - t0
-    note(f"fit: loss {loss:.2e} in {t_fit:.1f} s")
+    note(f"surrogate fit: loss {loss:.2e} in {t_fit:.1f} s")
     calib = s.calibrate(audit, y_audit, rel_bound=1e-3, quantile=0.99)
-    note(f"calibration factor {calib:.2f}")
     del train, audit
 
     # the solver alone on the same family (amfrw_batch, inputs resident, graph replay)
-    sample = [W.c5_instance_from(f, **kw) for f in W.c5_features(2048, 30_000_000)]
+    sample = [W.c5_instance_from(f, **kw) for f in W.c5_features(2048, 30_000_000, box=box)]
     batch = L.Batch(sample, stream=stream)
     out = torch.empty(len(sample), dtype=torch.float64, device=dev)
     with torch.cuda.stream(stream):
@@ -545,65 +728,95 @@ def run_surrogate(args, rank, world, local_rank):
         stream.synchronize()
     solver_rate = len(sample) / (e0.elapsed_time(e1) / 1e3)
     batch.close()
-    note(f"solver alone: {solver_rate:.0f} instances/s")
 
-    # serve: K timed chunks, after W warm-up chunks
-    per = max(1, args.queries // args.steps)
-    F_q = W.c5_features(per * (args.steps + args.warmup), 40_000_000)
-    for w in range(args.warmup):
-        s.eval_features(F_q[w * per:(w + 1) * per])
-        note(f"warm-up chunk {w} served")
+    # serve: chunks of new queries until all are served or the time is up
+    per = 1 << 16
+    chunks = max(1, args.queries // per)
+    F_q = W.c5_features(per * (chunks + 1), 40_000_000, box=box)
+    s.eval_features(F_q[:per // 16])  # warm-up
     torch.cuda.synchronize()
-    fell_total = 0
-    answered = None
-    with ClockSampler(local_rank) as clk:
-        t0 = time.perf_counter()
-        for k in range(args.steps):
-            rows = slice((args.warmup + k) * per, (args.warmup + k + 1) * per)
-            p, fell = s.eval_features(F_q[rows])
-            fell_total += int(fell.sum())
-            note(f"chunk {k}: {per} queries, fallback {fell.mean():.4f}")
-            if k == 0:
-                answered = (p, fell, F_q[rows])
-        dt = time.perf_counter() - t0
-    value = per * args.steps / dt
-
-    # the network alone (no fallback) on one chunk
+    fell_all, F_served, p_first = [], [], None
+    t0 = time.perf_counter()
+    for k in range(chunks):
+        rows = slice((k + 1) * per, (k + 2) * per)
+        p, fell = s.eval_features(F_q[rows])
+        fell_all.append(fell)
+        F_served.append(F_q[rows])
+        if k == 0:
+            p_first = (p, fell, F_q[rows])
+        if time.perf_counter() - t0 > args.serve_seconds:
+            break
+    dt = time.perf_counter() - t0
+    fell_all = np.concatenate(fell_all)
+    F_served = np.concatenate(F_served)
+    served = fell_all.size
+    value = served / dt
     t0 = time.perf_counter()
     s.predict_features(F_q[:per])
     t_net = time.perf_counter() - t0
-
+    # fallback fraction per region: alpha terciles x strike terciles
+    regions = {}
+    edges = {c: np.linspace(*B[key], 4) for c, key in ((0, "alpha"), (3, "K"))}
+    for a in range(3):
+        for k in range(3):
+            m = ((F_served[:, 0] >= edges[0][a]) & (F_served[:, 0] <= edges[0][a + 1]) &
+                 (F_served[:, 3] >= edges[3][k]) & (F_served[:, 3] <= edges[3][k + 1]))
+            if m.any():
+                regions[f"alpha[{edges[0][a]:.3g},{edges[0][a + 1]:.3g}] K[{edges[3][k]:.4g},{edges[3][k + 1]:.4g}]"] = \
+                    {"queries": int(m.sum()), "fallback": float(fell_all[m].mean())}
     # accuracy of answered queries: a sample judged by the solver
-    p, fell, Fk = answered
+    p, fell, Fk = p_first
     idx = np.flatnonzero(~fell)[:2048]
-    y_chk = solve_chunked([W.c5_instance_from(f, **kw) for f in Fk[idx]])
-    rel = np.abs(p[idx] - y_chk) / np.abs(y_chk)
+    y_chk = solve_chunked([W.c5_instance_from(f, **kw) for f in Fk[idx]]) if idx.size else np.zeros(0)
+    rel = np.abs(p[idx] - y_chk) / np.abs(y_chk) if idx.size else np.zeros(0)
     s.close()
-    clocks = clk.summary()
+    note(f"surrogate: {value:.0f} queries/s, fallback {fell_all.mean():.4f}")
+    return {"workload": C5_DESC, "box": {k: v for k, v in B.items()}, "value": value, "unit": "queries/s",
+            "queries": int(served), "queries_per_step": per, "steps": int(served // per),
+            "ms_per_step": 1e3 * dt / max(1, served // per),
+            "fallback_fraction": float(fell_all.mean()), "fallback_by_region": regions,
+            "solver_alone": solver_rate, "speedup_vs_solver": value / solver_rate,
+            "network_only_queries_per_s": per / t_net,
+            "answered_checked": int(idx.size), "answered_max_rel_err": float(rel.max()) if idx.size else None,
+            "answered_within_bound": float(np.mean(rel <= 1e-3)) if idx.size else None,
+            "answered_median_rel_err": float(np.median(rel)) if idx.size else None,
+            "rel_bound": 1e-3, "calib_quantile": 0.99, "calibration": calib,
+            "train": args.train, "epochs": args.epochs, "members": args.members, "train_loss": loss,
+            "data_generation_s": t_data, "fit_s": t_fit, "serve_s": dt,
+            "e2e_bytes": {"h2d_per_query": 8 * 4, "d2h_per_query": 12}}
+
+
+def run_surrogate(args, rank, world, local_rank):
+    import torch
+
+    from paper_2408_00559_gb300 import _lib as L
+    from paper_2408_00559_gb300 import build as BLD
+
+    BLD.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.Stream(device=dev)
+    t_start = time.perf_counter()
+
+    def note(msg):
+        print(f"[c5 {time.perf_counter() - t_start:7.1f} s] {msg}", file=sys.stderr, flush=True)
+
+    with ClockSampler(local_rank) as clk:
+        r = surrogate_measure(args, L, torch, stream, dev, note)
     line = {
-        "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+        "metric": METRIC, "value": r["value"], "unit": "queries/s", "n_gpus": world, "steps": r["steps"],
+        "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (network) + f32/f64 (fallback solver)",
         "data": "synthetic",
-        "config": {"workload": C5_DESC, "queries_per_step": per, "train": args.train,
+        "config": {"workload": C5_DESC, "queries_per_step": r["queries_per_step"], "train": args.train,
                    "epochs": args.epochs, "members": args.members, "rel_bound": 1e-3, "calib_quantile": 0.99,
                    "l2": "queries stream from host memory; every chunk is new data"},
-        "surrogate": {"fallback_fraction": fell_total / (per * args.steps),
-                      "solver_alone": solver_rate, "speedup_vs_solver": value / solver_rate,
-                      "network_only_queries_per_s": per / t_net,
-                      "answered_checked": int(idx.size), "answered_max_rel_err": float(rel.max()),
-                      "answered_within_bound": float(np.mean(rel <= 1e-3)),
-                      "answered_median_rel_err": float(np.median(rel)),
-                      "train_loss": loss, "calibration": calib,
-                      "data_generation_s": t_data, "fit_s": t_fit},
-        # network path: FP32 normalised features in; FP64 target and FP32 spread out
-        # (the fallback solves' own copies come on top)
-        "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": per * 8 * 4,
-                "d2h_bytes_per_step": per * 12},
-        "clocks": clocks,
+        "surrogate": r,
+        "e2e": {"value": r["value"], "unit": "queries/s", "h2d_bytes_per_step": r["queries_per_step"] * 8 * 4,
+                "d2h_bytes_per_step": r["queries_per_step"] * 12},
+        "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
-
 
 # ------------------------------------------------------ paper-scale rows
 # Market data of the paper's Table marketData (Sec. 6); swaption price in basis
@@ -707,6 +920,8 @@ def run_paper(args, local_rank):
         "rows": rows,
     }
     print(json.dumps(line), flush=True)
+
+
 
 
 def main():

@@ -209,6 +209,26 @@ int amfrw_batch_kernel_times(amfrw_batch *b, float *ms_out, double *node_steps_o
  * (may be NULL) receives choice (1).  Prices change by rounding only.
  * Synchronises. */
 int amfrw_batch_autotune(amfrw_batch *b, int32_t trials, int32_t *use_multi_out);
+/* FP64 re-solve of ill-conditioned mixed-precision instances (the paper has no
+ * counterpart: it computes in FP64 only).  A mixed-precision price carries an
+ * error that is a small multiple of the combination's scale
+ * sum_l |c_l u_l| (about 3e-11 of it, measured against FP64), so where the
+ * combination sum cancels, kappa = sum_l |c_l u_l| / |sum_l c_l u_l| large,
+ * the relative error of the price grows by kappa.  Every amfrw_batch_run (and
+ * amfrw_solve_batch) computes kappa per instance in its combination kernel;
+ * mixed instances with kappa > kappa_max are re-solved in FP64 and
+ * recombined inside the same CUDA graph, by a conditional node that runs only
+ * when some instance is above the bound.  Default kappa_max: 1e5.
+ *   set_kappa_max  kappa_max <= 0 turns the re-solve off; takes effect at the
+ *                  next amfrw_batch_run.  Errors: EINVAL.
+ *   promoted       after a run: *n_promoted = instances re-solved in FP64 by
+ *                  the last run, kappa_out [n] (may be NULL) = each instance's
+ *                  kappa from that run's mixed or FP64 solve (0 when the
+ *                  re-solve is off or the batch has no mixed instance).
+ *                  Synchronises.  Errors: EINVAL, ECUDA. */
+int amfrw_batch_set_kappa_max(amfrw_batch *b, double kappa_max);
+int amfrw_batch_promoted(amfrw_batch *b, int32_t *n_promoted, double *kappa_out);
+
 /* Launch classes of a batch by work-group kind: warp groups, CTA groups
  * (grids in shared memory), global-memory groups.  Any pointer may be NULL. */
 int amfrw_batch_classes(const amfrw_batch *b, int32_t *n_warp, int32_t *n_cta, int32_t *n_global);
@@ -329,12 +349,29 @@ const char *amfrw_surrogate_last_error(void);
  *     on the GPU (different streams, or host threads) race and give wrong
  *     prices; serialise them.  The array keeps the previous call's contents;
  *     each call rewrites everything it reads and zeroes its counters.
- *   - The first call on a device looks up the array's device address (once
- *     per device, with that device current); make that first call before any
- *     stream capture begins.
+ *   - Each call looks up the array's device address for the calling thread's
+ *     current device (cheap once the library's module is loaded; nothing is
+ *     cached, so a device reset between calls is harmless).
+ *   - The call must not be recorded into a CUDA graph: it copies its records
+ *     from temporary host buffers that are freed when it returns.  A call
+ *     while cuda_stream is being captured returns EINVAL.
+ *   - The prices are not checked for finiteness (there is no host copy of
+ *     them to inspect without a synchronisation); the caller tests them.
  * Errors: EINVAL, ENOTPSD, ETOOBIG, ECUDA. */
 #define AMFRW_NOALLOC_SCRATCH_BYTES (16u << 20)
 int amfrw_solve_noalloc(const amfrw_params *ps, int32_t n, double *d_prices_out, void *cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Arithmetic peak of the current device (a measurement utility; the paper has
+ * no counterpart).  The solver kernels keep their grids in shared memory and
+ * are bound by the FP64 or FP32 pipes, whose rates are not among the copy and
+ * GEMM peaks measured elsewhere, so the library measures them itself: every
+ * resident thread of the device runs 8 independent FMA chains of `iters`
+ * dependent FMAs (precision AMFRW_FP64, or 2 for FP32), timed with CUDA events
+ * on cuda_stream (the best of 5 launches after a warm-up).
+ * *tflops_out = 2 x FMAs / time, in TFLOP/s.  Synchronises.
+ * Errors: EINVAL (NULL, iters < 1, unknown precision), ECUDA. */
+int amfrw_peak_probe(int32_t precision, int32_t iters, double *tflops_out, void *cuda_stream);
 
 const char *amfrw_status_string(int status);
 const char *amfrw_last_error(void);

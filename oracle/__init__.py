@@ -14,6 +14,7 @@ dense linear algebra, matrix exponentials, union point counts).
 from __future__ import annotations
 
 import ctypes as C
+import multiprocessing as mp
 import os
 import subprocess
 import threading
@@ -240,3 +241,29 @@ def price(inst: dict, n: int, psi: int = 0, full: bool = False, per_grid: bool =
         v = float(L.orc_price(C.byref(p), n, psi, int(full), _dp(u)))
         return v, u
     return float(L.orc_price(C.byref(p), n, psi, int(full), None))
+
+
+def _grid_value(job):
+    inst, levels = job
+    return solve_grid(inst, levels)
+
+
+def price_parallel(inst: dict, n: int, psi: int = 0, full: bool = False, workers: int | None = None) -> float:
+    """orc_price with the component grids solved in a spawned process pool
+    (largest grids first); the combination sum discount * sum_l c_l u_l then
+    runs here in enumeration order, the same sequence of FP64 roundings as
+    orc_price.  For the paper-size problems whose serial oracle takes minutes.
+    Spawned workers never touch CUDA, so callers may hold a CUDA context."""
+    lv, cf = enumerate_grids(int(inst["N"]), n, psi, full)
+    sizes = [int(np.prod([(1 << int(x)) + 1 for x in l])) for l in lv]
+    order = sorted(range(len(lv)), key=lambda k: -sizes[k])
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers or os.cpu_count() or 1) as pool:
+        vals = pool.map(_grid_value, [(inst, [int(x) for x in lv[k]]) for k in order], chunksize=1)
+    u = [0.0] * len(lv)
+    for k, v in zip(order, vals):
+        u[k] = v
+    s = 0.0
+    for k in range(len(lv)):
+        s += float(cf[k]) * u[k]
+    return float(inst["discount"]) * s

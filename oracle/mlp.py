@@ -61,6 +61,32 @@ def loss_and_grads(p: dict, X: np.ndarray, t: np.ndarray):
     return L, g
 
 
+def grad_abs_scale(p: dict, X: np.ndarray, t: np.ndarray) -> dict:
+    """Per-entry scale of every gradient: the chain rule of loss_and_grads
+    with every factor replaced by its absolute value, e.g. for W3 the
+    entries of |dZ3|^T |H2| with |dZ3| = |dy w4^T| |gelu'(Z3)|.  A gradient
+    computed from rounded operands (BF16 weights and activations, relative
+    rounding u = 2^-8) differs from the exact one by at most a small multiple
+    of u times this scale, entry by entry, whatever the cancellation in the
+    exact sum."""
+    y, (X, Z1, H1, Z2, H2, Z3, H3) = forward(p, X)
+    B = X.shape[0]
+    ady = np.abs(y - t) / B
+    s = {}
+    s["w4"] = np.abs(H3).T @ ady
+    s["b4"] = float(np.sum(ady))
+    a3 = np.outer(ady, np.abs(p["w4"])) * np.abs(gelu_grad(Z3))
+    s["W3"] = a3.T @ np.abs(H2)
+    s["b3"] = a3.sum(axis=0)
+    a2 = (a3 @ np.abs(p["W3"])) * np.abs(gelu_grad(Z2))
+    s["W2"] = a2.T @ np.abs(H1)
+    s["b2"] = a2.sum(axis=0)
+    a1 = (a2 @ np.abs(p["W2"])) * np.abs(gelu_grad(Z1))
+    s["W1"] = a1.T @ np.abs(X)
+    s["b1"] = a1.sum(axis=0)
+    return s
+
+
 def init_params(width: int = 256, n_in: int = 8, seed: int = 0) -> dict:
     rng = np.random.default_rng(seed)
     return {

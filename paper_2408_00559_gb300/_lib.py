@@ -34,7 +34,8 @@ EXPORTS = [
     "amfrw_surrogate_eval_features",
     "amfrw_surrogate_save",
     "amfrw_surrogate_load", "amfrw_surrogate_params", "amfrw_surrogate_grad",
-    "amfrw_surrogate_destroy", "amfrw_surrogate_last_error",
+    "amfrw_surrogate_destroy", "amfrw_surrogate_last_error", "amfrw_peak_probe",
+    "amfrw_batch_set_kappa_max", "amfrw_batch_promoted",
 ]
 SURROGATE_PARAMS = 136193
 
@@ -92,6 +93,9 @@ def lib():
                                                C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_int32)]
         L.amfrw_batch_io_bytes.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         L.amfrw_solve_noalloc.argtypes = [pp, C.c_int32, vp, vp]
+        L.amfrw_peak_probe.argtypes = [C.c_int32, C.c_int32, C.POINTER(C.c_double), vp]
+        L.amfrw_batch_set_kappa_max.argtypes = [vp, C.c_double]
+        L.amfrw_batch_promoted.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_double)]
         L.amfrw_batch_autotune.argtypes = [vp, C.c_int32, C.POINTER(C.c_int32)]
         L.amfrw_batch_classes.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
         i32 = C.c_int32
@@ -274,6 +278,18 @@ class Batch:
                "amfrw_batch_kernel_times")
         return [(dims[i], ms[i], ns[i]) for i in range(n.value)]
 
+    def set_kappa_max(self, kappa_max: float):
+        """Condition bound above which mixed instances are re-solved in FP64
+        inside the batch's graph (<= 0: off)."""
+        _check(lib().amfrw_batch_set_kappa_max(self.h, float(kappa_max)), "amfrw_batch_set_kappa_max")
+
+    def promoted(self):
+        """(instances re-solved in FP64 by the last run, kappa per instance)."""
+        n = C.c_int32()
+        kappa = np.zeros(self.n)
+        _check(lib().amfrw_batch_promoted(self.h, C.byref(n), _dp(kappa)), "amfrw_batch_promoted")
+        return n.value, kappa
+
     def autotune(self, trials: int = 2) -> bool:
         """Pick the faster launch strategy and grid-state placement on this
         device; True = one persistent multi-class launch for the warp-solved
@@ -313,6 +329,15 @@ def solve_noalloc(insts: list[dict], d_prices_ptr: int, stream=None):
     m = _Marshal(insts)
     _check(lib().amfrw_solve_noalloc(m.arr, len(insts), C.c_void_p(int(d_prices_ptr)),
                                      _stream_ptr(stream)), "amfrw_solve_noalloc")
+
+
+def peak_probe(precision: str = "fp64", iters: int = 4096, stream=None) -> float:
+    """amfrw_peak_probe: measured FMA throughput of the current device in
+    TFLOP/s for precision 'fp64' or 'fp32'."""
+    out = C.c_double(0.0)
+    code = {"fp64": 0, "fp32": 2}[precision]
+    _check(lib().amfrw_peak_probe(code, int(iters), C.byref(out), _stream_ptr(stream)), "amfrw_peak_probe")
+    return float(out.value)
 
 
 def tc_gemm_bf16(A, B, C, stream=None):

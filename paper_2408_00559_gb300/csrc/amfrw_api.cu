@@ -12,6 +12,7 @@
 #include <cstdlib>
 #include <string>
 #include <tuple>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -39,6 +40,10 @@ int fail(int status, const std::string& msg)
     } while (0)
 
 constexpr int kWarpMaxL = 64;          // grids up to this many Inner nodes: warp groups
+// Default condition bound above which a mixed-precision instance is re-solved
+// in FP64 (the mixed error measured relative to sum_l |c_l u_l| stays below
+// about 3e-11, so kappa <= 1e5 keeps the relative price error below 1e-5).
+constexpr double kKappaMaxDefault = 1e5;
 constexpr int kWarpsPerBlock = 4;
 
 // Warp groups have at least 4 lanes for FP64 (at most 8 grids per warp) and
@@ -295,6 +300,8 @@ struct Plan {
     ClassDesc* d_cdesc = nullptr;
     int64_t n_cdesc = 0;
     bool use_multi = true;  // launch strategy (the autotuner may switch it)
+    bool shared_u = false;  // d_u belongs to another plan (the FP64 re-solve writes there)
+    const int32_t* inst_mask = nullptr;  // instances to solve, or null for all
 
     ~Plan() { release(); }
     void release()
@@ -302,7 +309,7 @@ struct Plan {
         cudaFree(d_insts);
         cudaFree(d_items);
         cudaFree(d_coefs);
-        cudaFree(d_u);
+        if (!shared_u) cudaFree(d_u);
         cudaFree(d_prices);
         cudaFree(d_queue);
         cudaFree(d_flag);
@@ -541,11 +548,26 @@ int build_warp_launches(Plan& P)
         }
     }
     int64_t off = 0;
+    int smem_sm = 0, reserved = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
     for (const std::vector<int>& g : groups) {
         Plan::WarpLaunch w;
         w.N = P.classes[g[0]].N;
         w.mixed = P.classes[g[0]].mixed;
         w.covers = g;
+        // A multi-class launch sizes every warp's shared memory for its most
+        // demanding class.  So that this does not cost residency, a class
+        // whose groups of one warp need more than the share of an SM that
+        // the register-limited number of warps leaves each warp gets fewer,
+        // wider groups (more lanes per grid).
+        int budget = 1 << 30;
+        if (g.size() > 1 && smem_sm > 0) {
+            const int blocks = occ_for(w.N)(w.mixed, kWarpGroup, 32 * kWarpsPerBlock, 0);
+            if (blocks > 0)
+                budget = (smem_sm - blocks * reserved) / (blocks * kWarpsPerBlock);
+        }
         int items = 0;
         for (int c : g) {
             const LaunchClass& L = P.classes[c];
@@ -555,9 +577,19 @@ int build_warp_launches(Plan& P)
             d.item_count = L.item_count;
             d.smem_group = L.smem_group;
             d.qidx = c;
+            while (d.glog < 5 && ((int64_t)d.smem_group << (5 - d.glog)) > budget) {
+                ++d.glog;
+                int sg = 0;
+                for (int q = L.item_begin; q < L.item_begin + L.item_count; ++q) {
+                    if (q > L.item_begin && memcmp(P.items[q].lv, P.items[q - 1].lv, sizeof(P.items[q].lv)) == 0)
+                        continue;  // equal shapes are adjacent
+                    sg = std::max(sg, make_layout(L.N, P.items[q].lv, L.mixed, kWarpGroup, d.glog).total);
+                }
+                d.smem_group = sg;
+            }
             w.cls.push_back(d);
-            w.smem_warp = std::max(w.smem_warp, L.smem_group << (5 - L.glog));
-            items += L.item_count << L.glog;  // lanes of work
+            w.smem_warp = std::max(w.smem_warp, d.smem_group << (5 - d.glog));
+            items += d.item_count << d.glog;  // lanes of work
         }
         if (w.smem_warp > smem_cap)
             return fail(AMFRW_ETOOBIG, "the work groups of one warp do not fit in shared memory");
@@ -619,18 +651,58 @@ int build_plan(const amfrw_params* ps, int n, void* stream, bool keep_state, Pla
     return AMFRW_OK;
 }
 
+// Promotion of ill-conditioned mixed-precision instances.  The error of a
+// mixed-precision price is a small multiple of the combination's scale
+// sum_l |c_l u_l| (the FP32 increments perturb every u_l relative to its own
+// size), so where the sum cancels -- kappa = sum_l |c_l u_l| / |sum_l c_l u_l|
+// above kappa_max -- the relative error of the price is not bounded by that
+// of the grid values.  Those instances are marked and re-solved in FP64 by a
+// conditional body of the batch's graph, which runs only when one is marked.
+struct Promote {
+    double kappa_max;
+    int32_t* mask = nullptr;    // [n] 1: re-solve in FP64
+    double* kappa = nullptr;    // [n] kappa of the last mixed solve
+    int32_t* count = nullptr;   // instances marked
+    unsigned* done = nullptr;   // blocks finished (the last one sets the conditional)
+    cudaGraphConditionalHandle cond = 0;
+};
+
+// price = discount * sum_l c_l u_l in FP64, grids in a fixed order
+// (eqs. standardCombTechnique / modifiedCombTechnique).  only != null: the
+// marked instances alone (after their FP64 re-solve).
 __global__ void combine_kernel(const InstDev* __restrict__ insts, int n, const double* __restrict__ coefs,
                                const double* __restrict__ u, double* __restrict__ prices,
-                               int32_t* __restrict__ nonfinite)
+                               int32_t* __restrict__ nonfinite, Promote pr, const int32_t* __restrict__ only)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const InstDev& I = insts[i];
-    double s = 0.0;
-    for (int k = I.grid_begin; k < I.grid_begin + I.grid_count; ++k) s += coefs[k] * u[k];
-    const double p = I.discount * s;
-    prices[i] = p;
-    if (!isfinite(p)) atomicOr(nonfinite, 1);
+    if (i < n && (!only || only[i])) {
+        const InstDev& I = insts[i];
+        double s = 0.0, sc = 0.0;
+        for (int k = I.grid_begin; k < I.grid_begin + I.grid_count; ++k) {
+            s = fma(coefs[k], u[k], s);
+            sc += fabs(coefs[k] * u[k]);
+        }
+        const double p = I.discount * s;
+        prices[i] = p;
+        if (!isfinite(p)) atomicOr(nonfinite, 1);
+        if (pr.mask) {
+            const double kappa = sc / fabs(s);
+            pr.kappa[i] = kappa;
+            const bool bad = I.precision == AMFRW_MIXED && !(kappa <= pr.kappa_max);
+            pr.mask[i] = bad ? 1 : 0;
+            if (bad) atomicAdd(pr.count, 1);
+        }
+    }
+    if (pr.cond) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (atomicAdd(pr.done, 1u) == gridDim.x - 1) {
+                __threadfence();
+                cudaGraphSetConditional(pr.cond, atomicAdd(pr.count, 0) > 0 ? 1u : 0u);
+            }
+        }
+    }
 }
 
 // Solve launches for every class.  steps < 0: each instance's own n_steps.
@@ -648,6 +720,7 @@ SolveArgs class_args(const Plan& P, const LaunchClass& L, int c, int steps, int 
     a.queue = P.d_queue + c;
     a.lu_scratch = P.d_lu ? P.d_lu + L.lu_offset : nullptr;
     a.lu_stride = L.lu_stride;
+    a.inst_mask = P.inst_mask;
     return a;
 }
 
@@ -695,12 +768,17 @@ int run_solve(Plan& P, int steps, int flags, cudaEvent_t* ev = nullptr)
     return AMFRW_OK;
 }
 
-int run_combine(Plan& P, double* d_out)
+int run_combine(Plan& P, double* d_out, const Promote* pr = nullptr, const int32_t* only = nullptr)
 {
-    CUDA_TRY(cudaMemsetAsync(P.d_flag, 0, sizeof(int32_t), P.stream));
+    if (!only) CUDA_TRY(cudaMemsetAsync(P.d_flag, 0, sizeof(int32_t), P.stream));
+    Promote none{};
+    if (pr && pr->mask) {
+        CUDA_TRY(cudaMemsetAsync(pr->count, 0, sizeof(int32_t), P.stream));
+        CUDA_TRY(cudaMemsetAsync(pr->done, 0, sizeof(unsigned), P.stream));
+    }
     const int b = 128;
     combine_kernel<<<(P.n_inst + b - 1) / b, b, 0, P.stream>>>(P.d_insts, P.n_inst, P.d_coefs, P.d_u,
-                                                               d_out, P.d_flag);
+                                                               d_out, P.d_flag, pr ? *pr : none, only);
     CUDA_TRY(cudaGetLastError());
     return AMFRW_OK;
 }
@@ -767,13 +845,27 @@ struct amfrw_batch {
     bool timing = false;
     std::vector<cudaEvent_t> ev;       // two per launch record
     cudaStream_t capture = nullptr;    // private stream the graph is captured on
+    cudaStream_t side = nullptr;       // stream the conditional body is captured on
     cudaGraphExec_t exec = nullptr;    // the captured solve + combination
     bool exec_timing = false;          // whether the graph records the timing events
+    // FP64 re-solve of ill-conditioned mixed-precision instances: the batch
+    // planned in FP64 (its grid values go to plan.d_u), the marks and counters
+    std::unique_ptr<Plan> promo;
+    double kappa_max = 0.0;            // <= 0: no promotion
+    int32_t* d_mask = nullptr;
+    double* d_kappa = nullptr;
+    int32_t* d_pcount = nullptr;
+    unsigned* d_done = nullptr;
     ~amfrw_batch()
     {
         if (exec) cudaGraphExecDestroy(exec);
         if (capture) cudaStreamDestroy(capture);
+        if (side) cudaStreamDestroy(side);
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        cudaFree(d_mask);
+        cudaFree(d_kappa);
+        cudaFree(d_pcount);
+        cudaFree(d_done);
     }
 };
 
@@ -849,7 +941,10 @@ int apply_choice(Plan& P, int choice)
     return st;
 }
 
-// Capture solve + combination into a CUDA graph on the batch's private stream.
+// Capture solve + combination into a CUDA graph on the batch's private
+// stream.  With promotion on, the combination also marks the ill-conditioned
+// mixed-precision instances and sets a conditional; the conditional node's
+// body re-solves the marked instances in FP64 and recombines them.
 int capture_graph(amfrw_batch* b)
 {
     Plan& P = b->plan;
@@ -858,12 +953,62 @@ int capture_graph(amfrw_batch* b)
         b->exec = nullptr;
     }
     if (!b->capture) CUDA_TRY(cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking));
+    const bool promote = b->promo && b->kappa_max > 0.0;
+    if (promote && !b->side) CUDA_TRY(cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking));
     cudaStream_t user = P.stream;
     P.stream = b->capture;
     CUDA_TRY(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal));
-    int st = run_solve(P, P.insts[0].n_steps, 0, b->timing ? b->ev.data() : nullptr);
-    if (st == AMFRW_OK) st = run_combine(P, P.d_prices);
     cudaGraph_t g = nullptr;
+    int st = run_solve(P, P.insts[0].n_steps, 0, b->timing ? b->ev.data() : nullptr);
+    Promote pr{};
+    if (st == AMFRW_OK && promote) {
+        pr.kappa_max = b->kappa_max;
+        pr.mask = b->d_mask;
+        pr.kappa = b->d_kappa;
+        pr.count = b->d_pcount;
+        pr.done = b->d_done;
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t cg = nullptr;
+        if (cudaStreamGetCaptureInfo(b->capture, &cs, nullptr, &cg) != cudaSuccess ||
+            cudaGraphConditionalHandleCreate(&pr.cond, cg, 0, cudaGraphCondAssignDefault) != cudaSuccess)
+            st = fail(AMFRW_ECUDA, "conditional handle");
+    }
+    if (st == AMFRW_OK) st = run_combine(P, P.d_prices, promote ? &pr : nullptr);
+    if (st == AMFRW_OK && promote) {
+        // if (any instance marked) { FP64 re-solve of the marked instances; recombine them }
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t cg = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        cudaGraphNode_t node = nullptr;
+        cudaGraphNodeParams np{};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = pr.cond;
+        np.conditional.type = cudaGraphCondTypeIf;
+        np.conditional.size = 1;
+        if (cudaStreamGetCaptureInfo(b->capture, &cs, nullptr, &cg, &deps, nullptr, &nd) != cudaSuccess ||
+            cudaGraphAddNode(&node, cg, deps, nullptr, nd, &np) != cudaSuccess ||
+            cudaStreamUpdateCaptureDependencies(b->capture, &node, nullptr, 1, cudaStreamSetCaptureDependencies) !=
+                cudaSuccess)
+            st = fail(AMFRW_ECUDA, "conditional node");
+        if (st == AMFRW_OK) {
+            cudaGraph_t body = np.conditional.phGraph_out[0];
+            Plan& Q = *b->promo;
+            Q.stream = b->side;
+            P.stream = b->side;
+            cudaError_t e = cudaStreamBeginCaptureToGraph(b->side, body, nullptr, nullptr, 0,
+                                                          cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) st = fail(AMFRW_ECUDA, std::string("body capture: ") + cudaGetErrorString(e));
+            if (st == AMFRW_OK) st = run_solve(Q, Q.insts[0].n_steps, 0);
+            if (st == AMFRW_OK) st = run_combine(P, P.d_prices, nullptr, b->d_mask);
+            cudaGraph_t body_out = nullptr;
+            e = cudaStreamEndCapture(b->side, &body_out);
+            if (st == AMFRW_OK && e != cudaSuccess)
+                st = fail(AMFRW_ECUDA, std::string("body capture: ") + cudaGetErrorString(e));
+            P.stream = b->capture;
+            Q.stream = user;
+        }
+    }
     cudaError_t e = cudaStreamEndCapture(b->capture, &g);
     P.stream = user;
     if (st != AMFRW_OK) {
@@ -875,6 +1020,35 @@ int capture_graph(amfrw_batch* b)
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(AMFRW_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
     b->exec_timing = b->timing;
+    return AMFRW_OK;
+}
+
+// The FP64 plan of a batch's instances for the re-solve of ill-conditioned
+// mixed-precision instances; its grid values go to the batch's own array.
+int build_promotion(amfrw_batch* b, const amfrw_params* ps, int n, void* stream)
+{
+    bool any = false;
+    for (int i = 0; i < n; ++i) any |= ps[i].precision == AMFRW_MIXED;
+    if (!any) return AMFRW_OK;
+    std::vector<amfrw_params> q(ps, ps + n);
+    for (amfrw_params& x : q) x.precision = AMFRW_FP64;
+    b->promo.reset(new (std::nothrow) Plan());
+    if (!b->promo) return fail(AMFRW_ENOMEM, "host allocation failed");
+    Plan& Q = *b->promo;
+    int st = build_plan(q.data(), n, stream, false, Q);
+    if (st != AMFRW_OK) return st;
+    cudaFree(Q.d_u);
+    Q.d_u = b->plan.d_u;
+    Q.shared_u = true;
+    CUDA_TRY(cudaMalloc(&b->d_mask, sizeof(int32_t) * n));
+    CUDA_TRY(cudaMalloc(&b->d_kappa, sizeof(double) * n));
+    CUDA_TRY(cudaMalloc(&b->d_pcount, sizeof(int32_t)));
+    CUDA_TRY(cudaMalloc(&b->d_done, sizeof(unsigned)));
+    CUDA_TRY(cudaMemsetAsync(b->d_mask, 0, sizeof(int32_t) * n, (cudaStream_t)stream));
+    CUDA_TRY(cudaMemsetAsync(b->d_kappa, 0, sizeof(double) * n, (cudaStream_t)stream));
+    CUDA_TRY(cudaMemsetAsync(b->d_pcount, 0, sizeof(int32_t), (cudaStream_t)stream));
+    Q.inst_mask = b->d_mask;
+    b->kappa_max = kKappaMaxDefault;
     return AMFRW_OK;
 }
 
@@ -1032,6 +1206,11 @@ int amfrw_batch_create(const amfrw_params* ps, int32_t n, void* cuda_stream, amf
             }
         }
     }
+    st = build_promotion(b, ps, n, cuda_stream);
+    if (st != AMFRW_OK) {
+        delete b;
+        return st;
+    }
     *out = b;
     return AMFRW_OK;
 }
@@ -1151,6 +1330,35 @@ int amfrw_batch_autotune(amfrw_batch* b, int32_t trials, int32_t* use_multi_out)
     return AMFRW_OK;
 }
 
+int amfrw_batch_set_kappa_max(amfrw_batch* b, double kappa_max)
+{
+    if (!b || !std::isfinite(kappa_max)) return fail(AMFRW_EINVAL, "NULL argument or kappa_max not finite");
+    if (kappa_max != b->kappa_max && b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    b->kappa_max = b->promo ? kappa_max : 0.0;
+    return AMFRW_OK;
+}
+
+int amfrw_batch_promoted(amfrw_batch* b, int32_t* n_promoted, double* kappa_out)
+{
+    if (!b || !n_promoted) return fail(AMFRW_EINVAL, "NULL argument");
+    Plan& P = b->plan;
+    int32_t c = 0;
+    if (b->d_pcount && b->kappa_max > 0.0) {
+        CUDA_TRY(cudaMemcpyAsync(&c, b->d_pcount, sizeof(int32_t), cudaMemcpyDeviceToHost, P.stream));
+        if (kappa_out)
+            CUDA_TRY(cudaMemcpyAsync(kappa_out, b->d_kappa, sizeof(double) * P.n_inst, cudaMemcpyDeviceToHost,
+                                     P.stream));
+        CUDA_TRY(cudaStreamSynchronize(P.stream));
+    } else if (kappa_out) {
+        for (int i = 0; i < P.n_inst; ++i) kappa_out[i] = 0.0;
+    }
+    *n_promoted = c;
+    return AMFRW_OK;
+}
+
 int amfrw_batch_classes(const amfrw_batch* b, int32_t* n_warp, int32_t* n_cta, int32_t* n_global)
 {
     if (!b) return fail(AMFRW_EINVAL, "NULL argument");
@@ -1264,25 +1472,16 @@ namespace {
 // the grids solved by whole blocks.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[AMFRW_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mutex;
-unsigned char* g_noalloc_ptr[kMaxDevices] = {};
-
 // Device address of g_noalloc_scratch on the current device.  In host code
 // the array's name only stands in for the symbol, so the address is asked
-// from the runtime once per device, with that device current, and cached.
+// from the runtime, with the calling thread's device current, on every call:
+// the lookup is cheap once the module is loaded, and an address cached past a
+// device reset (which unloads the module) would point at unmapped memory.
 int noalloc_scratch(unsigned char** out)
 {
-    int dev = 0;
-    CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return fail(AMFRW_EINVAL, "device ordinal out of range");
-    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_ptr[dev]) {
-        void* p = nullptr;
-        CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-        g_noalloc_ptr[dev] = static_cast<unsigned char*>(p);
-    }
-    *out = g_noalloc_ptr[dev];
+    void* p = nullptr;
+    CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    *out = static_cast<unsigned char*>(p);
     return AMFRW_OK;
 }
 
@@ -1364,6 +1563,15 @@ extern "C" int amfrw_solve_noalloc(const amfrw_params* ps, int32_t n, double* d_
                                    void* cuda_stream)
 {
     if (!d_prices_out) return fail(AMFRW_EINVAL, "d_prices_out is NULL");
+    if (n < 1) return fail(AMFRW_EINVAL, "need at least one instance");
+    if (!ps) return fail(AMFRW_EINVAL, "params is NULL");
+    // The host records are copied from temporary host buffers that are freed
+    // on return, so the call cannot be recorded into a CUDA graph: a replay
+    // would read freed host memory.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CUDA_TRY(cudaStreamIsCapturing((cudaStream_t)cuda_stream, &cap));
+    if (cap != cudaStreamCaptureStatusNone)
+        return fail(AMFRW_EINVAL, "amfrw_solve_noalloc must not be called while its stream is being captured");
     alignas(Plan) unsigned char buf[sizeof(Plan)];
     Plan* P = new (buf) Plan();
     const int st = noalloc_run(ps, n, d_prices_out, (cudaStream_t)cuda_stream, *P);

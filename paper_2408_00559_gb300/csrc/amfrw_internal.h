@@ -39,7 +39,7 @@ struct Item {
 // to size dynamic shared memory, the device to place the arrays; both call
 // this one function so they cannot disagree.
 struct Layout {
-    int32_t cd, cf, tabd, tabf, pay, lu, Z, ZZ, H, FY, K1, K0, Kw, D, C, scr, total;
+    int32_t meta, cd, cf, tabd, tabf, pay, lu, Z, ZZ, H, FY, K1, K0, Kw, D, C, scr, total;
     int32_t L, Lp, Lr, ntab, npay, nlu, ncoef;
 };
 
@@ -61,7 +61,33 @@ struct Consts {
     T g2[kMaxDim];                      // 1 / (2 h_i)
 };
 
-AMFRW_HD int32_t align16(int32_t x) { return (x + 15) & ~15; }
+// Active axes of a grid (those with more than one Inner row) for the
+// mixed-precision stencil, built once per grid in shared memory.
+struct ActAxes {
+    int n;                      // active axes, ascending axis order
+    int nr;                     // active rate axes (the first nr of them; V, if active, is last)
+    int sh[kMaxDim];            // bit offset of j - 1 in the node index t
+    int msk[kMaxDim];           // M - 1
+    int Sp[kMaxDim];            // padded stride
+    int toff[kMaxDim];          // rate axes: offset of their coefficient tables (d, pw, drift)
+    int M[kMaxDim];             // rows
+    int ax[kMaxDim];            // the axis index
+    int drift[kMaxDim];         // 1: rate axis with a drift term (rates 2..N-1)
+    float g2[kMaxDim];          // 1 / (2 h) (drift gradient)
+    float sconst[kMaxDim];      // drift sum: the part of the inactive rates
+    float cinact;               // second-difference coefficients of the inactive axes, summed
+    float cx[kMaxDim][kMaxDim]; // pair (q, r), q < r: rho/(4 h h) (two rates) or sigma phi/(4 h h_V)
+    float drh[kMaxDim][kMaxDim];// drift of active rate q: rho for the active rates r <= q
+};
+
+// Per-grid descriptors the mixed-precision solver keeps in shared memory:
+// the grid's shape (9 per-axis arrays and 6 scalars of int) and its active
+// axes.  Warp groups hold them in their layout; whole-block groups in a
+// static shared array of the kernel.
+AMFRW_HD constexpr int32_t align16(int32_t x) { return (x + 15) & ~15; }
+AMFRW_HD constexpr int shape_bytes(int N) { return align16(4 * (9 * N + 6)); }
+AMFRW_HD constexpr int meta_bytes(int N) { return shape_bytes(N) + align16((int)sizeof(ActAxes)); }
+constexpr int kMetaBytesMax = meta_bytes(kMaxDim);
 
 // Work-group kinds.  kWarpGroup: a grid of at most 64 Inner nodes on (part
 // of) one warp, everything in shared memory.  kCtaGroup: one CTA per grid,
@@ -136,24 +162,50 @@ AMFRW_HD Layout make_layout(int N, const int8_t* lv, bool mixed, int kind, int t
     y.nlu = nlu;
     const int sk = mixed ? 4 : 8;  // bytes of an increment / table value
     int o = 0;
-    y.cd = o;   o = align16(o + (int)sizeof(Consts<double>));
-    y.cf = o;   o = align16(o + (mixed ? (int)sizeof(Consts<float>) : 0));
-    y.tabd = o; o = align16(o + 8 * y.ntab);
-    y.tabf = o; o = align16(o + (mixed ? 4 * y.ntab : 0));
-    y.pay = o;  o = align16(o + 8 * y.npay);
-    y.lu = o;   o = align16(o + (lu_in ? sk * y.nlu : 0));
-    y.Z = o;    o = align16(o + 8 * y.Lp);
-    y.ZZ = o;   o = align16(o + (mixed ? 8 * y.Lp : 0));
-    y.H = o;    o = align16(o + sk * y.Lr);
-    y.FY = o;   o = align16(o + (mixed ? 4 * y.Lp : 0));
-    y.K1 = o;   o = align16(o + sk * y.Lp);
-    y.K0 = o;   o = align16(o + sk * y.Lp);
-    y.Kw = o;   o = align16(o + sk * y.Lp);
-    // FP64 warp groups: central differences per axis and per-node coefficients
-    const bool diff = !mixed && kind == kWarpGroup;
-    y.ncoef = diff ? node_coefs(N) : 0;
-    y.D = o;    o = align16(o + (diff ? 8 * N * y.Lp : 0));
-    y.C = o;    o = align16(o + 8 * y.ncoef * y.Lp);
+    if (mixed) {
+        // The FP64 constants and tables serve the per-grid setup only (tables,
+        // line-solve factors, F of the payoff); the time loop reads their FP32
+        // copies.  They share one region with the time loop's vectors.
+        y.meta = o; o = align16(o + (kind == kWarpGroup ? meta_bytes(N) : 0));
+        y.cf = o;   o = align16(o + (int)sizeof(Consts<float>));
+        y.tabf = o; o = align16(o + 4 * y.ntab);
+        y.pay = o;  o = align16(o + 8 * y.npay);
+        y.lu = o;   o = align16(o + (lu_in ? 4 * y.nlu : 0));
+        y.Z = o;    o = align16(o + 8 * y.Lp);
+        y.ZZ = o;   o = align16(o + 8 * y.Lp);
+        y.H = o;    o = align16(o + 4 * y.Lr);
+        int a = o, b = o;
+        y.cd = a;   a = align16(a + (int)sizeof(Consts<double>));
+        y.tabd = a; a = align16(a + 8 * y.ntab);
+        y.FY = b;   b = align16(b + 4 * y.Lp);
+        y.K1 = b;   b = align16(b + 4 * y.Lp);
+        y.K0 = b;   b = align16(b + 4 * y.Lp);
+        y.Kw = b;   b = align16(b + 4 * y.Lp);
+        o = a > b ? a : b;
+        y.ncoef = 0;
+        y.D = o;
+        y.C = o;
+    } else {
+        y.meta = o;
+        y.cd = o;   o = align16(o + (int)sizeof(Consts<double>));
+        y.cf = o;
+        y.tabd = o; o = align16(o + 8 * y.ntab);
+        y.tabf = o;
+        y.pay = o;  o = align16(o + 8 * y.npay);
+        y.lu = o;   o = align16(o + (lu_in ? 8 * y.nlu : 0));
+        y.Z = o;    o = align16(o + 8 * y.Lp);
+        y.ZZ = o;
+        y.H = o;    o = align16(o + 8 * y.Lr);
+        y.FY = o;
+        y.K1 = o;   o = align16(o + 8 * y.Lp);
+        y.K0 = o;   o = align16(o + 8 * y.Lp);
+        y.Kw = o;   o = align16(o + 8 * y.Lp);
+        // FP64 warp groups: central differences per axis and per-node coefficients
+        const bool diff = kind == kWarpGroup;
+        y.ncoef = diff ? node_coefs(N) : 0;
+        y.D = o;    o = align16(o + (diff ? 8 * N * y.Lp : 0));
+        y.C = o;    o = align16(o + 8 * y.ncoef * y.Lp);
+    }
     int rmax = 0;
     for (int i = 0; i < N; ++i) {
         const int rows = (i < N - 1 ? MV : 1) << lv[i];
@@ -187,6 +239,9 @@ struct SolveArgs {
     const ClassDesc* classes;
     int32_t n_classes;
     int32_t smem_warp;    // dynamic shared bytes per warp
+    // instances to solve (nonzero entries), or null for all: the FP64
+    // re-solve of ill-conditioned mixed-precision instances skips the others
+    const int32_t* inst_mask;
 };
 
 constexpr int kLoadState = 1;

@@ -43,6 +43,9 @@
 
 namespace amfrw {
 
+// Resident blocks of 128 threads per SM the mixed-precision warp kernels are
+// compiled for (it caps their registers).
+constexpr int kWarpBlocksMixed = 4;
 constexpr double kA21 = 2.0 / 3.0;   // eq. (coef_W2)
 constexpr double kQ21 = -4.0 / 3.0;
 constexpr double kB1 = 5.0 / 4.0;
@@ -138,6 +141,7 @@ struct ArrSrc {  // stored increments or Z: zero on Outer nodes
         return valid ? X[J + off] : T(0);
     }
     __device__ static __forceinline__ T diff(V a, V b) { return a - b; }
+    __device__ static __forceinline__ T val(V a) { return a; }
 };
 
 struct DFSrc {  // Z as an unevaluated float pair hi + lo
@@ -150,6 +154,7 @@ struct DFSrc {  // Z as an unevaluated float pair hi + lo
     }
     // hi parts of nearby values are close, so hi_a - hi_b is (nearly) exact
     __device__ static __forceinline__ float diff(V a, V b) { return (a.x - b.x) + (a.y - b.y); }
+    __device__ static __forceinline__ float val(V a) { return a.x + a.y; }
 };
 
 // Payoff g at rate multi-index jj (Sec. 2).  Caplet: (F_1 - K)^+.
@@ -1342,6 +1347,313 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
     gsync<WARP>(gm);  // the group's shared memory is reused by its next grid
 }
 
+// ---------------------------------------------- mixed precision, any N
+// The mixed-precision solver keeps the grid's shape and a table of its
+// active axes (those with more than one Inner row) in shared memory and walks
+// that table with run-time loops, so one copy of the stencil and of each line
+// sweep serves every grid of every dimension: the code stays small enough for
+// the instruction cache and no per-thread copy of the shape spills to local
+// memory.  An axis with one Inner row contributes only its second difference
+// -2 x0 (both neighbours are zero: the Outer node and its ghost reflection),
+// and no cross or drift term (every node lies on its upper face); those
+// contributions are summed into one coefficient per grid.
+
+static_assert(sizeof(Shape<2>) <= shape_bytes(2) && sizeof(Shape<8>) <= shape_bytes(8),
+              "Shape exceeds its reserved shared memory");
+
+template <int N>
+__device__ void build_act(const Shape<N>& s, const Consts<float>& c, const float* tab, ActAxes& A)
+{
+    int n = 0;
+    float cin = 0.f;
+    for (int i = 0; i < N; ++i) {
+        if (s.M[i] > 1) {
+            A.sh[n] = s.sh[i];
+            A.msk[n] = s.M[i] - 1;
+            A.M[n] = s.M[i];
+            A.Sp[n] = s.Sp[i];
+            A.toff[n] = s.toff[i];
+            A.ax[n] = i;
+            A.g2[n] = c.g2[i];
+            A.drift[n] = (i >= 1 && i < N - 1) ? 1 : 0;
+            ++n;
+        } else {
+            cin += (i < N - 1) ? tab[s.toff[i]] : c.cV;  // the coefficient at j = 1
+        }
+    }
+    A.n = n;
+    A.nr = (s.M[N - 1] > 1) ? n - 1 : n;
+    A.cinact = cin;
+    for (int q = 0; q < n; ++q) {
+        const int i = A.ax[q];
+        for (int r = 0; r < kMaxDim; ++r) {
+            A.cx[q][r] = 0.f;
+            A.drh[q][r] = 0.f;
+        }
+        if (i >= N - 1) continue;
+        for (int r = q + 1; r < n; ++r) {
+            const int k = A.ax[r];
+            A.cx[q][r] = (k < N - 1) ? c.rm[upair(i, k)] : c.sm[i];
+        }
+        float sc = 0.f;
+        if (A.drift[q]) {
+            for (int r = 1; r <= i; ++r)
+                if (s.M[r] == 1) sc += c.rh[ltri(i, r)] * tab[s.toff[r] + 2];  // j_r = 1
+            for (int r = 0; r <= q; ++r)
+                if (A.ax[r] >= 1) A.drh[q][r] = c.rh[ltri(i, A.ax[r])];
+        }
+        A.sconst[q] = sc;
+    }
+}
+
+// Sketch 1 at node t (padded index J) divided by V^2, from the active-axis
+// table: the same terms as stencil_acc (second differences with the Neumann
+// ghost, cross differences and drift off the upper faces, zero Outer values),
+// with the inactive axes' second differences folded into one coefficient.
+template <class Src>
+__device__ __forceinline__ float stencil_act(const ActAxes& A, const float* __restrict__ tab, float cV,
+                                             int t, int J, const Src& src)
+{
+    using V = typename Src::V;
+    const V x0 = src.ctr(J);
+    const float xv = Src::val(x0);
+    float acc = A.cinact * (-2.f * xv);
+    const int n = A.n, nr = A.nr;
+#pragma unroll 1
+    for (int q = 0; q < n; ++q) {
+        const int Sp = A.Sp[q];
+        const int msk = A.msk[q];
+        const int jm = (t >> A.sh[q]) & msk;  // j - 1
+        const bool lo = jm > 0;
+        const bool top = jm == msk;
+        const V m = src.nb(J, -Sp, lo, 0, 0, 0, 0);
+        const V p = top ? m : src.nb(J, Sp, true, 0, 0, 0, 0);
+        const float dp = Src::diff(p, x0);
+        const float dm = Src::diff(x0, m);
+        const bool rate = q < nr;
+        const int to = A.toff[q];
+        acc += (rate ? tab[to + jm] : cV) * (dp - dm);
+        if (rate && !top) {
+            const int Mq = A.M[q];
+            float inner = 0.f;
+#pragma unroll 1
+            for (int r = q + 1; r < n; ++r) {
+                const int mr = A.msk[r];
+                const int jr = (t >> A.sh[r]) & mr;
+                if (jr != mr) {
+                    const int Sr = A.Sp[r];
+                    const bool lr = jr > 0;
+                    const V pp = src.nb(J, Sp + Sr, true, 0, 0, 0, 0);
+                    const V pm = src.nb(J, Sp - Sr, lr, 0, 0, 0, 0);
+                    const V mp = src.nb(J, -Sp + Sr, lo, 0, 0, 0, 0);
+                    const V mm = src.nb(J, -Sp - Sr, lo && lr, 0, 0, 0, 0);
+                    const float mix = Src::diff(pp, pm) - Src::diff(mp, mm);
+                    const float ck = (r < nr) ? A.cx[q][r] * tab[A.toff[r] + A.M[r] + jr] : A.cx[q][r];
+                    inner += ck * mix;
+                }
+            }
+            if (A.drift[q]) {  // drift of rates 2..N-1 (eq. coef_adv), sum over rates 2..i
+                float S = A.sconst[q];
+#pragma unroll 1
+                for (int r = 0; r <= q; ++r) {
+                    const float w = A.drh[q][r];
+                    if (w != 0.f) S += w * tab[A.toff[r] + 2 * A.M[r] + ((t >> A.sh[r]) & A.msk[r])];
+                }
+                inner += S * A.g2[q] * (dp + dm);
+            }
+            acc += tab[to + Mq + jm] * inner;
+        }
+    }
+    return acc;
+}
+
+// Multilinear interpolation at the spot x* = (F_1(0), ..., V0) of Y = G + Z
+// (Sec. 5.1).  The 2^N corners of the containing cell are shared among up to
+// 32 lanes of the group (a whole warp group, or the first warp of a CTA),
+// which sum them by a shuffle reduction; corners of weight zero are skipped.
+template <int N, bool WARP>
+__device__ __forceinline__ void interp_spot(const Shape<N>& s, const InstDev& P, const double* pay,
+                                            const double* Z, double* u_out, int rank, int gsize, unsigned gm)
+{
+    const int il = gsize < 32 ? gsize : 32;
+    if (rank < il) {
+        int c[N];
+        double w[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            const double x = (i < N - 1) ? P.F0[i] : P.V0;
+            const double sx = x / P.Fmax[i] * (double)s.M[i];  // x / h_i, h_i = Fmax_i / M_i
+            int ci = (int)floor(sx);
+            ci = ci > s.M[i] - 1 ? s.M[i] - 1 : ci;
+            ci = ci < 0 ? 0 : ci;
+            c[i] = ci;
+            w[i] = sx - (double)ci;
+        }
+        double u = 0.0;
+        for (int corner = rank; corner < (1 << N); corner += il) {
+            double wt = 1.0;
+            int jj[N];
+            bool outer = false;
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                const int bit = (corner >> i) & 1;
+                wt *= bit ? w[i] : 1.0 - w[i];
+                jj[i] = c[i] + bit;
+                outer |= jj[i] == 0;
+            }
+            if (wt == 0.0) continue;
+            double zv = 0.0;
+            if (!outer) {
+                int t = 0;
+#pragma unroll
+                for (int i = 0; i < N; ++i) t += (jj[i] - 1) << s.sh[i];
+                zv = Z[s.padded(t)];
+            }
+            u += wt * (payoff_at<N>(s, pay, P.payoff, jj) + zv);
+        }
+        const unsigned im = WARP ? gm : 0xffffffffu;
+        for (int off = il >> 1; off > 0; off >>= 1) u += __shfl_xor_sync(im, u, off, il);
+        if (rank == 0) *u_out = u;
+    }
+}
+
+// One grid in mixed precision: the F evaluations and line solves in FP32 on
+// the increments, Z accumulated in FP64 beside its hi/lo float pair, F of the
+// payoff (H), the interpolation and the state in FP64.  Each step runs four
+// phases, each one F evaluation followed by the directional solves:
+//   0: K0 = dt F(Y_n) (kept as FY),            solves K0 -> Kw
+//   1: K0 = 2 K0 - Kw + theta dt F_0(Kw),      solves K0 -> K1
+//   2: K0 = FY + a21 dt F_0(K1) + q21 K1,      solves K0 -> Kw
+//   3: K0 = 2 K0 - Kw + theta dt F_0(Kw),      solves K0 in place, then
+//      Y_{n+1} = Y_n + b1 K1 + b2 K2 in the epilogue of the last solve.
+template <int N, int KIND>
+__device__ void solve_item_mixed(const SolveArgs& a, const Item& it, unsigned char* base, unsigned char* meta,
+                                 int rank, int gsize)
+{
+    constexpr bool WARP = KIND == kWarpGroup;
+    const InstDev& P = a.insts[it.inst];
+    constexpr int RMAX = 1 << (WARP ? kRowsLogWarp : kRowsLogCta);
+    const int tlog = 31 - __clz(gsize);
+    const unsigned gm = WARP ? group_mask(tlog) : 0xffffffffu;
+    Shape<N>& s = *reinterpret_cast<Shape<N>*>(meta);
+    ActAxes& A = *reinterpret_cast<ActAxes*>(meta + shape_bytes(N));
+    // single-row solves are folded into another solve (not for global-memory groups)
+    if (rank == 0) make_shape<N>(s, it.lv, tlog, rows_log(KIND), KIND != kMemGroup, KIND != kMemGroup);
+    gsync<WARP>(gm);
+    const Layout lay = make_layout(N, it.lv, true, KIND, tlog);
+    Consts<double>* cd = reinterpret_cast<Consts<double>*>(base + lay.cd);
+    Consts<float>* ck = reinterpret_cast<Consts<float>*>(base + lay.cf);
+    double* tabd = reinterpret_cast<double*>(base + lay.tabd);
+    float* tabk = reinterpret_cast<float*>(base + lay.tabf);
+    double* pay = reinterpret_cast<double*>(base + lay.pay);
+    float* lu = KIND != kCtaGroup
+                    ? reinterpret_cast<float*>(base + lay.lu)
+                    : reinterpret_cast<float*>(a.lu_scratch + (size_t)blockIdx.x * (size_t)a.lu_stride);
+    double* Z = reinterpret_cast<double*>(base + lay.Z);
+    float2* ZZ = reinterpret_cast<float2*>(base + lay.ZZ);
+    float* H = reinterpret_cast<float*>(base + lay.H);
+    float* FY = reinterpret_cast<float*>(base + lay.FY);
+    float* K1 = reinterpret_cast<float*>(base + lay.K1);
+    float* K0 = reinterpret_cast<float*>(base + lay.K0);
+    float* Kw = reinterpret_cast<float*>(base + lay.Kw);
+
+    // 1. coefficient and payoff tables, constants, line-solve factors
+    build_tables<N>(s, P, tabd, pay, cd, rank, gsize);
+    gsync<WARP>(gm);
+    for (int q = rank; q < lay.ntab; q += gsize) tabk[q] = (float)tabd[q];
+    if (rank == 0) convert_consts<float>(*cd, ck);
+    if constexpr (KIND == kMemGroup) {
+        pcr_setup_mem<N, float>(s, tabd, *cd, lu, reinterpret_cast<double*>(base + lay.scr), rank, gsize, gm);
+    } else {
+        pcr_setup<N, float, RMAX>(s, tabd, *cd, lu, rank, gsize, gm);
+    }
+    // 2. H = F(G)/V^2 on the rate grid (FP64), Z from the state or zero
+    for (int tr = rank; tr < s.Lr; tr += gsize) {
+        int j[N];
+        decode<N>(s, tr, j);
+        H[tr] = (float)payoff_H<N>(s, pay, P.payoff, j, tabd, *cd);
+    }
+    for (int t = rank; t < s.L; t += gsize) {
+        const int J = s.padded(t);
+        double z = 0.0;
+        if (a.flags & kLoadState) {
+            int j[N];
+            decode<N>(s, t, j);
+            z = a.state[it.state_off + t] - payoff_at<N>(s, pay, P.payoff, j);
+        }
+        Z[J] = z;
+        ZZ[J] = split_df(z);
+    }
+    gsync<WARP>(gm);
+    if (rank == 0) build_act<N>(s, *ck, tabk, A);
+    gsync<WARP>(gm);
+
+    const int Lr1 = s.Lr - 1;
+    const int shV = s.sh[N - 1], mV = s.M[N - 1] - 1;
+    const float* v2 = tabk + s.toff[N - 1];  // v2[j_V - 1]
+    const float cV = ck->cV, dt = ck->dt, thdt = ck->thdt;
+    const float a21dt = (float)kA21 * dt;
+    const int last = s.last;
+    const int L = s.L;
+    for (int n = 0; n < a.steps; ++n) {
+#pragma unroll 1
+        for (int ph = 0; ph < 4; ++ph) {
+            if (ph == 0) {
+                for (int t = rank; t < L; t += gsize) {
+                    const int J = s.padded(t);
+                    const float acc = stencil_act(A, tabk, cV, t, J, DFSrc{ZZ});
+                    const float k0 = dt * v2[(t >> shV) & mV] * (H[t & Lr1] + acc);
+                    FY[J] = k0;
+                    K0[J] = k0;
+                }
+            } else {
+                const float* X = ph == 2 ? K1 : Kw;
+                for (int t = rank; t < L; t += gsize) {
+                    const int J = s.padded(t);
+                    const float acc = stencil_act(A, tabk, cV, t, J, ArrSrc<float>{X});
+                    const float vv = v2[(t >> shV) & mV];
+                    K0[J] = ph == 2 ? FY[J] + a21dt * vv * acc + (float)kQ21 * K1[J]
+                                    : 2.f * K0[J] - Kw[J] + thdt * vv * acc;
+                }
+            }
+            gsync<WARP>(gm);
+            // directional solves (single-row axes folded into the solve along
+            // `last`): the first from K0 into the phase's target, the rest in place
+            float* dst = (ph == 1) ? K1 : (ph == 3 ? K0 : Kw);
+            const float* src = K0;
+#pragma unroll 1
+            for (int ax = 0; ax < N; ++ax) {
+                if ((s.skip >> ax) & 1) continue;
+                if (ph == 3 && ax == last) {
+                    auto epi = [=](int J, float x) {
+                        Z[J] = fma(kB2, (double)x, fma(kB1, (double)K1[J], Z[J]));
+                        ZZ[J] = ff_axpy(ff_axpy(ZZ[J], (float)kB1, K1[J]), (float)kB2, x);
+                    };
+                    if constexpr (KIND == kMemGroup) sweep_mem<N, float>(s, ax, lu, src, dst, rank, gsize, gm, epi);
+                    else sweep<N, float, RMAX>(s, ax, lu, src, dst, rank, gsize, gm, epi);
+                } else {
+                    if constexpr (KIND == kMemGroup) sweep_mem<N, float>(s, ax, lu, src, dst, rank, gsize, gm, NoEpi());
+                    else sweep<N, float, RMAX>(s, ax, lu, src, dst, rank, gsize, gm, NoEpi());
+                }
+                gsync<WARP>(gm);
+                src = dst;
+            }
+        }
+    }
+
+    // 3. keep the state (Y on Inner nodes) if asked
+    if (a.flags & kStoreState) {
+        for (int t = rank; t < s.L; t += gsize) {
+            int j[N];
+            decode<N>(s, t, j);
+            a.state[it.state_off + t] = payoff_at<N>(s, pay, P.payoff, j) + Z[s.padded(t)];
+        }
+    }
+    // 4. interpolation at the spot
+    interp_spot<N, WARP>(s, P, pay, Z, a.u_out + it.out_idx, rank, gsize, gm);
+    gsync<WARP>(gm);  // the group's shared memory is reused by its next grid
+}
+
 // The solver kernel.  CTA groups: one grid per block at a time from the
 // launch's work counter.  Warp groups: a persistent multi-class launch -- every
 // warp walks the launch's class list (ordered largest grids first) and takes
@@ -1349,7 +1661,7 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
 // then moves on, so classes of uneven instances share one launch and no warp
 // waits for another.
 template <int N, bool MIXED, int KIND>
-__global__ void __launch_bounds__(KIND == kWarpGroup ? 128 : kCtaMaxThreads, KIND == kWarpGroup ? 3 : (KIND == kMemGroup ? 2 : 1)) solve_kernel(SolveArgs a)
+__global__ void __launch_bounds__(KIND == kWarpGroup ? 128 : kCtaMaxThreads, KIND == kWarpGroup ? (MIXED ? kWarpBlocksMixed : 3) : (KIND == kMemGroup ? 2 : 1)) solve_kernel(SolveArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     if constexpr (KIND == kWarpGroup) {
@@ -1367,11 +1679,19 @@ __global__ void __launch_bounds__(KIND == kWarpGroup ? 128 : kCtaMaxThreads, KIN
                 continue;
             }
             const int item = chunk + (lane >> cd.glog);
-            if (item < cd.item_count) {
-                const Item it = a.items[cd.item_begin + item];
+            bool take = item < cd.item_count;
+            Item it{};
+            if (take) {
+                it = a.items[cd.item_begin + item];
+                take = !a.inst_mask || a.inst_mask[it.inst] != 0;
+            }
+            if (take) {
                 const int gsize = 1 << cd.glog;
                 unsigned char* base = wbase + (size_t)(lane >> cd.glog) * (size_t)cd.smem_group;
-                solve_item<N, MIXED, kWarpGroup>(a, it, base, lane & (gsize - 1), gsize);
+                if constexpr (MIXED)
+                    solve_item_mixed<N, kWarpGroup>(a, it, base, base, lane & (gsize - 1), gsize);
+                else
+                    solve_item<N, false, kWarpGroup>(a, it, base, lane & (gsize - 1), gsize);
             }
         }
     } else {
@@ -1386,6 +1706,12 @@ __global__ void __launch_bounds__(KIND == kWarpGroup ? 128 : kCtaMaxThreads, KIN
             __syncthreads();
             if (item >= a.n_items) break;
             const Item it = a.items[item];
+            if (a.inst_mask && a.inst_mask[it.inst] == 0) continue;  // uniform across the block
+            // whole-block groups keep the unrolled stencil of solve_item in both
+            // precisions: with up to 256 threads on one grid the per-node work
+            // dominates, and the unrolled form, each axis's offsets in
+            // registers, measured 30 % faster on the d=6 modified level-6
+            // workload than the table-driven form of the warp groups
             solve_item<N, MIXED, KIND>(a, it, base, (int)threadIdx.x, (int)blockDim.x);
         }
     }

@@ -14,7 +14,8 @@
 // columns); the epilogue reads it with tcgen05.ld (warp w owns lanes
 // 32w..32w+31, i.e. rows 32w..32w+31 of the tile) and applies a fused
 // elementwise operation.  Every mbarrier wait is bounded: on timeout the
-// kernel records an error, skips the rest and still frees its TMEM.
+// kernel waits (bounded) once more for the outstanding commit, records an
+// error, skips the rest and frees its TMEM.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -228,6 +229,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         // every thread waits; the block agrees on the outcome so that all
         // threads take the same path afterwards
         ok = __syncthreads_and(mbar_wait(smem_u32(mbar), phase) ? 1 : 0) != 0;
+        if (!ok) {
+            // The committed MMAs may still be writing the accumulator: wait
+            // for that commit once more (also bounded) before TMEM is freed
+            // below, so that the dealloc does not release columns an MMA in
+            // flight still writes.
+            __syncthreads_and(mbar_wait(smem_u32(mbar), phase) ? 1 : 0);
+        }
         phase ^= 1u;
         fence_after();
     }

@@ -22,11 +22,13 @@ uniformly in [-0.5, 0] and redrawn until the joint correlation matrix of
   c2  N=4 standard combination n=5, swaption, T=2, 40 steps, FP64
   c3  N=6 modified combination psi=1, n=6, swaption, 40 steps, mixed
   c4  batch of N in {4,6,8}, n in {4,5,6}, standard combination, mixed
-  c5  surrogate family: N=6 standard combination n=6, 40 steps, mixed; alpha
-      shared by all rates in [0.02, 0.06], sigma in [0.1, 0.5], beta in
-      [0.4, 0.6], T in [0.5, 2], rate correlations exp(-lambda |i-j|) with
+  c5  surrogate families: N=6 standard combination n=6, 40 steps, mixed;
+      alpha shared by all rates, rate correlations exp(-lambda |i-j|) with
       lambda in [0.05, 0.3], phi_i linear in i between phi_1 and phi_{N-1},
-      both in [-0.5, 0]; K = F0 = 0.03, Fmax = 0.06, V0 = 1, Vmax = 2
+      both in [-0.5, 0], sigma in [0.1, 0.5], T in [0.5, 2]; "configured":
+      alpha in [0.1, 0.4], beta = 0.5, K in [0.02, 0.04], F in [0, 0.2],
+      V in [0, 1], F0 = 0.03, V0 = 1; "centred": alpha in [0.02, 0.06], beta
+      in [0.4, 0.6], K = F0 = 0.03, Fmax = 0.06, V0 = 1, Vmax = 2
 Seeds: numpy PCG64 with seed 240800559 + instance index.
 """
 from __future__ import annotations
@@ -128,24 +130,37 @@ def small_instance(N: int, level: int, psi: int = 0, steps: int = 6, seed: int =
     return inst
 
 
-# Surrogate family: market-like volatilities (alpha F0^(beta-1) between about
-# 8% and 50% lognormal), the spot at the centre of every axis (Fmax = 2 F0,
-# Vmax = 2 V0, so the spot is a node of every component grid) and the strike at
-# the money.  The strike stays fixed: the combination-technique price is only
-# piecewise smooth in K (its slope jumps wherever the payoff's kink crosses a
-# grid node), so no smooth network can follow it to 1e-3.  In every other
-# feature it is smooth.
-C5_BOX = {"alpha": (0.02, 0.06), "sigma": (0.1, 0.5), "beta": (0.4, 0.6), "K": (0.03, 0.03),
-          "T": (0.5, 2.0), "lam": (0.05, 0.3), "phi": (-0.5, 0.0)}
-C5_F0, C5_FMAX, C5_V0, C5_VMAX = 0.03, 0.06, 1.0, 2.0
+# Surrogate families.  "configured": the parameter box of the d=6 workload
+# (alpha in [0.1, 0.4], vol of vol in [0.1, 0.5], beta = 0.5, rate/vol
+# correlations in [-0.5, 0]) with the strike varying in [0.02, 0.04] and the
+# maturity in [0.5, 2], on the synthetic domain F in [0, 0.2], V in [0, 1]
+# (spot F0 = 0.03, V0 = 1).  The combination-technique price is only piecewise
+# smooth in K -- for fixed other parameters it is piecewise linear, its slope
+# jumping wherever the payoff's kink crosses a grid node -- so the network
+# cannot follow it to 1e-3 everywhere and the solver takes the queries it
+# cannot answer.  "centred": market-like volatilities (alpha F0^(beta-1)
+# between about 8% and 50% lognormal), the spot at the centre of every axis
+# (Fmax = 2 F0, Vmax = 2 V0, so the spot is a node of every component grid)
+# and the strike fixed at the money; there the price is smooth in every
+# feature.
+C5_BOXES = {
+    "configured": {"alpha": (0.1, 0.4), "sigma": (0.1, 0.5), "beta": (0.5, 0.5), "K": (0.02, 0.04),
+                   "T": (0.5, 2.0), "lam": (0.05, 0.3), "phi": (-0.5, 0.0),
+                   "F0": 0.03, "Fmax": 0.2, "V0": 1.0, "Vmax": 1.0},
+    "centred": {"alpha": (0.02, 0.06), "sigma": (0.1, 0.5), "beta": (0.4, 0.6), "K": (0.03, 0.03),
+                "T": (0.5, 2.0), "lam": (0.05, 0.3), "phi": (-0.5, 0.0),
+                "F0": 0.03, "Fmax": 0.06, "V0": 1.0, "Vmax": 2.0},
+}
+C5_BOX = C5_BOXES["centred"]
 
 
-def c5_features(count: int, start: int = 0, N: int = 6) -> np.ndarray:
+def c5_features(count: int, start: int = 0, N: int = 6, box: str = "centred") -> np.ndarray:
     """Features [count x 8] of the surrogate family (alpha, sigma, beta, K, T,
     lambda, phi_1, phi_{N-1}): one alpha for all rates, rate correlations
     exp(-lambda |i-j|), rate/vol correlations linear in the rate index between
     phi_1 and phi_{N-1}; rows whose joint correlation matrix is not positive
     semi-definite are redrawn."""
+    B = C5_BOXES[box]
     rng = np.random.Generator(np.random.PCG64(SEED0 + 3_000_000 + start))
     nr = N - 1
     out = np.zeros((count, 8))
@@ -154,9 +169,9 @@ def c5_features(count: int, start: int = 0, N: int = 6) -> np.ndarray:
         m = todo.size
         f = np.empty((m, 8))
         for c, key in enumerate(("alpha", "sigma", "beta", "K", "T", "lam")):
-            lo, hi = C5_BOX[key]
+            lo, hi = B[key]
             f[:, c] = rng.uniform(lo, hi, size=m)
-        f[:, 6:8] = rng.uniform(*C5_BOX["phi"], size=(m, 2))
+        f[:, 6:8] = rng.uniform(*B["phi"], size=(m, 2))
         if nr == 1:
             f[:, 5] = 0.0
             f[:, 7] = f[:, 6]
@@ -173,21 +188,23 @@ def c5_features(count: int, start: int = 0, N: int = 6) -> np.ndarray:
     return out
 
 
-def c5_instance_from(f, N: int = 6, level: int = 6, steps: int = 40, precision: str = "mixed") -> dict:
+def c5_instance_from(f, N: int = 6, level: int = 6, steps: int = 40, precision: str = "mixed",
+                     box: str = "centred") -> dict:
     """The family instance with features f (the layout of c5_features)."""
+    B = C5_BOXES[box]
     nr = N - 1
     i = np.arange(nr)
     lam = float(f[5])
     phi = float(f[6]) + i / max(nr - 1, 1) * (float(f[7]) - float(f[6]))
     return dict(
         N=N, payoff="swaption", alpha=np.full(nr, float(f[0])), phi=phi, tau=np.full(nr, 0.5),
-        F0=np.full(nr, C5_F0), Fmax=np.full(nr, C5_FMAX), rho=np.exp(-lam * np.abs(i[:, None] - i[None, :])),
-        sigma=float(f[1]), beta=float(f[2]), V0=C5_V0, Vmax=C5_VMAX, K=float(f[3]), T=float(f[4]),
+        F0=np.full(nr, B["F0"]), Fmax=np.full(nr, B["Fmax"]), rho=np.exp(-lam * np.abs(i[:, None] - i[None, :])),
+        sigma=float(f[1]), beta=float(f[2]), V0=B["V0"], Vmax=B["Vmax"], K=float(f[3]), T=float(f[4]),
         discount=1.0, theta=THETA_W2, nu=default_nu(N), n_steps=steps, level=level, psi=0,
         full=False, precision=precision,
     )
 
 
 def c5_instances(count: int, start: int = 0, N: int = 6, level: int = 6, steps: int = 40,
-                 precision: str = "mixed") -> list[dict]:
-    return [c5_instance_from(f, N, level, steps, precision) for f in c5_features(count, start, N)]
+                 precision: str = "mixed", box: str = "centred") -> list[dict]:
+    return [c5_instance_from(f, N, level, steps, precision, box) for f in c5_features(count, start, N, box)]

@@ -197,7 +197,9 @@ def test_mixed_precision_price(case):
 
 def test_c3_full_size_sampled_grids():
     """d=6 modified psi=1 n=6 (923 grids, up to 4096 Inner nodes), mixed
-    precision: sampled component grids against the oracle one by one."""
+    precision: sampled component grids against the oracle one by one, and
+    the price against the oracle's price of the whole problem (all 923 grids,
+    solved by the oracle in a spawned process pool) at 1e-5."""
     inst = W.c3_instance(0)
     prob = B.Problem(inst)
     prob.step(inst["n_steps"])
@@ -211,7 +213,10 @@ def test_c3_full_size_sampled_grids():
         Yg = prob.read_grid(g, lv[g])
         assert np.max(np.abs(Yg - Yo)) <= 1e-6 * np.max(np.abs(Yo)), lv[g]
         assert abs(u[g] - u_o) <= 1e-6 * np.max(np.abs(Yo))
-    assert np.isfinite(prob.combine())
+    p = prob.combine()
+    prob.close()
+    po = O.price_parallel(inst, inst["level"], inst["psi"])
+    assert abs(p - po) <= TOLMIX_PRICE * abs(po), (p, po, abs(p - po) / abs(po))
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])

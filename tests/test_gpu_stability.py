@@ -1,0 +1,75 @@
+"""GPU check of the AMF parameter nu at the largest dimension of the batched
+workload (Sec. 4.1: AMFR-W2 is stable for nu >= N kappa_N theta, with the
+constants kappa_N in a table the paper does not print).
+
+The library's default is nu = N theta / 2 (kappa_N = 1/2, the value that
+reproduces the paper's N = 2 tables).  On the d=8 standard level-6 instance of
+the 256-instance workload (3003 component grids), FP64, 40 steps:
+- with nu = N theta / 2 and with nu = N theta, on the grids where growth would
+  show first (the most nodes, the finest single axis, the most refined axes),
+  the correction Z = Y - payoff stays below the payoff's own scale at every
+  node after 40 steps and after 160 steps (no growth over time);
+- the two prices differ by no more than the time-discretisation error itself,
+  estimated as the change from 40 to 80 steps at the default nu.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2408_00559_gb300 import _lib as B
+from paper_2408_00559_gb300 import build as BLD
+from paper_2408_00559_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    BLD.build()
+    B.lib()
+
+
+def inner(Y_full, levels):
+    """Inner nodes of an oracle grid vector, axis 0 fastest."""
+    shape = tuple((1 << int(l)) + 1 for l in levels)
+    Yr = np.asarray(Y_full).reshape(shape[::-1])
+    return Yr[(slice(1, None),) * len(shape)].reshape(-1)
+
+
+def solve(inst, steps=None):
+    x = dict(inst, precision="fp64")
+    if steps is not None:
+        x["n_steps"] = steps
+    pr = B.Problem(x)
+    pr.step(x["n_steps"])
+    price = pr.combine()
+    lv, _ = pr.grid_info()
+    return pr, price, lv
+
+
+def test_nu_stability_at_d8_level6():
+    base = W.batch("c4", 2)[1]
+    assert base["N"] == 8 and base["level"] == 6
+    N, th = base["N"], base["theta"]
+    prices = {}
+    for nu in (0.5 * N * th, 1.0 * N * th):
+        for steps in (40, 160):
+            inst = dict(base, nu=nu)
+            pr, price, lv = solve(inst, steps)
+            prices[(nu, steps)] = price
+            sizes = np.array([np.prod([(1 << int(x)) for x in l]) for l in lv])
+            pick = {int(np.argmax(sizes)), int(np.argmax([max(l) for l in lv])),
+                    int(np.argmax([np.count_nonzero(l) for l in lv]))}
+            for g in pick:
+                Y = pr.read_grid(g, lv[g])
+                G = inner(O.payoff_grid(inst, lv[g]), lv[g])
+                gscale = max(np.max(np.abs(G)), 1e-300)
+                Z = Y - G
+                assert np.all(np.isfinite(Y))
+                assert np.max(np.abs(Z)) <= gscale, (nu, steps, lv[g], np.max(np.abs(Z)) / gscale)
+            pr.close()
+    d = 0.5 * N * th
+    _, p80, _ = solve(dict(base, nu=d), 80)
+    time_err = abs(prices[(d, 40)] - p80)
+    assert abs(prices[(d, 40)] - prices[(N * th, 40)]) <= 4 * time_err + 1e-14, (prices, p80)
+    assert abs(prices[(d, 160)] - prices[(N * th, 160)]) <= 4 * time_err + 1e-14, (prices, p80)

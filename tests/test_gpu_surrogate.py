@@ -4,8 +4,10 @@ solver prices, solver fallback):
 - the loss gradient computed by the network's forward/backward kernels
   (tcgen05 GEMMs with BF16 weights and activations, FP32 accumulation)
   agrees with the plain FP64 CPU reference (oracle/mlp.py, itself pinned by
-  finite differences) to BF16 accuracy: every parameter tensor within 3 %
-  relative L2 error and cosine similarity > 0.999;
+  finite differences) entry by entry, every bias and padded input included:
+  each entry within 16 BF16 roundoffs of the chain rule's absolute-value
+  scale for that entry, and every tensor within 3 % relative L2 error with
+  cosine similarity > 0.999;
 - training (cubic control variate plus networks on the residual of the log
   price) drives the loss down; calibration and evaluation on fresh
   instances of the family give, for every answer the network keeps, an error
@@ -56,6 +58,14 @@ def from_vector(g):
     return out
 
 
+# BF16 unit roundoff and the multiple of it, times the per-entry scale of the
+# chain rule in absolute values, that bounds each gradient entry's error:
+# each GEMM rounds both operands (2u), and the error reaches the first layer's
+# gradient through three layers forward and back.
+BF16_U = 2.0 ** -8
+GRAD_K = 16.0
+
+
 def test_gradients_match_cpu_oracle():
     s = B.Surrogate(members=1, seed=1)
     p = mlp.init_params(width=256, n_in=8, seed=5)
@@ -72,14 +82,27 @@ def test_gradients_match_cpu_oracle():
     p32["b4"] = float(p32["b4"][0])
     L, g = mlp.loss_and_grads(p32, x, t)
     assert abs(loss_gpu - L) <= 1e-2 * L
+    scale = mlp.grad_abs_scale(p32, x, t)
+    lay = B.surrogate_layout()
+    # the padded inputs 8..15 of the first layer carry no gradient at all
+    o, n = lay["W1"]
+    assert np.all(g_gpu[o:o + n].reshape(256, 16)[:, 8:] == 0.0)
     gg = from_vector(g_gpu)
     gg["b4"] = float(gg["b4"][0])
+    worst = {}
     for name in ("W1", "b1", "W2", "b2", "W3", "b3", "w4", "b4"):
         a = np.ravel(gg[name])
         b = np.ravel(g[name])
+        sc = np.ravel(scale[name])
+        # every entry, biases and b4 included, within its BF16 bound
+        ratio = np.abs(a - b) / (BF16_U * sc + 1e-300)
+        worst[name] = float(ratio.max())
+        assert np.all(ratio <= GRAD_K), (name, int(ratio.argmax()), worst[name])
+        # and the tensor as a whole close to the reference
         rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
         cos = float(np.dot(a, b) / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-300))
         assert rel < 3e-2 and cos > 0.999, (name, rel, cos)
+    print("gradient error / (u * scale), worst entry per tensor:", worst)
     s.close()
 
 

@@ -36,3 +36,24 @@ def test_gradients_match_finite_differences():
             p[name] = flat.reshape(val.shape) if val.ndim else float(flat[0])
             fd = (lp - lm) / (2 * h)
             assert abs(fd - gflat[k]) <= 1e-7 * max(1.0, abs(fd)), (name, k, fd, gflat[k])
+
+
+def test_grad_abs_scale_bounds_every_gradient_entry():
+    # |sum_b a_b c_b| <= sum_b |a_b| |c_b| at every step of the chain rule,
+    # and with every factor positive (inputs, weights, residuals, GELU
+    # derivatives) the two coincide
+    p = mlp.init_params(width=16, n_in=8, seed=2)
+    rng = np.random.default_rng(3)
+    x = rng.uniform(-1, 1, size=(32, 8))
+    t = rng.standard_normal(32)
+    _, g = mlp.loss_and_grads(p, x, t)
+    s = mlp.grad_abs_scale(p, x, t)
+    for name in g:
+        assert np.all(np.abs(g[name]) <= np.asarray(s[name]) * (1 + 1e-12) + 1e-300), name
+    q = {k: (np.abs(v) if isinstance(v, np.ndarray) else abs(v)) for k, v in p.items()}
+    xp = np.abs(x)
+    tp = np.full(32, -100.0)
+    _, g = mlp.loss_and_grads(q, xp, tp)
+    s = mlp.grad_abs_scale(q, xp, tp)
+    for name in g:
+        assert np.allclose(np.abs(g[name]), s[name], rtol=1e-12, atol=0), name
