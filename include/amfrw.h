@@ -90,15 +90,24 @@ enum amfrw_precision {
  *   psi       0: standard combination; >= 1: modified combination.
  *   full_grid nonzero: one full grid with `level` on every axis.
  *   precision AMFRW_FP64 or AMFRW_MIXED.
- *   flags     0, or AMFRW_FLAG_GLOBAL_GRIDS: solve every component grid with
- *             its state in global memory, the path that grids too large for
- *             shared memory (or with lines of more than 256 rows) always
- *             take; the result is the same to rounding.  Other bits: EINVAL.
+ *   flags     bitwise or of
+ *             AMFRW_FLAG_GLOBAL_GRIDS: solve every component grid with its
+ *               state in global memory, the path that grids too large for
+ *               shared memory (or with lines of more than 256 rows) always
+ *               take; the result is the same to rounding;
+ *             AMFRW_FLAG_DIRICHLET: the earlier boundary conditions of eq.
+ *               bound1_0 instead of the Neumann faces of eq. bound1 on the
+ *               rate axes: u = payoff on the upper face F_i = F_i^max of every
+ *               rate (the lower faces and V = 0 keep their Dirichlet data,
+ *               V = V^max its Neumann condition); a rate line then has
+ *               M_i - 1 Inner nodes;
+ *             other bits: EINVAL.
  *   theta     W-method parameter; AMFR-W2 has order 3 for (3+sqrt(3))/6.
  *   nu_amf    AMF parameter nu > 0 of eq. (Wmat1) (the paper's nu; named so
  *             apart from the volatility of volatility).
  */
 #define AMFRW_FLAG_GLOBAL_GRIDS 1
+#define AMFRW_FLAG_DIRICHLET 2
 
 typedef struct amfrw_params {
     int32_t n_rates;
@@ -263,7 +272,10 @@ int amfrw_tc_gemm_bf16(const void *dA, int32_t lda, const void *dB, int32_t ldb,
  *     rho_ik = exp(-lambda |i - k|); rate/vol correlations phi_i linear in the
  *     rate index between phi_1 and phi_{N-1}.
  * The features (alpha, sigma, beta, K, T, lambda, phi_1, phi_{N-1}), in this
- * order, then determine the instance (lambda = 0 when N = 2).  The ensemble
+ * order, then determine the instance (lambda = 0 when N = 2).  A feature that
+ * takes between 2 and 32 distinct values in the training set (for instance
+ * strikes on a lattice) is a lattice feature: queries off its training values
+ * are outside the box and fall back.  The ensemble
  * spread times a calibration factor estimates the error; eval answers from
  * the network where that estimate is within rel_bound * |price| and falls
  * back to the batched solver (amfrw_solve_batch) for every other query,
@@ -292,8 +304,8 @@ int amfrw_tc_gemm_bf16(const void *dA, int32_t lda, const void *dB, int32_t ldb,
  *              (row-major, the order above) of the family's instances; a
  *              fallback query is solved as the family instance with those
  *              features (EINVAL if that instance is not valid).
- *   save/load  plain binary file (magic AMFRWSG2, scaling, family, FP32
- *              weights).
+ *   save/load  plain binary file (magic AMFRWSG3, scaling, family,
+ *              lattices, FP32 weights).
  *   params     FP32 parameters of one member (136193 floats: W1 [256 x 16]
  *              (inputs 8..15 are padding), b1 [256], W2 [256 x 256], b2, W3,
  *              b3, w4 [256], b4), read to params_out and/or set from

@@ -20,6 +20,7 @@ STATUS = {0: "AMFRW_OK", 1: "AMFRW_EINVAL", 2: "AMFRW_ENOTPSD", 3: "AMFRW_ENOMEM
 PAYOFF = {"caplet": 0, "swaption": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
 FLAG_GLOBAL_GRIDS = 1
+FLAG_DIRICHLET = 2
 
 # every symbol include/amfrw.h declares
 EXPORTS = [
@@ -157,7 +158,8 @@ class _Marshal:
         p.psi = int(inst.get("psi", 0))
         p.full_grid = int(bool(inst.get("full", False)))
         p.precision = PRECISION[inst.get("precision", "fp64")]
-        p.flags = FLAG_GLOBAL_GRIDS if inst.get("global_grids", False) else 0
+        p.flags = ((FLAG_GLOBAL_GRIDS if inst.get("global_grids", False) else 0) |
+                   (FLAG_DIRICHLET if inst.get("bc", "neumann") == "dirichlet" else 0))
         for name in ("alpha", "phi", "tau", "F0", "Fmax"):
             setattr(p, name, _dp(self._vec(inst[name])))
         p.rho = _dp(self._vec(inst["rho"]))

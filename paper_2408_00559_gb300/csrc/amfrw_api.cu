@@ -109,7 +109,7 @@ int validate(const amfrw_params* p)
     if (p->precision != AMFRW_FP64 && p->precision != AMFRW_MIXED)
         return fail(AMFRW_EINVAL, "unknown precision");
     if (p->n_steps < 1) return fail(AMFRW_EINVAL, "n_steps must be >= 1");
-    if (p->flags & ~AMFRW_FLAG_GLOBAL_GRIDS) return fail(AMFRW_EINVAL, "unknown flag bits");
+    if (p->flags & ~(AMFRW_FLAG_GLOBAL_GRIDS | AMFRW_FLAG_DIRICHLET)) return fail(AMFRW_EINVAL, "unknown flag bits");
     if (p->level < 0 || p->psi < 0) return fail(AMFRW_EINVAL, "level and psi must be >= 0");
     const double sc[] = {p->sigma, p->beta, p->V0, p->Vmax, p->K, p->T, p->discount, p->theta, p->nu_amf};
     for (double v : sc)
@@ -195,6 +195,7 @@ InstDev to_device(const amfrw_params* p)
     I.payoff = p->payoff;
     I.n_steps = p->n_steps;
     I.precision = p->precision;
+    I.bc = (p->flags & AMFRW_FLAG_DIRICHLET) ? 1 : 0;
     for (int i = 0; i < nr; ++i) {
         I.alpha[i] = p->alpha[i];
         I.phi[i] = p->phi[i];

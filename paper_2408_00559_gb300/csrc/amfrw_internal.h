@@ -16,7 +16,9 @@ constexpr int kCtaMaxThreads = 256;  // CTA work groups (grids of more than 64 I
 // Per-instance parameters on the device (one per pricing problem).
 struct InstDev {
     int32_t N, payoff, n_steps, precision;
-    int32_t grid_begin, grid_count, pad0, pad1;
+    int32_t grid_begin, grid_count;
+    int32_t bc;          // 0: Neumann upper faces (Sketch 1); 1: Dirichlet rate faces (eq. bound1_0)
+    int32_t pad1;
     double alpha[kMaxDim], phi[kMaxDim], tau[kMaxDim], F0[kMaxDim];
     double Fmax[kMaxDim];          // Fmax[N-1] = V^max
     double rho[kMaxDim * kMaxDim];  // rate correlations, leading dimension 8
@@ -68,6 +70,7 @@ struct ActAxes {
     int nr;                     // active rate axes (the first nr of them; V, if active, is last)
     int sh[kMaxDim];            // bit offset of j - 1 in the node index t
     int msk[kMaxDim];           // M - 1
+    int nfm[kMaxDim];           // j - 1 of the Neumann face, or -2 (Dirichlet data on the upper face)
     int Sp[kMaxDim];            // padded stride
     int toff[kMaxDim];          // rate axes: offset of their coefficient tables (d, pw, drift)
     int M[kMaxDim];             // rows
@@ -81,11 +84,11 @@ struct ActAxes {
 };
 
 // Per-grid descriptors the mixed-precision solver keeps in shared memory:
-// the grid's shape (9 per-axis arrays and 6 scalars of int) and its active
+// the grid's shape (10 per-axis arrays and 7 scalars of int) and its active
 // axes.  Warp groups hold them in their layout; whole-block groups in a
 // static shared array of the kernel.
 AMFRW_HD constexpr int32_t align16(int32_t x) { return (x + 15) & ~15; }
-AMFRW_HD constexpr int shape_bytes(int N) { return align16(4 * (9 * N + 6)); }
+AMFRW_HD constexpr int shape_bytes(int N) { return align16(4 * (10 * N + 7)); }
 AMFRW_HD constexpr int meta_bytes(int N) { return shape_bytes(N) + align16((int)sizeof(ActAxes)); }
 constexpr int kMetaBytesMax = meta_bytes(kMaxDim);
 

@@ -89,6 +89,7 @@ namespace amfrw {
 namespace sg {
 
 constexpr int kIn = 8;        // features
+constexpr int kMaxLattice = 32;  // most distinct training values of a feature treated as a lattice
 constexpr int kInPad = 16;    // first-layer K padded to the MMA's K
 constexpr int kW = 256;       // hidden width
 constexpr int kTrainRows = 1024;
@@ -440,6 +441,10 @@ struct amfrw_surrogate {
     double poly[kPolyTerms] = {};
     int adam_t = 0;
     double fmin[kIn], fmax[kIn];
+    // features that took at most kMaxLattice distinct values in the training
+    // set (a lattice, e.g. strikes): queries must lie on one of them
+    int nlat[kIn] = {};
+    double lat[kIn][kMaxLattice] = {};
     double ymu = 0.0, ysd = 1.0;    // target scaling: t = (g(price) - ymu) / ysd
     bool log_target = false;        // g = log (all training prices > 0), else identity
     double calib = 0.0, rel_bound = 1e-3;
@@ -641,6 +646,12 @@ void sg_normalise(const amfrw_surrogate* s, const double* raw, int64_t n, std::v
             const double span = s->fmax[c] - s->fmin[c];
             const double z = span > 0 ? 2.0 * (f - s->fmin[c]) / span - 1.0 : (f == s->fmin[c] ? 0.0 : 2.0);
             if (ok && !(z >= -1.0 - 1e-9 && z <= 1.0 + 1e-9)) ok[i] = 0;
+            if (ok && s->nlat[c] > 0) {  // a lattice feature: only its training values
+                bool on = false;
+                for (int q = 0; q < s->nlat[c] && !on; ++q)
+                    on = std::fabs(f - s->lat[c][q]) <= 1e-12 * std::max(1.0, std::fabs(f));
+                if (!on) ok[i] = 0;
+            }
             out[(size_t)i * kIn + c] = (float)z;
         }
     }
@@ -829,6 +840,23 @@ int amfrw_surrogate_fit(amfrw_surrogate* s, const amfrw_params* ps, const double
         for (int c = 0; c < kIn; ++c) {
             s->fmin[c] = std::min(s->fmin[c], raw[(size_t)i * kIn + c]);
             s->fmax[c] = std::max(s->fmax[c], raw[(size_t)i * kIn + c]);
+        }
+    }
+    // features with at most kMaxLattice distinct training values (and more
+    // than one) are lattices: the network is trained, and answers, only there
+    for (int c = 0; c < kIn; ++c) {
+        std::vector<double> v;
+        s->nlat[c] = 0;
+        for (int64_t i = 0; i < n && (int)v.size() <= kMaxLattice; ++i) {
+            const double x = raw[(size_t)i * kIn + c];
+            bool seen = false;
+            for (double y : v) seen = seen || std::fabs(x - y) <= 1e-12 * std::max(1.0, std::fabs(x));
+            if (!seen) v.push_back(x);
+        }
+        if (v.size() >= 2 && (int)v.size() <= kMaxLattice) {
+            std::sort(v.begin(), v.end());
+            s->nlat[c] = (int)v.size();
+            for (size_t q = 0; q < v.size(); ++q) s->lat[c][q] = v[q];
         }
     }
     // the network learns log(price) when every price is positive (its squared
@@ -1048,7 +1076,7 @@ int amfrw_surrogate_save(const amfrw_surrogate* s, const char* path)
     if (!s || !path) return sg_fail(AMFRW_EINVAL, "NULL argument");
     FILE* f = fopen(path, "wb");
     if (!f) return sg_fail(AMFRW_EINVAL, std::string("cannot open ") + path);
-    const char magic[8] = {'A', 'M', 'F', 'R', 'W', 'S', 'G', '2'};
+    const char magic[8] = {'A', 'M', 'F', 'R', 'W', 'S', 'G', '3'};
     std::vector<float> h(kParams);
     bool ok = fwrite(magic, 1, 8, f) == 8;
     ok = ok && fwrite(&s->members, sizeof(int), 1, f) == 1;
@@ -1060,6 +1088,8 @@ int amfrw_surrogate_save(const amfrw_surrogate* s, const char* path)
     ok = ok && fwrite(flags, sizeof(int), 3, f) == 3;
     ok = ok && fwrite(&s->fam, sizeof(Family), 1, f) == 1;
     ok = ok && fwrite(s->poly, sizeof(double), kPolyTerms, f) == (size_t)kPolyTerms;
+    ok = ok && fwrite(s->nlat, sizeof(int), kIn, f) == (size_t)kIn;
+    ok = ok && fwrite(s->lat, sizeof(double), kIn * kMaxLattice, f) == (size_t)(kIn * kMaxLattice);
     for (int m = 0; m < s->members && ok; ++m) {
         ok = cudaMemcpy(h.data(), s->P[m], sizeof(float) * kParams, cudaMemcpyDeviceToHost) == cudaSuccess;
         ok = ok && fwrite(h.data(), sizeof(float), kParams, f) == (size_t)kParams;
@@ -1076,7 +1106,7 @@ int amfrw_surrogate_load(const char* path, void* cuda_stream, amfrw_surrogate** 
     if (!f) return sg_fail(AMFRW_EINVAL, std::string("cannot open ") + path);
     char magic[8];
     int members = 0;
-    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "AMFRWSG2", 8) == 0;
+    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "AMFRWSG3", 8) == 0;
     ok = ok && fread(&members, sizeof(int), 1, f) == 1 && members >= 1 && members <= 16;
     amfrw_surrogate* s = nullptr;
     if (ok && amfrw_surrogate_create(members, 0, cuda_stream, &s) != AMFRW_OK) ok = false;
@@ -1087,6 +1117,9 @@ int amfrw_surrogate_load(const char* path, void* cuda_stream, amfrw_surrogate** 
         ok = ok && fread(sc, sizeof(double), 4, f) == 4 && fread(flags, sizeof(int), 3, f) == 3;
         ok = ok && fread(&s->fam, sizeof(Family), 1, f) == 1;
         ok = ok && fread(s->poly, sizeof(double), kPolyTerms, f) == (size_t)kPolyTerms;
+        ok = ok && fread(s->nlat, sizeof(int), kIn, f) == (size_t)kIn;
+        ok = ok && fread(s->lat, sizeof(double), kIn * kMaxLattice, f) == (size_t)(kIn * kMaxLattice);
+        for (int c = 0; c < kIn && ok; ++c) ok = s->nlat[c] >= 0 && s->nlat[c] <= kMaxLattice;
         ok = ok && cudaMemcpy(s->dpoly, s->poly, sizeof(double) * kPolyTerms, cudaMemcpyHostToDevice) == cudaSuccess;
     }
     std::vector<float> h(kParams);

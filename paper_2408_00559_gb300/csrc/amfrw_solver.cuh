@@ -54,6 +54,9 @@ constexpr double kB2 = 3.0 / 4.0;
 template <int N>
 struct Shape {
     int lv[N], M[N], sh[N], Sp[N];
+    int nf[N];     // j of the Neumann face of the axis (Sketch 1), or -1 where eq. bound1_0
+                   // puts Dirichlet data on the upper face (rate axes)
+    int dmask;     // rate axes with Dirichlet data on their upper face
     int toff[N];   // coefficient tables: rate axis a -> [dI | pw | ph] of M_a each; V -> v2
     int poff[N];   // payoff tables: rate axis a -> M_a + 1 entries (Outer node included)
     int luoff[N];  // line-solve factors: rate axis -> M_V classes x M_a rows; V -> M_V rows
@@ -67,7 +70,7 @@ struct Shape {
 
 template <int N>
 __device__ __forceinline__ void make_shape(Shape<N>& s, const int8_t* lv, int tlog, int rlog, bool fold,
-                                           bool fold_v)
+                                           bool fold_v, bool dirichlet)
 {
     int sh = 0;
 #pragma unroll
@@ -75,8 +78,10 @@ __device__ __forceinline__ void make_shape(Shape<N>& s, const int8_t* lv, int tl
         s.lv[i] = lv[i];
         s.M[i] = 1 << lv[i];
         s.sh[i] = sh;
+        s.nf[i] = (dirichlet && i < N - 1) ? -1 : s.M[i];
         sh += lv[i];
     }
+    s.dmask = dirichlet ? (1 << (N - 1)) - 1 : 0;
     s.L = 1 << sh;
     s.Lr = s.L >> s.lv[N - 1];
     s.pad = s.M[0] > 1 ? 1 : 0;
@@ -117,6 +122,20 @@ __device__ __forceinline__ void make_shape(Shape<N>& s, const int8_t* lv, int tl
         s.skip |= 1 << (N - 1);
         s.last = lastr;
     }
+}
+
+// Under eq. bound1_0 the nodes on the upper face of a rate axis hold
+// Dirichlet data: they are stored (Z = 0 there, as on the lower faces) but
+// are not Inner nodes, so every increment is 0 on them.
+template <int N>
+__device__ __forceinline__ bool dirichlet_node(const Shape<N>& s, int t)
+{
+    bool out = false;
+    if (s.dmask) {
+#pragma unroll
+        for (int i = 0; i < N - 1; ++i) out |= ((t >> s.sh[i]) & (s.M[i] - 1)) == s.M[i] - 1;
+    }
+    return out;
 }
 
 template <int N>
@@ -198,7 +217,7 @@ __device__ __forceinline__ TC stencil_acc(const Shape<N>& s, const int (&j)[N], 
 #pragma unroll
     for (int i = 0; i < N; ++i) {
         const bool has_lo = j[i] > 1;
-        const bool top = j[i] == s.M[i];
+        const bool top = j[i] == s.nf[i];
         const V m = src.nb(J, -s.Sp[i], has_lo, i, -1, -1, 0);
         const V p = top ? m : src.nb(J, s.Sp[i], true, i, 1, -1, 0);
         const TC dp = Src::diff(p, x0);
@@ -211,13 +230,13 @@ __device__ __forceinline__ TC stencil_acc(const Shape<N>& s, const int (&j)[N], 
     for (int i = 0; i < N - 1; ++i) acc += tab[s.toff[i] + j[i] - 1] * lap[i];
 #pragma unroll
     for (int i = 0; i < N - 1; ++i) {
-        // cross and drift terms of rate i: zero on its upper face
-        if (j[i] != s.M[i]) {
+        // cross and drift terms of rate i: zero on its upper (Neumann) face
+        if (j[i] != s.nf[i]) {
             TC inner = TC(0);
             const bool li = j[i] > 1;
 #pragma unroll
             for (int k = i + 1; k < N; ++k) {
-                if (j[k] != s.M[k]) {
+                if (j[k] != s.nf[k]) {
                     const bool lk = j[k] > 1;
                     const V pp = src.nb(J, s.Sp[i] + s.Sp[k], true, i, 1, k, 1);
                     const V pm = src.nb(J, s.Sp[i] - s.Sp[k], lk, i, 1, k, -1);
@@ -264,7 +283,7 @@ __device__ __noinline__ double payoff_H(const Shape<N>& s, const double* pay, in
         const int o = s.poff[0] + j[0];
         const double x0 = fmax(A[o], 0.0);
         const double m = fmax(A[o - 1], 0.0);
-        const double p = (j[0] == s.M[0]) ? m : fmax(A[o + 1], 0.0);
+        const double p = (j[0] == s.nf[0]) ? m : fmax(A[o + 1], 0.0);
         return tab[s.toff[0] + j[0] - 1] * ((p - x0) - (x0 - m));
     }
     double a[n], b[n], P0[n], S0[n];  // P0[r], S0[r]: product and sum before rate r
@@ -296,7 +315,7 @@ __device__ __noinline__ double payoff_H(const Shape<N>& s, const double* pay, in
 #pragma unroll
     for (int i = 0; i < n; ++i) {
         const int o = s.poff[i] + j[i];
-        const bool top = j[i] == s.M[i];
+        const bool top = j[i] == s.nf[i];
         const double m = g(i, o - 1, -1, 0);
         const double p = top ? m : g(i, o + 1, -1, 0);
         const double dp = p - x0;
@@ -310,11 +329,11 @@ __device__ __noinline__ double payoff_H(const Shape<N>& s, const double* pay, in
 #pragma unroll
     for (int i = 0; i < n; ++i) {
         double inner = 0.0;
-        if (j[i] != s.M[i]) {
+        if (j[i] != s.nf[i]) {
             const int oi = s.poff[i] + j[i];
 #pragma unroll
             for (int k = i + 1; k < n; ++k) {
-                if (j[k] != s.M[k]) {
+                if (j[k] != s.nf[k]) {
                     const int ok = s.poff[k] + j[k];
                     const double pp = g(i, oi + 1, k, ok + 1);
                     const double pm = g(i, oi + 1, k, ok - 1);
@@ -418,7 +437,7 @@ __device__ __forceinline__ void diff_pass(const Shape<N>& s, const double* X, do
         const int J = s.padded(t);
 #pragma unroll
         for (int k = 1; k < N; ++k) {
-            if (j[k] != s.M[k]) {
+            if (j[k] != s.M[k]) {  // (also not on a Dirichlet face: never read there)
                 const double xm = (j[k] > 1) ? X[J - s.Sp[k]] : 0.0;
                 D[k * Lp + J] = X[J + s.Sp[k]] - xm;
             }
@@ -441,17 +460,17 @@ __device__ __forceinline__ double diff_F(const Shape<N>& s, const int (&j)[N], i
     for (int i = 0; i < N; ++i) {
         if (s.M[i] > 1) {
             const double xm = (j[i] > 1) ? X[J - s.Sp[i]] : 0.0;
-            const double xp = (j[i] == s.M[i]) ? xm : X[J + s.Sp[i]];
+            const double xp = (j[i] == s.nf[i]) ? xm : X[J + s.Sp[i]];
             f += C[(I::diag + i) * Lp + J] * (xp + xm);
         }
     }
 #pragma unroll
     for (int i = 0; i < N - 1; ++i) {
-        if (j[i] != s.M[i]) {
+        if (j[i] != s.nf[i]) {
             const bool li = j[i] > 1;
 #pragma unroll
             for (int k = i + 1; k < N; ++k) {
-                if (j[k] != s.M[k]) {
+                if (j[k] != s.nf[k]) {
                     const double dp = D[k * Lp + J + s.Sp[i]];
                     const double dm = li ? D[k * Lp + J - s.Sp[i]] : 0.0;
                     f += C[I::pair(i, k) * Lp + J] * (dp - dm);
@@ -461,7 +480,7 @@ __device__ __forceinline__ double diff_F(const Shape<N>& s, const int (&j)[N], i
     }
 #pragma unroll
     for (int i = 1; i < N - 1; ++i)
-        if (j[i] != s.M[i]) f += C[(I::drift + i - 1) * Lp + J] * D[i * Lp + J];
+        if (j[i] != s.nf[i]) f += C[(I::drift + i - 1) * Lp + J] * D[i * Lp + J];
     return f;
 }
 
@@ -502,6 +521,16 @@ __device__ __forceinline__ void matrix_row(const Shape<N>& s, const double* tabd
     const double delta = (axis < N - 1) ? tabd[s.toff[axis] + r] * tabd[s.toff[N - 1] + cls]
                                         : c.cV * tabd[s.toff[N - 1] + r];
     const double nd = c.nudt * delta;
+    if ((s.dmask >> axis) & 1) {
+        // eq. bound1_0: rows 0..M-2 are the M-1 Inner nodes (no super-diagonal
+        // in the last, whose upper neighbour holds Dirichlet data); row M-1 is
+        // that Dirichlet node, an identity row
+        const bool dir = r == M - 1;
+        b = dir ? 1.0 : 1.0 + 2.0 * nd;
+        u = (r < M - 2) ? -nd : 0.0;
+        a = (r == 0 || dir) ? 0.0 : -nd;
+        return;
+    }
     b = 1.0 + 2.0 * nd;
     u = (r < M - 1) ? -nd : 0.0;
     a = (r == 0) ? 0.0 : ((r < M - 1) ? -nd : -2.0 * nd);
@@ -524,8 +553,8 @@ __device__ __forceinline__ double fold_scale(const Shape<N>& s, const double* ta
     const int v = (axis == N - 1) ? r : cls;  // V index of the row
     double f = 1.0;
 #pragma unroll
-    for (int i = 0; i < N - 1; ++i)
-        if ((s.skip >> i) & 1) f *= 1.0 + 2.0 * (c.nudt * (tabd[s.toff[i]] * tabd[s.toff[N - 1] + v]));
+    for (int i = 0; i < N - 1; ++i)  // (a Dirichlet axis of one row has no Inner node: identity)
+        if (((s.skip & ~s.dmask) >> i) & 1) f *= 1.0 + 2.0 * (c.nudt * (tabd[s.toff[i]] * tabd[s.toff[N - 1] + v]));
     if ((s.skip >> (N - 1)) & 1) f *= 1.0 + 2.0 * (c.nudt * (c.cV * tabd[s.toff[N - 1]]));
     return f;
 }
@@ -1087,7 +1116,7 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
     // groups); into a rate-axis solve only where the register sweep is called
     // out of line (N <= 4), since the epilogue then moves to a runtime axis
     constexpr bool kFoldV = N <= 4 && KIND != kMemGroup;
-    make_shape<N>(s, it.lv, tlog, rows_log(KIND), KIND != kMemGroup, kFoldV);
+    make_shape<N>(s, it.lv, tlog, rows_log(KIND), KIND != kMemGroup, kFoldV, P.bc != 0);
     const int last = kFoldV ? s.last : N - 1;  // the axis whose solve carries the epilogues
     const Layout lay = make_layout(N, it.lv, MIXED, KIND, tlog);
     Consts<double>* cd = reinterpret_cast<Consts<double>*>(base + lay.cd);
@@ -1133,7 +1162,7 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
     for (int tr = rank; tr < s.Lr; tr += gsize) {
         int j[N];
         decode<N>(s, tr, j);
-        H[tr] = (TK)payoff_H<N>(s, pay, P.payoff, j, tabd, *cd);
+        H[tr] = dirichlet_node(s, tr) ? TK(0) : (TK)payoff_H<N>(s, pay, P.payoff, j, tabd, *cd);
     }
     for (int t = rank; t < s.L; t += gsize) {
         const int J = s.padded(t);
@@ -1167,12 +1196,18 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
                 int j[N];
                 decode<N>(s, t, j);
                 const int J = s.padded(t);
-                K0[J] = (TK)diff_F<N>(s, j, J, Z, Dd, Cc, Lp, Cc[CI::fg * Lp + J]);
+                if (dirichlet_node(s, t)) K0[J] = TK(0);
+                else K0[J] = (TK)diff_F<N>(s, j, J, Z, Dd, Cc, Lp, Cc[CI::fg * Lp + J]);
             }
         } else for (int t = rank; t < s.L; t += gsize) {
             int j[N];
             decode<N>(s, t, j);
             const int J = s.padded(t);
+            if (dirichlet_node(s, t)) {  // no stencil on a Dirichlet face (its far neighbour is not stored)
+                K0[J] = TK(0);
+                if constexpr (MIXED) FY[J] = 0.f;
+                continue;
+            }
             TK k0;
             if constexpr (MIXED) {
                 const float acc = stencil_acc<N, float>(s, j, J, DFSrc{ZZ}, (const float*)tabk,
@@ -1197,6 +1232,10 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
                 int j[N];
                 decode<N>(s, t, j);
                 const int J = s.padded(t);
+                if (dirichlet_node(s, t)) {
+                    K0[J] = TK(0);
+                    continue;
+                }
                 const double f = diff_F<N>(s, j, J, (const double*)Kw, Dd, Cc, Lp, 0.0);
                 K0[J] = (TK)(2.0 * (double)K0[J] - (double)Kw[J] + theta * f);
             }
@@ -1204,6 +1243,10 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
             int j[N];
             decode<N>(s, t, j);
             const int J = s.padded(t);
+            if (dirichlet_node(s, t)) {
+                K0[J] = TK(0);
+                continue;
+            }
             const TK acc = stencil_acc<N, TK>(s, j, J, ArrSrc<TK>{Kw}, tabk, *ck);
             K0[J] = TK(2) * K0[J] - Kw[J] + ck->thdt * v2[j[N - 1]] * acc;
         }
@@ -1233,20 +1276,24 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
                 int j[N];
                 decode<N>(s, t, j);
                 const int J = s.padded(t);
-                K0[J] = (TK)diff_F<N>(s, j, J, (const double*)Kw, Dd, Cc, Lp,
-                                      fma(kQ21, (double)K1[J], Cc[CI::fg * Lp + J]));
+                if (dirichlet_node(s, t)) K0[J] = TK(0);
+                else K0[J] = (TK)diff_F<N>(s, j, J, (const double*)Kw, Dd, Cc, Lp,
+                                           fma(kQ21, (double)K1[J], Cc[CI::fg * Lp + J]));
             }
         } else for (int t = rank; t < s.L; t += gsize) {
             int j[N];
             decode<N>(s, t, j);
             const int J = s.padded(t);
+            if (dirichlet_node(s, t)) {
+                K0[J] = TK(0);
+                continue;
+            }
             if constexpr (MIXED) {
                 const float acc = stencil_acc<N, float>(s, j, J, ArrSrc<float>{(const float*)K1},
                                                         (const float*)tabk,
                                                         *(const Consts<float>*)ck);
                 const float a21dt = (float)kA21 * (float)ck->dt;
-                K0[J] = (TK)(FY[J] + a21dt * (float)v2[j[N - 1]] * acc +
-                             (float)kQ21 * (float)K1[J]);
+                K0[J] = (TK)(FY[J] + a21dt * (float)v2[j[N - 1]] * acc + (float)kQ21 * (float)K1[J]);
             } else {
                 const double acc = stencil_acc<N, double>(s, j, J, ArrSrc<double>{(const double*)Kw},
                                                           (const double*)tabk,
@@ -1264,6 +1311,10 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
                 int j[N];
                 decode<N>(s, t, j);
                 const int J = s.padded(t);
+                if (dirichlet_node(s, t)) {
+                    K0[J] = TK(0);
+                    continue;
+                }
                 const double f = diff_F<N>(s, j, J, (const double*)Kw, Dd, Cc, Lp, 0.0);
                 K0[J] = (TK)(2.0 * (double)K0[J] - (double)Kw[J] + theta * f);
             }
@@ -1271,6 +1322,10 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
             int j[N];
             decode<N>(s, t, j);
             const int J = s.padded(t);
+            if (dirichlet_node(s, t)) {
+                K0[J] = TK(0);
+                continue;
+            }
             const TK acc = stencil_acc<N, TK>(s, j, J, ArrSrc<TK>{Kw}, tabk, *ck);
             K0[J] = TK(2) * K0[J] - Kw[J] + ck->thdt * v2[j[N - 1]] * acc;
         }
@@ -1370,6 +1425,7 @@ __device__ void build_act(const Shape<N>& s, const Consts<float>& c, const float
         if (s.M[i] > 1) {
             A.sh[n] = s.sh[i];
             A.msk[n] = s.M[i] - 1;
+            A.nfm[n] = s.nf[i] - 1;
             A.M[n] = s.M[i];
             A.Sp[n] = s.Sp[i];
             A.toff[n] = s.toff[i];
@@ -1425,7 +1481,7 @@ __device__ __forceinline__ float stencil_act(const ActAxes& A, const float* __re
         const int msk = A.msk[q];
         const int jm = (t >> A.sh[q]) & msk;  // j - 1
         const bool lo = jm > 0;
-        const bool top = jm == msk;
+        const bool top = jm == A.nfm[q];
         const V m = src.nb(J, -Sp, lo, 0, 0, 0, 0);
         const V p = top ? m : src.nb(J, Sp, true, 0, 0, 0, 0);
         const float dp = Src::diff(p, x0);
@@ -1440,7 +1496,7 @@ __device__ __forceinline__ float stencil_act(const ActAxes& A, const float* __re
             for (int r = q + 1; r < n; ++r) {
                 const int mr = A.msk[r];
                 const int jr = (t >> A.sh[r]) & mr;
-                if (jr != mr) {
+                if (jr != A.nfm[r]) {
                     const int Sr = A.Sp[r];
                     const bool lr = jr > 0;
                     const V pp = src.nb(J, Sp + Sr, true, 0, 0, 0, 0);
@@ -1538,7 +1594,8 @@ __device__ void solve_item_mixed(const SolveArgs& a, const Item& it, unsigned ch
     Shape<N>& s = *reinterpret_cast<Shape<N>*>(meta);
     ActAxes& A = *reinterpret_cast<ActAxes*>(meta + shape_bytes(N));
     // single-row solves are folded into another solve (not for global-memory groups)
-    if (rank == 0) make_shape<N>(s, it.lv, tlog, rows_log(KIND), KIND != kMemGroup, KIND != kMemGroup);
+    if (rank == 0)
+        make_shape<N>(s, it.lv, tlog, rows_log(KIND), KIND != kMemGroup, KIND != kMemGroup, P.bc != 0);
     gsync<WARP>(gm);
     const Layout lay = make_layout(N, it.lv, true, KIND, tlog);
     Consts<double>* cd = reinterpret_cast<Consts<double>*>(base + lay.cd);
@@ -1571,7 +1628,7 @@ __device__ void solve_item_mixed(const SolveArgs& a, const Item& it, unsigned ch
     for (int tr = rank; tr < s.Lr; tr += gsize) {
         int j[N];
         decode<N>(s, tr, j);
-        H[tr] = (float)payoff_H<N>(s, pay, P.payoff, j, tabd, *cd);
+        H[tr] = dirichlet_node(s, tr) ? 0.f : (float)payoff_H<N>(s, pay, P.payoff, j, tabd, *cd);
     }
     for (int t = rank; t < s.L; t += gsize) {
         const int J = s.padded(t);
@@ -1601,8 +1658,9 @@ __device__ void solve_item_mixed(const SolveArgs& a, const Item& it, unsigned ch
             if (ph == 0) {
                 for (int t = rank; t < L; t += gsize) {
                     const int J = s.padded(t);
-                    const float acc = stencil_act(A, tabk, cV, t, J, DFSrc{ZZ});
-                    const float k0 = dt * v2[(t >> shV) & mV] * (H[t & Lr1] + acc);
+                    float k0 = 0.f;  // (a Dirichlet face node: no stencil, its far neighbour is not stored)
+                    if (!dirichlet_node(s, t))
+                        k0 = dt * v2[(t >> shV) & mV] * (H[t & Lr1] + stencil_act(A, tabk, cV, t, J, DFSrc{ZZ}));
                     FY[J] = k0;
                     K0[J] = k0;
                 }
@@ -1610,6 +1668,10 @@ __device__ void solve_item_mixed(const SolveArgs& a, const Item& it, unsigned ch
                 const float* X = ph == 2 ? K1 : Kw;
                 for (int t = rank; t < L; t += gsize) {
                     const int J = s.padded(t);
+                    if (dirichlet_node(s, t)) {
+                        K0[J] = 0.f;
+                        continue;
+                    }
                     const float acc = stencil_act(A, tabk, cV, t, J, ArrSrc<float>{X});
                     const float vv = v2[(t >> shV) & mV];
                     K0[J] = ph == 2 ? FY[J] + a21dt * vv * acc + (float)kQ21 * K1[J]

@@ -147,6 +147,9 @@ C5_BOXES = {
     "configured": {"alpha": (0.1, 0.4), "sigma": (0.1, 0.5), "beta": (0.5, 0.5), "K": (0.02, 0.04),
                    "T": (0.5, 2.0), "lam": (0.05, 0.3), "phi": (-0.5, 0.0),
                    "F0": 0.03, "Fmax": 0.2, "V0": 1.0, "Vmax": 1.0},
+    "configured_strikes": {"alpha": (0.1, 0.4), "sigma": (0.1, 0.5), "beta": (0.5, 0.5), "K": (0.02, 0.04),
+                           "K_lattice": 9, "T": (0.5, 2.0), "lam": (0.05, 0.3), "phi": (-0.5, 0.0),
+                           "F0": 0.03, "Fmax": 0.2, "V0": 1.0, "Vmax": 1.0},
     "centred": {"alpha": (0.02, 0.06), "sigma": (0.1, 0.5), "beta": (0.4, 0.6), "K": (0.03, 0.03),
                 "T": (0.5, 2.0), "lam": (0.05, 0.3), "phi": (-0.5, 0.0),
                 "F0": 0.03, "Fmax": 0.06, "V0": 1.0, "Vmax": 2.0},
@@ -172,6 +175,10 @@ def c5_features(count: int, start: int = 0, N: int = 6, box: str = "centred") ->
             lo, hi = B[key]
             f[:, c] = rng.uniform(lo, hi, size=m)
         f[:, 6:8] = rng.uniform(*B["phi"], size=(m, 2))
+        if B.get("K_lattice"):  # strikes on a lattice of equally spaced values
+            n = B["K_lattice"]
+            lo, hi = B["K"]
+            f[:, 3] = lo + (hi - lo) * rng.integers(0, n, size=m) / (n - 1)
         if nr == 1:
             f[:, 5] = 0.0
             f[:, 7] = f[:, 6]

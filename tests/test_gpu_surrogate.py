@@ -159,3 +159,27 @@ def test_train_calibrate_eval_with_fallback(tmp_path):
           f"kept within 1e-3 {np.mean(rel[kept] <= 1e-3):.4f} max rel err kept {rel[kept].max():.2e} "
           f"median {np.median(rel[kept]):.2e}; {len(test)} queries: solver {t_solver:.3f} s, "
           f"surrogate+fallback {t_sur:.3f} s ({t_solver / t_sur:.1f}x)")
+
+
+def test_lattice_feature_answers_only_on_its_values():
+    # strikes on a lattice of 9 values: the network is trained and answers
+    # there only; a strike between two lattice values falls back to the
+    # solver (its price is not smooth in K between kinks of the payoff)
+    kw = dict(N=4, level=3, steps=4, box="configured_strikes")
+    F = W.c5_features(2048, 0, N=4, box="configured_strikes")
+    assert len(np.unique(F[:, 3])) == 9
+    train = [W.c5_instance_from(f, **kw) for f in F]
+    y = B.solve_batch(train)
+    s = B.Surrogate(members=2, seed=3)
+    s.fit(train, y, epochs=4, lr=3e-3)
+    s.calibrate(train[:256], y[:256], rel_bound=1e-3, quantile=0.9)
+    q = np.array(F[:8])
+    q[4:, 3] = q[4:, 3] + 0.5 * (0.04 - 0.02) / 8  # halfway between lattice strikes
+    q[4:, 3] = np.minimum(q[4:, 3], 0.0399)
+    _, _, in_box = s.predict_features(q)
+    assert in_box[:4].all() and not in_box[4:].any(), in_box
+    p, fell = s.eval_features(q)
+    assert fell[4:].all()
+    ref = B.solve_batch([W.c5_instance_from(f, **kw) for f in q[4:]])
+    assert np.array_equal(p[4:], ref)
+    s.close()
