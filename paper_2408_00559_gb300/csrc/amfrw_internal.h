@@ -41,7 +41,7 @@ struct Item {
 // to size dynamic shared memory, the device to place the arrays; both call
 // this one function so they cannot disagree.
 struct Layout {
-    int32_t meta, cd, cf, tabd, tabf, pay, lu, Z, ZZ, H, FY, K1, K0, Kw, D, C, scr, total;
+    int32_t meta, cd, cf, tabd, tabf, pay, lu, Z, ZZ, H, DR, FY, K1, K0, Kw, D, C, scr, total;
     int32_t L, Lp, Lr, ntab, npay, nlu, ncoef;
 };
 
@@ -76,6 +76,7 @@ struct ActAxes {
     int M[kMaxDim];             // rows
     int ax[kMaxDim];            // the axis index
     int drift[kMaxDim];         // 1: rate axis with a drift term (rates 2..N-1)
+    int dslot[kMaxDim];         // warp groups: its slot in the per-node drift coefficients
     float g2[kMaxDim];          // 1 / (2 h) (drift gradient)
     float sconst[kMaxDim];      // drift sum: the part of the inactive rates
     float cinact;               // second-difference coefficients of the inactive axes, summed
@@ -177,6 +178,12 @@ AMFRW_HD Layout make_layout(int N, const int8_t* lv, bool mixed, int kind, int t
         y.Z = o;    o = align16(o + 8 * y.Lp);
         y.ZZ = o;   o = align16(o + 8 * y.Lp);
         y.H = o;    o = align16(o + 4 * y.Lr);
+        // warp groups: per node, the drift coefficient of every refined rate
+        // axis 2..N-1 (it depends on the node only, and the time loop would
+        // otherwise re-sum it at every F evaluation)
+        int ndrift = 0;
+        for (int i = 1; i < N - 1; ++i) ndrift += lv[i] > 0 ? 1 : 0;
+        y.DR = o;   o = align16(o + (kind == kWarpGroup ? 4 * ndrift * y.Lp : 0));
         int a = o, b = o;
         y.cd = a;   a = align16(a + (int)sizeof(Consts<double>));
         y.tabd = a; a = align16(a + 8 * y.ntab);
@@ -199,6 +206,7 @@ AMFRW_HD Layout make_layout(int N, const int8_t* lv, bool mixed, int kind, int t
         y.Z = o;    o = align16(o + 8 * y.Lp);
         y.ZZ = o;
         y.H = o;    o = align16(o + 8 * y.Lr);
+        y.DR = o;
         y.FY = o;
         y.K1 = o;   o = align16(o + 8 * y.Lp);
         y.K0 = o;   o = align16(o + 8 * y.Lp);

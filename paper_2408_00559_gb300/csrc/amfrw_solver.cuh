@@ -355,6 +355,96 @@ __device__ __noinline__ double payoff_H(const Shape<N>& s, const double* pay, in
     return acc;
 }
 
+// The same H for the mixed-precision mode, with every neighbour's payoff in
+// O(1) instead of resuming the forward loop: with the centre's prefix
+// P0[r] = prod_{l<r} b_l, S0[r] = sum_{m<r} a_m prod_{l<=m} b_l and suffix
+// T[r] = b_r (a_r + T[r+1]) (so that S = S0[r] + P0[r] T[r] for every r), a
+// neighbour that changes rate i to (a', b') has S' = S0[i] + P0[i] b' (a' +
+// T[i+1]); one that also changes rate k > i has T[i+1] replaced by
+// U_ik + Q_ik b_k' (a_k' + T[k+1]), with Q_ik = prod_{i<l<k} b_l and
+// U_ik = sum_{i<m<k} a_m prod_{i<l<=m} b_l built up as k grows.  The sums are
+// associated differently from payoff_at, which moves H by a few ulps: far
+// below the FP32 rounding of the mode, and not used by the FP64 mode.
+template <int N>
+__device__ __noinline__ float payoff_H_fast(const Shape<N>& s, const double* pay, int payoff, const int (&j)[N],
+                                            const float* __restrict__ tab, const Consts<float>& c)
+{
+    constexpr int n = N - 1;  // rate axes
+    const double* A = pay;
+    if (payoff == 0) {  // caplet: G = (F_1 - K)^+ depends on rate 1 only
+        const int o = s.poff[0] + j[0];
+        const double x0 = fmax(A[o], 0.0);
+        const double m = fmax(A[o - 1], 0.0);
+        const double p = (j[0] == s.nf[0]) ? m : fmax(A[o + 1], 0.0);
+        return tab[s.toff[0] + j[0] - 1] * (float)((p - x0) - (x0 - m));
+    }
+    const double* Bv = pay + s.phalf;
+    double a[n], b[n], P0[n], S0[n], T[n + 1];
+    double P = 1.0, S = 0.0;
+#pragma unroll
+    for (int r = 0; r < n; ++r) {
+        a[r] = A[s.poff[r] + j[r]];
+        b[r] = Bv[s.poff[r] + j[r]];
+        P0[r] = P;
+        S0[r] = S;
+        P *= b[r];
+        S = fma(a[r], P, S);
+    }
+    T[n] = 0.0;
+#pragma unroll
+    for (int r = n - 1; r >= 0; --r) T[r] = b[r] * (a[r] + T[r + 1]);
+    const double x0 = fmax(S, 0.0);
+    // differences of payoffs in FP64 (they cancel), their coefficients in FP32
+    float lap[n], grad[n];
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        const int o = s.poff[i] + j[i];
+        const bool top = j[i] == s.nf[i];
+        const double m = fmax(fma(P0[i] * Bv[o - 1], A[o - 1] + T[i + 1], S0[i]), 0.0);
+        const double p = top ? m : fmax(fma(P0[i] * Bv[o + 1], A[o + 1] + T[i + 1], S0[i]), 0.0);
+        const double dp = p - x0;
+        const double dm = x0 - m;
+        lap[i] = (float)(dp - dm);
+        grad[i] = top ? 0.f : (float)(dp + dm);
+    }
+    float acc = 0.f;
+#pragma unroll
+    for (int i = 0; i < n; ++i) acc += tab[s.toff[i] + j[i] - 1] * lap[i];
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        float inner = 0.f;
+        if (j[i] != s.nf[i]) {
+            const int oi = s.poff[i] + j[i];
+            double Q = 1.0, U = 0.0;  // Q_ik, U_ik for the current k
+#pragma unroll
+            for (int k = i + 1; k < n; ++k) {
+                if (j[k] != s.nf[k]) {
+                    const int ok = s.poff[k] + j[k];
+                    const double wp = U + Q * Bv[ok + 1] * (A[ok + 1] + T[k + 1]);
+                    const double wm = U + Q * Bv[ok - 1] * (A[ok - 1] + T[k + 1]);
+                    const double cp = P0[i] * Bv[oi + 1], cm = P0[i] * Bv[oi - 1];
+                    const double pp = fmax(fma(cp, A[oi + 1] + wp, S0[i]), 0.0);
+                    const double pm = fmax(fma(cp, A[oi + 1] + wm, S0[i]), 0.0);
+                    const double mp = fmax(fma(cm, A[oi - 1] + wp, S0[i]), 0.0);
+                    const double mm = fmax(fma(cm, A[oi - 1] + wm, S0[i]), 0.0);
+                    const float mix = (float)((pp - pm) - (mp - mm));
+                    inner += c.rm[upair(i, k)] * tab[s.toff[k] + s.M[k] + j[k] - 1] * mix;
+                }
+                Q *= b[k];
+                U = fma(a[k], Q, U);
+            }
+        }
+        if (i >= 1) {  // drift of rates 2..N-1 (eq. coef_adv), sum over rates 2..i
+            float Sd = 0.f;
+#pragma unroll
+            for (int r = 1; r <= i; ++r) Sd += c.rh[ltri(i, r)] * tab[s.toff[r] + 2 * s.M[r] + j[r] - 1];
+            inner += Sd * c.g2[i] * grad[i];
+        }
+        acc += tab[s.toff[i] + s.M[i] + j[i] - 1] * inner;
+    }
+    return acc;
+}
+
 // ------------------------------------------- difference-array stencil
 // FP64 warp groups evaluate Sketch 1 in two passes.  Pass 1 stores, per
 // axis k, the central difference D_k = X(J+E_k) - X(J-E_k) (zero on Outer
@@ -563,7 +653,10 @@ __device__ __forceinline__ double fold_scale(const Shape<N>& s, const double* ta
 // reduction as the solve, applied to the matrix coefficients (FP64).  Rows
 // are updated in ascending order; each lane keeps the pre-update values of
 // its previous row, which is the wrap-around neighbour the next row needs.
-template <int N, typename T, int RMAX>
+// TC: the precision of the reduction (FP64 for the FP64 mode; the
+// mixed-precision mode solves its lines in FP32 and factors them in FP32 as
+// well, from matrix rows formed in FP64).
+template <int N, typename T, int RMAX, typename TC = double>
 __device__ void pcr_setup(const Shape<N>& s, const double* tabd, const Consts<double>& c, T* lu,
                           int rank, int gsize, unsigned gm)
 {
@@ -582,17 +675,21 @@ __device__ void pcr_setup(const Shape<N>& s, const double* tabd, const Consts<do
             const bool act = cls < ncls;
             const int cl = act ? cls : 0;
             T* tb = lu + s.luoff[axis] + (cl * M + p) * S;
-            double a[RMAX], b[RMAX], u[RMAX];
+            TC a[RMAX], b[RMAX], u[RMAX];
 #pragma unroll
             for (int q = 0; q < RMAX; ++q) {
                 if (q < R) {
-                    matrix_row<N>(s, tabd, c, axis, cl, p + P * q, a[q], b[q], u[q]);
+                    double ad, bd, ud;
+                    matrix_row<N>(s, tabd, c, axis, cl, p + P * q, ad, bd, ud);
                     if (axis == s.last && s.skip) {  // the folded single-row solves
                         const double f = fold_scale<N>(s, tabd, c, axis, cl, p + P * q);
-                        a[q] *= f;
-                        b[q] *= f;
-                        u[q] *= f;
+                        ad *= f;
+                        bd *= f;
+                        ud *= f;
                     }
+                    a[q] = (TC)ad;
+                    b[q] = (TC)bd;
+                    u[q] = (TC)ud;
                 }
             }
             for (int k = 0; k < plog; ++k) {
@@ -603,34 +700,34 @@ __device__ void pcr_setup(const Shape<N>& s, const double* tabd, const Consts<do
                 const bool send_next = p < d;               // my receiver (p - d) wraps
                 // reciprocals of this level's diagonals (one division per row;
                 // the neighbours' reciprocals arrive by shuffle)
-                double rb[RMAX];
+                TC rb[RMAX];
 #pragma unroll
-                for (int q = 0; q < RMAX; ++q) rb[q] = (q < R) ? 1.0 / b[q] : 1.0;
-                double pa = 0.0, prb = 1.0, pu = 0.0;        // pre-update values of row q-1
+                for (int q = 0; q < RMAX; ++q) rb[q] = (q < R) ? TC(1) / b[q] : TC(1);
+                TC pa = TC(0), prb = TC(1), pu = TC(0);      // pre-update values of row q-1
 #pragma unroll
                 for (int q = 0; q < RMAX; ++q) {
                     if (q < R) {
                         const int qn = (q + 1 < RMAX) ? q + 1 : q;  // static after unrolling
                         const bool nx = q + 1 < R;
                         // to the lane above (p + d): my row q, or my row q-1 across the wrap
-                        const double a_m = shfl(send_prev ? pa : a[q], sm, P, gm);
-                        const double rb_m = shfl(send_prev ? prb : rb[q], sm, P, gm);
-                        const double u_m = shfl(send_prev ? pu : u[q], sm, P, gm);
+                        const TC a_m = shfl(send_prev ? pa : a[q], sm, P, gm);
+                        const TC rb_m = shfl(send_prev ? prb : rb[q], sm, P, gm);
+                        const TC u_m = shfl(send_prev ? pu : u[q], sm, P, gm);
                         // to the lane below (p - d): my row q, or my row q+1 across the wrap
-                        const double a_p = shfl(send_next ? (nx ? a[qn] : 0.0) : a[q], sp, P, gm);
-                        const double rb_p = shfl(send_next ? (nx ? rb[qn] : 1.0) : rb[q], sp, P, gm);
-                        const double u_p = shfl(send_next ? (nx ? u[qn] : 0.0) : u[q], sp, P, gm);
+                        const TC a_p = shfl(send_next ? (nx ? a[qn] : TC(0)) : a[q], sp, P, gm);
+                        const TC rb_p = shfl(send_next ? (nx ? rb[qn] : TC(1)) : rb[q], sp, P, gm);
+                        const TC u_p = shfl(send_next ? (nx ? u[qn] : TC(0)) : u[q], sp, P, gm);
                         const bool hm = !wm || q >= 1;
-                        const double al = hm ? a[q] * rb_m : 0.0;
-                        const double ga = u[q] * rb_p;  // identity row sent past the end
+                        const TC al = hm ? a[q] * rb_m : TC(0);
+                        const TC ga = u[q] * rb_p;  // identity row sent past the end
                         if (act) {
                             tb[q * P * S + 2 * k] = (T)al;
-                            tb[q * P * S + 2 * k + 1] = (T)(wp && !nx ? 0.0 : ga);
+                            tb[q * P * S + 2 * k + 1] = (T)(wp && !nx ? TC(0) : ga);
                         }
                         pa = a[q];
                         prb = rb[q];
                         pu = u[q];
-                        const double gg = (wp && !nx) ? 0.0 : ga;
+                        const TC gg = (wp && !nx) ? TC(0) : ga;
                         b[q] = b[q] - al * u_m - gg * a_p;
                         a[q] = -al * a_m;
                         u[q] = -gg * u_p;
@@ -638,11 +735,11 @@ __device__ void pcr_setup(const Shape<N>& s, const double* tabd, const Consts<do
                 }
             }
             // Thomas factors of the lane's interleaved system (rows coupled at distance P)
-            double gam = 0.0;
+            TC gam = TC(0);
 #pragma unroll
             for (int q = 0; q < RMAX; ++q) {
                 if (q < R) {
-                    const double inv = 1.0 / (b[q] - a[q] * gam);
+                    const TC inv = TC(1) / (b[q] - a[q] * gam);
                     gam = u[q] * inv;
                     if (act) {
                         T* row = tb + q * P * S + 2 * plog;
@@ -1157,12 +1254,16 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
     } else {
         pcr_setup<N, TK, RMAX>(s, tabd, *cd, lu, rank, gsize, gm);
     }
+    if constexpr (MIXED) gsync<WARP>(gm);  // the FP32 tables and constants are complete
 
     // 2. H = F(G)/V^2 on the rate grid (FP64), Z from the state or zero
     for (int tr = rank; tr < s.Lr; tr += gsize) {
         int j[N];
         decode<N>(s, tr, j);
-        H[tr] = dirichlet_node(s, tr) ? TK(0) : (TK)payoff_H<N>(s, pay, P.payoff, j, tabd, *cd);
+        if (dirichlet_node(s, tr)) H[tr] = TK(0);
+        else if constexpr (MIXED) H[tr] = (TK)payoff_H_fast<N>(s, pay, P.payoff, j, (const float*)tabk,
+                                                               *(const Consts<float>*)ck);
+        else H[tr] = (TK)payoff_H<N>(s, pay, P.payoff, j, tabd, *cd);
     }
     for (int t = rank; t < s.L; t += gsize) {
         const int J = s.padded(t);
@@ -1440,6 +1541,8 @@ __device__ void build_act(const Shape<N>& s, const Consts<float>& c, const float
     A.n = n;
     A.nr = (s.M[N - 1] > 1) ? n - 1 : n;
     A.cinact = cin;
+    int slot = 0;
+    for (int q = 0; q < n; ++q) A.dslot[q] = A.drift[q] ? slot++ : -1;
     for (int q = 0; q < n; ++q) {
         const int i = A.ax[q];
         for (int r = 0; r < kMaxDim; ++r) {
@@ -1462,65 +1565,81 @@ __device__ void build_act(const Shape<N>& s, const Consts<float>& c, const float
     }
 }
 
-// Sketch 1 at node t (padded index J) divided by V^2, from the active-axis
-// table: the same terms as stencil_acc (second differences with the Neumann
-// ghost, cross differences and drift off the upper faces, zero Outer values),
-// with the inactive axes' second differences folded into one coefficient.
+// Sketch 1 divided by V^2 at two nodes of a lane at once (t[0], t[1];
+// padded indices J), from the active-axis table: the same terms as
+// stencil_acc (second differences with the Neumann ghost, cross differences
+// and drift off the upper faces, zero Outer values), with the inactive axes'
+// second differences folded into one coefficient and the drift coefficients
+// taken per node from DR.  The table entries of an axis or a pair are loaded
+// once for both nodes, and the two accumulations are independent chains.
+// Both nodes must be Inner (a caller substitutes an Inner node for an unused
+// one and discards its result).
 template <class Src>
-__device__ __forceinline__ float stencil_act(const ActAxes& A, const float* __restrict__ tab, float cV,
-                                             int t, int J, const Src& src)
+__device__ __forceinline__ void stencil_act2(const ActAxes& A, const float* __restrict__ tab, float cV,
+                                             const int (&t)[2], const int (&J)[2], const Src& src, float (&acc)[2],
+                                             const float* __restrict__ DR, int Lp)
 {
     using V = typename Src::V;
-    const V x0 = src.ctr(J);
-    const float xv = Src::val(x0);
-    float acc = A.cinact * (-2.f * xv);
+    V x0[2];
+    float xv[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        x0[k] = src.ctr(J[k]);
+        xv[k] = Src::val(x0[k]);
+        acc[k] = A.cinact * (-2.f * xv[k]);
+    }
     const int n = A.n, nr = A.nr;
 #pragma unroll 1
     for (int q = 0; q < n; ++q) {
-        const int Sp = A.Sp[q];
-        const int msk = A.msk[q];
-        const int jm = (t >> A.sh[q]) & msk;  // j - 1
-        const bool lo = jm > 0;
-        const bool top = jm == A.nfm[q];
-        const V m = src.nb(J, -Sp, lo, 0, 0, 0, 0);
-        const V p = top ? m : src.nb(J, Sp, true, 0, 0, 0, 0);
-        const float dp = Src::diff(p, x0);
-        const float dm = Src::diff(x0, m);
+        const int Sp = A.Sp[q], msk = A.msk[q], sh = A.sh[q], nfm = A.nfm[q], to = A.toff[q];
         const bool rate = q < nr;
-        const int to = A.toff[q];
-        acc += (rate ? tab[to + jm] : cV) * (dp - dm);
-        if (rate && !top) {
+        int jm[2];
+        bool lo[2], top[2];
+        float dp[2], dm[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            jm[k] = (t[k] >> sh) & msk;  // j - 1
+            lo[k] = jm[k] > 0;
+            top[k] = jm[k] == nfm;
+            const V m = src.nb(J[k], -Sp, lo[k], 0, 0, 0, 0);
+            const V p = top[k] ? m : src.nb(J[k], Sp, true, 0, 0, 0, 0);
+            dp[k] = Src::diff(p, x0[k]);
+            dm[k] = Src::diff(x0[k], m);
+            acc[k] += (rate ? tab[to + jm[k]] : cV) * (dp[k] - dm[k]);
+        }
+        if (rate && !(top[0] && top[1])) {
             const int Mq = A.M[q];
-            float inner = 0.f;
+            float inner[2] = {0.f, 0.f};
 #pragma unroll 1
             for (int r = q + 1; r < n; ++r) {
-                const int mr = A.msk[r];
-                const int jr = (t >> A.sh[r]) & mr;
-                if (jr != A.nfm[r]) {
-                    const int Sr = A.Sp[r];
-                    const bool lr = jr > 0;
-                    const V pp = src.nb(J, Sp + Sr, true, 0, 0, 0, 0);
-                    const V pm = src.nb(J, Sp - Sr, lr, 0, 0, 0, 0);
-                    const V mp = src.nb(J, -Sp + Sr, lo, 0, 0, 0, 0);
-                    const V mm = src.nb(J, -Sp - Sr, lo && lr, 0, 0, 0, 0);
-                    const float mix = Src::diff(pp, pm) - Src::diff(mp, mm);
-                    const float ck = (r < nr) ? A.cx[q][r] * tab[A.toff[r] + A.M[r] + jr] : A.cx[q][r];
-                    inner += ck * mix;
+                const int mr = A.msk[r], shr = A.sh[r], nfr = A.nfm[r], Sr = A.Sp[r];
+                const float cx = A.cx[q][r];
+                const bool vr = r >= nr;
+                const int pw = vr ? 0 : A.toff[r] + A.M[r];
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const int jr = (t[k] >> shr) & mr;
+                    if (!top[k] && jr != nfr) {
+                        const bool lr = jr > 0;
+                        const V pp = src.nb(J[k], Sp + Sr, true, 0, 0, 0, 0);
+                        const V pm = src.nb(J[k], Sp - Sr, lr, 0, 0, 0, 0);
+                        const V mp = src.nb(J[k], -Sp + Sr, lo[k], 0, 0, 0, 0);
+                        const V mm = src.nb(J[k], -Sp - Sr, lo[k] && lr, 0, 0, 0, 0);
+                        const float mix = Src::diff(pp, pm) - Src::diff(mp, mm);
+                        inner[k] += (vr ? cx : cx * tab[pw + jr]) * mix;
+                    }
                 }
             }
-            if (A.drift[q]) {  // drift of rates 2..N-1 (eq. coef_adv), sum over rates 2..i
-                float S = A.sconst[q];
-#pragma unroll 1
-                for (int r = 0; r <= q; ++r) {
-                    const float w = A.drh[q][r];
-                    if (w != 0.f) S += w * tab[A.toff[r] + 2 * A.M[r] + ((t >> A.sh[r]) & A.msk[r])];
-                }
-                inner += S * A.g2[q] * (dp + dm);
+            if (A.drift[q]) {  // drift of rates 2..N-1 (eq. coef_adv): its per-node coefficient
+                const float* dr = DR + A.dslot[q] * Lp;
+#pragma unroll
+                for (int k = 0; k < 2; ++k) inner[k] += dr[J[k]] * (dp[k] + dm[k]);
             }
-            acc += tab[to + Mq + jm] * inner;
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+                if (!top[k]) acc[k] += tab[to + Mq + jm[k]] * inner[k];
         }
     }
-    return acc;
 }
 
 // Multilinear interpolation at the spot x* = (F_1(0), ..., V0) of Y = G + Z
@@ -1622,13 +1741,14 @@ __device__ void solve_item_mixed(const SolveArgs& a, const Item& it, unsigned ch
     if constexpr (KIND == kMemGroup) {
         pcr_setup_mem<N, float>(s, tabd, *cd, lu, reinterpret_cast<double*>(base + lay.scr), rank, gsize, gm);
     } else {
-        pcr_setup<N, float, RMAX>(s, tabd, *cd, lu, rank, gsize, gm);
+        pcr_setup<N, float, RMAX, float>(s, tabd, *cd, lu, rank, gsize, gm);
     }
-    // 2. H = F(G)/V^2 on the rate grid (FP64), Z from the state or zero
+    gsync<WARP>(gm);  // the FP32 tables and constants are complete
+    // 2. H = F(G)/V^2 on the rate grid (payoff differences in FP64), Z from the state or zero
     for (int tr = rank; tr < s.Lr; tr += gsize) {
         int j[N];
         decode<N>(s, tr, j);
-        H[tr] = dirichlet_node(s, tr) ? 0.f : (float)payoff_H<N>(s, pay, P.payoff, j, tabd, *cd);
+        H[tr] = dirichlet_node(s, tr) ? 0.f : payoff_H_fast<N>(s, pay, P.payoff, j, tabk, *ck);
     }
     for (int t = rank; t < s.L; t += gsize) {
         const int J = s.padded(t);
@@ -1644,6 +1764,25 @@ __device__ void solve_item_mixed(const SolveArgs& a, const Item& it, unsigned ch
     gsync<WARP>(gm);
     if (rank == 0) build_act<N>(s, *ck, tabk, A);
     gsync<WARP>(gm);
+    // per-node drift coefficients S_i g2_i, S_i = sum over rates 2..i of
+    // rho_ir alpha_r tau_r F_r^beta / (1 + tau_r F_r) (eq. coef_adv)
+    float* DR = reinterpret_cast<float*>(base + lay.DR);
+    const int Lp = lay.Lp;
+    if constexpr (WARP) {
+        for (int t = rank; t < s.L; t += gsize) {
+            const int J = s.padded(t);
+            for (int q = 0; q < A.n; ++q) {
+                if (!A.drift[q]) continue;
+                float S = A.sconst[q];
+                for (int r = 0; r <= q; ++r) {
+                    const float w = A.drh[q][r];
+                    if (w != 0.f) S += w * tabk[A.toff[r] + 2 * A.M[r] + ((t >> A.sh[r]) & A.msk[r])];
+                }
+                DR[A.dslot[q] * Lp + J] = S * A.g2[q];
+            }
+        }
+        gsync<WARP>(gm);
+    }
 
     const int Lr1 = s.Lr - 1;
     const int shV = s.sh[N - 1], mV = s.M[N - 1] - 1;
@@ -1652,30 +1791,45 @@ __device__ void solve_item_mixed(const SolveArgs& a, const Item& it, unsigned ch
     const float a21dt = (float)kA21 * dt;
     const int last = s.last;
     const int L = s.L;
+    // a Dirichlet rate axis of one row leaves no Inner node: F is 0 everywhere
+    bool all_dir = false;
+    for (int i = 0; i < N - 1; ++i) all_dir |= ((s.dmask >> i) & 1) && s.M[i] == 1;
     for (int n = 0; n < a.steps; ++n) {
 #pragma unroll 1
         for (int ph = 0; ph < 4; ++ph) {
-            if (ph == 0) {
-                for (int t = rank; t < L; t += gsize) {
-                    const int J = s.padded(t);
-                    float k0 = 0.f;  // (a Dirichlet face node: no stencil, its far neighbour is not stored)
-                    if (!dirichlet_node(s, t))
-                        k0 = dt * v2[(t >> shV) & mV] * (H[t & Lr1] + stencil_act(A, tabk, cV, t, J, DFSrc{ZZ}));
-                    FY[J] = k0;
-                    K0[J] = k0;
+            // a lane's nodes two at a time; a node that is unused or holds
+            // Dirichlet data (eq. bound1_0: its far neighbour is not stored) is
+            // evaluated as node 0 (always Inner when any node is) and discarded
+            for (int tb = rank; tb < L; tb += 2 * gsize) {
+                int t[2] = {tb, tb + gsize};
+                bool use[2];
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    use[k] = t[k] < L && !dirichlet_node(s, t[k]);
+                    if (!use[k]) t[k] = 0;
                 }
-            } else {
-                const float* X = ph == 2 ? K1 : Kw;
-                for (int t = rank; t < L; t += gsize) {
-                    const int J = s.padded(t);
-                    if (dirichlet_node(s, t)) {
-                        K0[J] = 0.f;
-                        continue;
+                int J[2] = {s.padded(t[0]), s.padded(t[1])};
+                float acc[2] = {0.f, 0.f};
+                if ((use[0] || use[1]) && !all_dir) {
+                    if (ph == 0) stencil_act2(A, tabk, cV, t, J, DFSrc{ZZ}, acc, DR, Lp);
+                    else stencil_act2(A, tabk, cV, t, J, ArrSrc<float>{ph == 2 ? K1 : Kw}, acc, DR, Lp);
+                }
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const int tk = tb + k * gsize;
+                    if (tk >= L) continue;
+                    const int Jk = use[k] ? J[k] : s.padded(tk);
+                    const float vv = v2[(t[k] >> shV) & mV];
+                    float out;
+                    if (ph == 0) {
+                        out = use[k] ? dt * vv * (H[t[k] & Lr1] + acc[k]) : 0.f;
+                        FY[Jk] = out;
+                    } else if (ph == 2) {
+                        out = use[k] ? FY[Jk] + a21dt * vv * acc[k] + (float)kQ21 * K1[Jk] : 0.f;
+                    } else {
+                        out = use[k] ? 2.f * K0[Jk] - Kw[Jk] + thdt * vv * acc[k] : 0.f;
                     }
-                    const float acc = stencil_act(A, tabk, cV, t, J, ArrSrc<float>{X});
-                    const float vv = v2[(t >> shV) & mV];
-                    K0[J] = ph == 2 ? FY[J] + a21dt * vv * acc + (float)kQ21 * K1[J]
-                                    : 2.f * K0[J] - Kw[J] + thdt * vv * acc;
+                    K0[Jk] = out;
                 }
             }
             gsync<WARP>(gm);
