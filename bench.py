@@ -100,7 +100,41 @@ def parse():
     ap.add_argument("--only", default=None,
                     help="paper: one row, TABLE:LEVEL[:STEPS] (e.g. sg_d4:12:8, d4:level:12), for profiling")
     ap.add_argument("--psi", type=int, default=None, help="paper: with --only, the table's psi")
+    ap.add_argument("--profile-once", action="store_true",
+                    help="c2/c3/c4: build the batch and run it once, without the FP64 re-solve node "
+                         "(whose graphs ncu cannot profile kernel by kernel); for ncu captures")
+    ap.add_argument("--gemm", default=None,
+                    help="M,N,K: run the tensor-core GEMM of the surrogate on that shape (for ncu captures)")
     return ap.parse_args()
+
+
+def profile_once(args):
+    """One run of a solver batch (or of the surrogate's GEMM), for profilers."""
+    import torch
+
+    from paper_2408_00559_gb300 import _lib as L
+    from paper_2408_00559_gb300 import build as BLD
+    BLD.build()
+    if args.gemm:
+        M, N, K = (int(x) for x in args.gemm.split(","))
+        g = torch.Generator(device="cuda").manual_seed(0)
+        A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
+        Bm = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
+        Cm = torch.empty(M, N, device="cuda", dtype=torch.float32)
+        for _ in range(args.warmup + 1):
+            L.tc_gemm_bf16(A, Bm, Cm)
+        torch.cuda.synchronize()
+        print(f"gemm {M}x{N}x{K} done", flush=True)
+        return
+    wl = WORKLOADS[args.workload]
+    B = args.batch or wl["batch"]
+    b = L.Batch(workload_batch(args.workload, B))
+    b.set_kappa_max(0.0)
+    out = torch.zeros(B, dtype=torch.float64, device="cuda")
+    b.run(out.data_ptr())
+    torch.cuda.synchronize()
+    print(f"{args.workload}: {B} instances, {b.launches()} launches, classes {b.classes()}", flush=True)
+    b.close()
 
 
 def workload_batch(name: str, count: int, start: int = 0, precision: str | None = None) -> list[dict]:
@@ -939,6 +973,10 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.profile_once or args.gemm:
+        if rank == 0:
+            profile_once(args)
         return
     if args.workload == "c5":
         if rank == 0:

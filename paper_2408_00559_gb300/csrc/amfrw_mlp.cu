@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cudaTypedefs.h>
+
 #include <mutex>
 #include <string>
 
@@ -12,13 +14,55 @@
 namespace amfrw {
 namespace tc {
 
+// cuTensorMapEncodeTiled from the driver, looked up through the runtime (no
+// link against the driver library).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// Tensor map of a row-major BF16 matrix [rows x K] with leading dimension ld
+// (elements): boxes of 8 elements of K by box_rows rows, no swizzle, zero fill
+// outside the matrix.
+bool make_map(CUtensorMap* tm, const __nv_bfloat16* base, int rows, int K, int ld, int box_rows)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {8, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)base, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // C[M x N] = A[M x K] * B[N x K]^T with the fused epilogue `epi`; N split in
-// column tiles of at most 256.
+// column tiles of at most 256.  A, B: 16-byte aligned, lda and ldb multiples
+// of 8 (the tensor maps' row strides are multiples of 16 bytes).
 int gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N, int K,
          const Epi& epi, cudaStream_t st)
 {
+    const int BN = N <= 256 ? N : 256;
+    const int nk = (K + kBK - 1) / kBK;
+    // at most two stages of the widest tile (96 KB), so that two CTAs share an
+    // SM and one's epilogue overlaps the other's loads and MMAs
+    int S = kMaxStages;
+    while (S > 1 && (S > nk || smem_bytes(BN, S) > 110 * 1024)) --S;
+    const int smem = smem_bytes(BN, S);
     // The dynamic shared-memory limit is a per-device attribute of the
-    // kernel: raise it once on every device that launches it.
+    // kernel: raise it once on every device that launches it (to the most any
+    // launch asks for).
     static std::mutex mu;
     static bool attr[64] = {};
     int dev = 0;
@@ -28,15 +72,15 @@ int gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M
     {
         std::lock_guard<std::mutex> lock(mu);
         if (!attr[dev]) {
-            e = cudaFuncSetAttribute(gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kSmemBytes);
+            e = cudaFuncSetAttribute(gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 1024);
             if (e != cudaSuccess) return (int)e;
             attr[dev] = true;
         }
     }
-    const int BN = N <= 256 ? N : 256;
+    CUtensorMap tA, tB;
+    if (!make_map(&tA, A, M, K, lda, kBM) || !make_map(&tB, B, N, K, ldb, BN)) return (int)cudaErrorInvalidValue;
     dim3 grid((M + kBM - 1) / kBM, (N + BN - 1) / BN);
-    gemm_bf16_kernel<<<grid, kThreads, kSmemBytes, st>>>(A, lda, B, ldb, M, N, K, BN, epi);
+    gemm_bf16_kernel<<<grid, kThreads, smem, st>>>(tA, tB, M, N, K, BN, S, epi);
     return (int)cudaGetLastError();
 }
 
