@@ -70,6 +70,11 @@ WORKLOADS = {
     "c3": dict(desc=C3_DESC, dtype="f32+f64", batch=4, mixed=True),
 }
 L2_FLUSH_BYTES = 256 << 20
+# DRAM bytes (read + write) of the solver launches of one 256-instance batched
+# mixed-precision batch in its multi-class configuration (one launch per N):
+# one ncu capture, dram__bytes_read.sum 540 416 + 1 752 064 + 7 318 016 and
+# dram__bytes_write.sum 0 + 0 + 45 548 288 for N = 4, 6, 8.
+C4_DRAM_BYTES_PER_BATCH = 540416 + 1752064 + 7318016 + 45548288
 
 
 def parse():
@@ -577,6 +582,10 @@ def run_ours(args, rank, world, local_rank):
     kernel_ms = float(np.mean([sum(ms for (_, ms, _) in kt) for kt in ktimes]))
     roof = roofline_entry(insts, kernel_ms, peak64, peak32, wl["mixed"])
     roof["solver_launches_per_batch"] = launches_per_batch
+    if name == "c4" and B == 256 and launches_per_batch == 3 and not args.global_grids:
+        roof["traffic"] = C4_DRAM_BYTES_PER_BATCH
+        roof["traffic_note"] = ("DRAM bytes of the batch's three solver launches, one ncu capture: "
+                                "parameter records, grid list, values, local-memory write-back")
 
     # accuracy: mixed prices against the FP64 GPU prices of the same instances
     # (the FP64 path is pinned to the oracle at 1e-12 by the parity tests),

@@ -211,7 +211,9 @@ int amfrw_batch_kernel_times(amfrw_batch *b, float *ms_out, double *node_steps_o
  * after a warm-up): (1) per-class launches against one persistent
  * multi-class launch for the warp-solved grids; (2) for every CTA class
  * (grids in shared memory) its launch with the grid states in shared memory
- * against in global memory, class by class.  Keeps the faster choices and
+ * against in global memory, class by class.  Keeps the faster choices (the
+ * single persistent launch unless the per-class launches are more than 10 %
+ * faster) and
  * caches them in-process under the batch's class signature (and, if the
  * environment variable AMFRW_TUNE_CACHE names a file, appends them there),
  * so later batches with the same classes start with them.  *use_multi_out

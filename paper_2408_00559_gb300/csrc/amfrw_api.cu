@@ -1279,7 +1279,10 @@ int amfrw_batch_autotune(amfrw_batch* b, int32_t trials, int32_t* use_multi_out)
             if (st == AMFRW_OK) st = timed(t[m], nullptr);
         }
         if (st != AMFRW_OK) return st;
-        best = t[1] <= t[0];
+        // one persistent launch per (N, precision) unless the per-class
+        // launches are clearly faster: a launch count that does not grow with
+        // the classes is worth a few percent
+        best = t[1] <= 1.10f * t[0];
         P.use_multi = best;
         st = build_warp_launches(P);
         if (st == AMFRW_OK) st = upload_warp_launches(P);
