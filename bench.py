@@ -722,7 +722,34 @@ def solver_variants(args, L, torch, stream, dev, flush, peak64, peak32, note):
                        "max_rel_err_vs_fp64": float(rel.max()), "within_1e-5": float(np.mean(rel <= 1e-5)),
                        "roofline": roofline_entry(insts, kms, peak64, peak32, True)}
     note(f"c3 mixed: {out['c3_mixed']['value']:.1f} instances/s")
+    out["boundary_conditions"] = boundary_report(L)
     return out
+
+
+def boundary_report(L):
+    """Prices under the paper's Neumann faces (eq. bound1) against the earlier
+    Dirichlet faces (eq. bound1_0): the d=4 level-5 FP64 batch, and the
+    paper's Black caplet (Sec. 6.1, Table fg_sigma0: sigma = 0, full grids,
+    256 steps) against its closed form 6.058877 bps."""
+    insts = workload_batch("c2", 1024, start=0)
+    pn = L.solve_batch(insts)
+    pd = L.solve_batch([dict(x, bc="dirichlet") for x in insts])
+    rel = np.abs(pd - pn) / np.abs(pn)
+    tau = 0.5
+    p2 = 1.0 / ((1.0 + tau * MKT_F0[0]) * (1.0 + tau * MKT_F0[1]))
+    th = W.THETA_W2
+    cap = dict(N=2, payoff="caplet", n_steps=256, alpha=np.array([MKT_ALPHA[1]]), phi=np.array([0.0]),
+               tau=np.array([tau]), F0=np.array([MKT_F0[1]]), Fmax=np.array([0.04]), Vmax=3.5,
+               rho=np.ones((1, 1)), sigma=0.0, beta=1.0, V0=1.0, K=0.011, T=MKT_T[1], theta=th, nu=th,
+               discount=1.0, psi=0, full=True, precision="fp64")
+    rows = []
+    for lev in (5, 6, 7):
+        u = [float(L.solve_batch([dict(cap, level=lev, bc=bc)])[0]) for bc in ("neumann", "dirichlet")]
+        bps = [1e4 * p2 * tau * x for x in u]
+        rows.append({"level": lev, "neumann_bps": bps[0], "dirichlet_bps": bps[1],
+                     "neumann_err_bps": bps[0] - 6.058877, "dirichlet_err_bps": bps[1] - 6.058877})
+    return {"c2_fp64_1024": {"median_rel_diff": float(np.median(rel)), "max_rel_diff": float(rel.max())},
+            "caplet_black_6.058877_bps": rows}
 
 
 # ------------------------------------------------------------ surrogate (c5)

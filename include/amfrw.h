@@ -205,16 +205,18 @@ int amfrw_batch_enable_timing(amfrw_batch *b, int32_t on);
 int amfrw_batch_kernel_times(amfrw_batch *b, float *ms_out, double *node_steps_out,
                              int32_t *dims_out, int32_t cap, int32_t *n_out);
 
-/* Autotuning of the launch strategy and of where grid states live (the
- * paper has no counterpart; its CPU code schedules grids with OpenMP's
- * dynamic schedule).  Times, on this batch and device (`trials` solves each
- * after a warm-up): (1) per-class launches against one persistent
- * multi-class launch for the warp-solved grids; (2) for every CTA class
+/* Autotuning of the launch strategy, of the warp groups' width and of where
+ * grid states live (the paper has no counterpart; its CPU code schedules
+ * grids with OpenMP's dynamic schedule).  Times, on this batch and device
+ * (`trials` solves each after a warm-up): (1) per-class launches against one
+ * persistent multi-class launch for the warp-solved grids; (2) the warp
+ * groups' width: each grid on its natural number of lanes (two nodes per
+ * lane) against twice as many (one node per lane, one more level of parallel
+ * cyclic reduction and fewer Thomas rows per line); (3) for every CTA class
  * (grids in shared memory) its launch with the grid states in shared memory
  * against in global memory, class by class.  Keeps the faster choices (the
  * single persistent launch unless the per-class launches are more than 10 %
- * faster) and
- * caches them in-process under the batch's class signature (and, if the
+ * faster) and caches them in-process under the batch's class signature (and, if the
  * environment variable AMFRW_TUNE_CACHE names a file, appends them there),
  * so later batches with the same classes start with them.  *use_multi_out
  * (may be NULL) receives choice (1).  Prices change by rounding only.

@@ -301,6 +301,7 @@ struct Plan {
     ClassDesc* d_cdesc = nullptr;
     int64_t n_cdesc = 0;
     bool use_multi = true;  // launch strategy (the autotuner may switch it)
+    int glog_delta = 0;     // warp groups: lanes per grid widened by 2^glog_delta (autotuned)
     bool shared_u = false;  // d_u belongs to another plan (the FP64 re-solve writes there)
     const int32_t* inst_mask = nullptr;  // instances to solve, or null for all
 
@@ -578,15 +579,26 @@ int build_warp_launches(Plan& P)
             d.item_count = L.item_count;
             d.smem_group = L.smem_group;
             d.qidx = c;
-            while (d.glog < 5 && ((int64_t)d.smem_group << (5 - d.glog)) > budget) {
-                ++d.glog;
+            // the group's shared memory for a width of 2^g lanes
+            auto group_smem = [&](int g) {
                 int sg = 0;
                 for (int q = L.item_begin; q < L.item_begin + L.item_count; ++q) {
                     if (q > L.item_begin && memcmp(P.items[q].lv, P.items[q - 1].lv, sizeof(P.items[q].lv)) == 0)
                         continue;  // equal shapes are adjacent
-                    sg = std::max(sg, make_layout(L.N, P.items[q].lv, L.mixed, kWarpGroup, d.glog).total);
+                    sg = std::max(sg, make_layout(L.N, P.items[q].lv, L.mixed, kWarpGroup, g).total);
                 }
-                d.smem_group = sg;
+                return sg;
+            };
+            // the tuned width: more lanes per grid, so more lanes per line (one
+            // more PCR level, fewer Thomas rows) and fewer nodes per lane
+            const int g0 = std::min(5, d.glog + P.glog_delta);
+            if (g0 != d.glog) {
+                d.glog = g0;
+                d.smem_group = group_smem(g0);
+            }
+            while (d.glog < 5 && ((int64_t)d.smem_group << (5 - d.glog)) > budget) {
+                ++d.glog;
+                d.smem_group = group_smem(d.glog);
             }
             w.cls.push_back(d);
             w.smem_warp = std::max(w.smem_warp, d.smem_group << (5 - d.glog));
@@ -918,6 +930,11 @@ void save_tune_entry(const std::string& sig, int choice)
     fclose(f);
 }
 
+// Bits of a cached choice: bit 0 one persistent multi-class launch; bit 1 + k
+// the k-th CTA class in global memory; bits kChoiceWidthShift.. the widening of
+// the warp groups (log2).
+constexpr int kChoiceWidthShift = 24;
+
 // Apply cached choice bits to a freshly planned batch.
 int apply_choice(Plan& P, int choice)
 {
@@ -934,8 +951,10 @@ int apply_choice(Plan& P, int choice)
     }
     if (st == AMFRW_OK && moved) st = relayout_scratch(P);
     const bool multi = (choice & 1) != 0;
-    if (st == AMFRW_OK && multi != P.use_multi) {
+    const int delta = (choice >> kChoiceWidthShift) & 3;
+    if (st == AMFRW_OK && (multi != P.use_multi || delta != P.glog_delta)) {
         P.use_multi = multi;
+        P.glog_delta = delta;
         st = build_warp_launches(P);
         if (st == AMFRW_OK) st = upload_warp_launches(P);
     }
@@ -1288,8 +1307,26 @@ int amfrw_batch_autotune(amfrw_batch* b, int32_t trials, int32_t* use_multi_out)
         if (st == AMFRW_OK) st = upload_warp_launches(P);
         if (st != AMFRW_OK) return st;
     }
-    // 2. CTA classes: grid state in shared memory against global memory, class by class
-    int choice = best ? 1 : 0;
+    // 2. warp groups: their natural width against twice the lanes per grid
+    //    (one more PCR level per line, half the nodes per lane)
+    bool narrow = false;
+    for (const LaunchClass& c : P.classes) narrow |= c.warp && c.glog < 5;
+    if (narrow) {
+        float t[2] = {0.f, 0.f};
+        for (int d = 0; d < 2 && st == AMFRW_OK; ++d) {
+            P.glog_delta = d;
+            st = build_warp_launches(P);
+            if (st == AMFRW_OK) st = upload_warp_launches(P);
+            if (st == AMFRW_OK) st = timed(t[d], nullptr);
+        }
+        if (st != AMFRW_OK) return st;
+        P.glog_delta = t[1] < t[0] ? 1 : 0;
+        st = build_warp_launches(P);
+        if (st == AMFRW_OK) st = upload_warp_launches(P);
+        if (st != AMFRW_OK) return st;
+    }
+    // 3. CTA classes: grid state in shared memory against global memory, class by class
+    int choice = (best ? 1 : 0) | (P.glog_delta << kChoiceWidthShift);
     std::vector<int> cta;
     for (size_t c = 0; c < P.classes.size(); ++c)
         if (P.classes[c].kind == kCtaGroup) cta.push_back((int)c);

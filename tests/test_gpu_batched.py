@@ -3,8 +3,8 @@
 launch-strategy autotuner, and the accuracy of the mixed-precision path.
 
 - The multi-class launch and per-class launches run the same per-grid code,
-  so their prices agree bitwise; replays of the captured graph are bitwise
-  identical.
+  so their prices agree bitwise, and a tuned group width changes them by
+  rounding only; replays of the captured graph are bitwise identical.
 - FP64 batch prices agree with the oracle (sampled small instances) to 1e-12.
 - Mixed precision (FP32 F and line solves, FP64 accumulation, interpolation
   and combination) agrees with the FP64 path, itself pinned to the oracle, to
@@ -70,7 +70,9 @@ def test_multi_class_launch_equals_per_class_launches():
     choice = b.autotune(1)
     b.close()
     p_tuned, n_tuned = run_batch(insts)  # the cached choice applies to a new batch
-    assert np.array_equal(p_auto, p_tuned)
+    # the launch strategy does not change a price; the tuned group width (the
+    # lanes per line of the line solves) changes it by FP32 rounding only
+    assert np.allclose(p_auto, p_tuned, rtol=1e-6, atol=0), np.max(np.abs(p_auto - p_tuned) / np.abs(p_auto))
     assert isinstance(choice, bool) and n_tuned >= 2
 
 
