@@ -152,7 +152,9 @@ int amfrw_problem_create(const amfrw_params *p, void *cuda_stream, amfrw_problem
 int amfrw_step(amfrw_problem *h, int32_t n_steps);
 
 /* price = discount * sum_l c_l u_l(x*) in FP64 in a fixed grid order
- * (eq. standardCombTechnique / modifiedCombTechnique).  Synchronises.
+ * (eq. standardCombTechnique / modifiedCombTechnique).  Synchronises.  (A
+ * mixed-precision problem is not re-solved in FP64 when its sum cancels; the
+ * batch entry points do that, see amfrw_batch_set_kappa_max.)
  * Errors: EINVAL, ECUDA, ENONFINITE. */
 int amfrw_combine(amfrw_problem *h, double *price_out);
 
@@ -373,6 +375,9 @@ const char *amfrw_surrogate_last_error(void);
  *     while cuda_stream is being captured returns EINVAL.
  *   - The prices are not checked for finiteness (there is no host copy of
  *     them to inspect without a synchronisation); the caller tests them.
+ *     Mixed-precision instances whose combination sum cancels are not
+ *     re-solved in FP64 (amfrw_batch_set_kappa_max describes that re-solve of
+ *     the allocating batch entry points).
  * Errors: EINVAL, ENOTPSD, ETOOBIG, ECUDA. */
 #define AMFRW_NOALLOC_SCRATCH_BYTES (16u << 20)
 int amfrw_solve_noalloc(const amfrw_params *ps, int32_t n, double *d_prices_out, void *cuda_stream);
