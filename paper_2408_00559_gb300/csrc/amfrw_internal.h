@@ -65,21 +65,27 @@ struct Consts {
 
 // Active axes of a grid (those with more than one Inner row) for the
 // mixed-precision stencil, built once per grid in shared memory.
+// One active axis: read by the stencil as two 16-byte loads.
+struct alignas(16) ActAxis {
+    int sh;       // bit offset of j - 1 in the node index t
+    int msk;      // M - 1
+    int nfm;      // j - 1 of the Neumann face, or -2 (Dirichlet data on the upper face)
+    int Sp;       // padded stride
+    int toff;     // rate axes: offset of their coefficient tables (d, pw, drift)
+    int M;        // rows
+    int drift;    // 1: rate axis with a drift term (rates 2..N-1)
+    int dslot;    // warp groups: its slot in the per-node drift coefficients
+};
+
 struct ActAxes {
     int n;                      // active axes, ascending axis order
     int nr;                     // active rate axes (the first nr of them; V, if active, is last)
-    int sh[kMaxDim];            // bit offset of j - 1 in the node index t
-    int msk[kMaxDim];           // M - 1
-    int nfm[kMaxDim];           // j - 1 of the Neumann face, or -2 (Dirichlet data on the upper face)
-    int Sp[kMaxDim];            // padded stride
-    int toff[kMaxDim];          // rate axes: offset of their coefficient tables (d, pw, drift)
-    int M[kMaxDim];             // rows
+    float cinact;               // second-difference coefficients of the inactive axes, summed
+    int pad;
+    ActAxis rec[kMaxDim];
     int ax[kMaxDim];            // the axis index
-    int drift[kMaxDim];         // 1: rate axis with a drift term (rates 2..N-1)
-    int dslot[kMaxDim];         // warp groups: its slot in the per-node drift coefficients
     float g2[kMaxDim];          // 1 / (2 h) (drift gradient)
     float sconst[kMaxDim];      // drift sum: the part of the inactive rates
-    float cinact;               // second-difference coefficients of the inactive axes, summed
     float cx[kMaxDim][kMaxDim]; // pair (q, r), q < r: rho/(4 h h) (two rates) or sigma phi/(4 h h_V)
     float drh[kMaxDim][kMaxDim];// drift of active rate q: rho for the active rates r <= q
 };

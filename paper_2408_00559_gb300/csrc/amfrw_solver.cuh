@@ -1524,15 +1524,15 @@ __device__ void build_act(const Shape<N>& s, const Consts<float>& c, const float
     float cin = 0.f;
     for (int i = 0; i < N; ++i) {
         if (s.M[i] > 1) {
-            A.sh[n] = s.sh[i];
-            A.msk[n] = s.M[i] - 1;
-            A.nfm[n] = s.nf[i] - 1;
-            A.M[n] = s.M[i];
-            A.Sp[n] = s.Sp[i];
-            A.toff[n] = s.toff[i];
+            A.rec[n].sh = s.sh[i];
+            A.rec[n].msk = s.M[i] - 1;
+            A.rec[n].nfm = s.nf[i] - 1;
+            A.rec[n].M = s.M[i];
+            A.rec[n].Sp = s.Sp[i];
+            A.rec[n].toff = s.toff[i];
             A.ax[n] = i;
             A.g2[n] = c.g2[i];
-            A.drift[n] = (i >= 1 && i < N - 1) ? 1 : 0;
+            A.rec[n].drift = (i >= 1 && i < N - 1) ? 1 : 0;
             ++n;
         } else {
             cin += (i < N - 1) ? tab[s.toff[i]] : c.cV;  // the coefficient at j = 1
@@ -1542,7 +1542,7 @@ __device__ void build_act(const Shape<N>& s, const Consts<float>& c, const float
     A.nr = (s.M[N - 1] > 1) ? n - 1 : n;
     A.cinact = cin;
     int slot = 0;
-    for (int q = 0; q < n; ++q) A.dslot[q] = A.drift[q] ? slot++ : -1;
+    for (int q = 0; q < n; ++q) A.rec[q].dslot = A.rec[q].drift ? slot++ : -1;
     for (int q = 0; q < n; ++q) {
         const int i = A.ax[q];
         for (int r = 0; r < kMaxDim; ++r) {
@@ -1555,7 +1555,7 @@ __device__ void build_act(const Shape<N>& s, const Consts<float>& c, const float
             A.cx[q][r] = (k < N - 1) ? c.rm[upair(i, k)] : c.sm[i];
         }
         float sc = 0.f;
-        if (A.drift[q]) {
+        if (A.rec[q].drift) {
             for (int r = 1; r <= i; ++r)
                 if (s.M[r] == 1) sc += c.rh[ltri(i, r)] * tab[s.toff[r] + 2];  // j_r = 1
             for (int r = 0; r <= q; ++r)
@@ -1591,7 +1591,9 @@ __device__ __forceinline__ void stencil_act2(const ActAxes& A, const float* __re
     const int n = A.n, nr = A.nr;
 #pragma unroll 1
     for (int q = 0; q < n; ++q) {
-        const int Sp = A.Sp[q], msk = A.msk[q], sh = A.sh[q], nfm = A.nfm[q], to = A.toff[q];
+        const int4 q0 = reinterpret_cast<const int4*>(&A.rec[q])[0];  // sh, msk, nfm, Sp
+        const int4 q1 = reinterpret_cast<const int4*>(&A.rec[q])[1];  // toff, M, drift, dslot
+        const int sh = q0.x, msk = q0.y, nfm = q0.z, Sp = q0.w, to = q1.x;
         const bool rate = q < nr;
         int jm[2];
         bool lo[2], top[2];
@@ -1608,14 +1610,19 @@ __device__ __forceinline__ void stencil_act2(const ActAxes& A, const float* __re
             acc[k] += (rate ? tab[to + jm[k]] : cV) * (dp[k] - dm[k]);
         }
         if (rate && !(top[0] && top[1])) {
-            const int Mq = A.M[q];
+            const int Mq = q1.y;
             float inner[2] = {0.f, 0.f};
 #pragma unroll 1
             for (int r = q + 1; r < n; ++r) {
-                const int mr = A.msk[r], shr = A.sh[r], nfr = A.nfm[r], Sr = A.Sp[r];
+                const int4 r0 = reinterpret_cast<const int4*>(&A.rec[r])[0];
+                const int mr = r0.y, shr = r0.x, nfr = r0.z, Sr = r0.w;
                 const float cx = A.cx[q][r];
                 const bool vr = r >= nr;
-                const int pw = vr ? 0 : A.toff[r] + A.M[r];
+                int pw = 0;
+                if (!vr) {
+                    const int2 r1 = reinterpret_cast<const int2*>(&A.rec[r])[2];  // toff, M
+                    pw = r1.x + r1.y;
+                }
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
                     const int jr = (t[k] >> shr) & mr;
@@ -1630,8 +1637,8 @@ __device__ __forceinline__ void stencil_act2(const ActAxes& A, const float* __re
                     }
                 }
             }
-            if (A.drift[q]) {  // drift of rates 2..N-1 (eq. coef_adv): its per-node coefficient
-                const float* dr = DR + A.dslot[q] * Lp;
+            if (q1.z) {  // drift of rates 2..N-1 (eq. coef_adv): its per-node coefficient
+                const float* dr = DR + q1.w * Lp;
 #pragma unroll
                 for (int k = 0; k < 2; ++k) inner[k] += dr[J[k]] * (dp[k] + dm[k]);
             }
@@ -1772,13 +1779,13 @@ __device__ void solve_item_mixed(const SolveArgs& a, const Item& it, unsigned ch
         for (int t = rank; t < s.L; t += gsize) {
             const int J = s.padded(t);
             for (int q = 0; q < A.n; ++q) {
-                if (!A.drift[q]) continue;
+                if (!A.rec[q].drift) continue;
                 float S = A.sconst[q];
                 for (int r = 0; r <= q; ++r) {
                     const float w = A.drh[q][r];
-                    if (w != 0.f) S += w * tabk[A.toff[r] + 2 * A.M[r] + ((t >> A.sh[r]) & A.msk[r])];
+                    if (w != 0.f) S += w * tabk[A.rec[r].toff + 2 * A.rec[r].M + ((t >> A.rec[r].sh) & A.rec[r].msk)];
                 }
-                DR[A.dslot[q] * Lp + J] = S * A.g2[q];
+                DR[A.rec[q].dslot * Lp + J] = S * A.g2[q];
             }
         }
         gsync<WARP>(gm);
