@@ -91,11 +91,11 @@ struct ActAxes {
 };
 
 // Per-grid descriptors the mixed-precision solver keeps in shared memory:
-// the grid's shape (10 per-axis arrays and 7 scalars of int) and its active
+// the grid's shape (10 per-axis arrays and 8 scalars of int) and its active
 // axes.  Warp groups hold them in their layout; whole-block groups in a
 // static shared array of the kernel.
 AMFRW_HD constexpr int32_t align16(int32_t x) { return (x + 15) & ~15; }
-AMFRW_HD constexpr int shape_bytes(int N) { return align16(4 * (10 * N + 7)); }
+AMFRW_HD constexpr int shape_bytes(int N) { return align16(4 * (10 * N + 8)); }
 AMFRW_HD constexpr int meta_bytes(int N) { return shape_bytes(N) + align16((int)sizeof(ActAxes)); }
 constexpr int kMetaBytesMax = meta_bytes(kMaxDim);
 
@@ -139,6 +139,17 @@ AMFRW_HD int lanes_log(int mlog, int llog, int tlog, int rlog)
 // (lower, 1/pivot, upper/pivot) of the reduced interleaved systems.
 AMFRW_HD int lu_row_values(int plog) { return 2 * plog + 3; }
 
+// Mixed-precision warp groups hold a grid's values in registers (at most two
+// nodes per lane) and solve the lines of an axis of 2..8 rows by the explicit
+// inverse of its directional matrix: M values per matrix row, the rows of a
+// line exchanged by shuffles.  Their offsets are kept 16-byte aligned for
+// vector loads.
+constexpr int kDenseMaxRows = 8;
+AMFRW_HD bool dense_axis(int kind, bool mixed, int M)
+{
+    return mixed && kind == kWarpGroup && M >= 2 && M <= kDenseMaxRows;
+}
+
 // kind: the work-group kind.  Warp and global-memory groups keep the
 // line-solve factors inside the layout; CTA groups in the group's slice of a
 // global scratch array.  Global-memory groups also get FP64 scratch for the
@@ -166,11 +177,15 @@ AMFRW_HD Layout make_layout(int N, const int8_t* lv, bool mixed, int kind, int t
     int nlu = 0;
     for (int i = 0; i < N; ++i) {
         const int rows = (i < N - 1 ? MV : 1) << lv[i];  // classes x rows
-        nlu += rows * lu_row_values(lanes_log(lv[i], llog, tlog, rows_log(kind)));
+        if (dense_axis(kind, mixed, 1 << lv[i])) {
+            nlu = (nlu + 3) & ~3;
+            nlu += rows << lv[i];
+        } else {
+            nlu += rows * lu_row_values(lanes_log(lv[i], llog, tlog, rows_log(kind)));
+        }
     }
     const bool lu_in = kind != kCtaGroup;
     y.nlu = nlu;
-    const int sk = mixed ? 4 : 8;  // bytes of an increment / table value
     int o = 0;
     if (mixed) {
         // The FP64 constants and tables serve the per-grid setup only (tables,

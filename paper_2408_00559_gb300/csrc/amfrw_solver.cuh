@@ -65,12 +65,13 @@ struct Shape {
     int L, Lr, pad, phalf;
     int skip;      // axes whose single-row solves are folded into the solve along `last`
     int last;      // the last axis solved in a stage (carries the stage's epilogue)
+    int dense;     // axes solved by the explicit inverse of their directional matrix
     __device__ __forceinline__ int padded(int t) const { return t + pad * (t >> lv[0]); }
 };
 
 template <int N>
 __device__ __forceinline__ void make_shape(Shape<N>& s, const int8_t* lv, int tlog, int rlog, bool fold,
-                                           bool fold_v, bool dirichlet)
+                                           bool fold_v, bool dirichlet, bool dense = false)
 {
     int sh = 0;
 #pragma unroll
@@ -103,10 +104,17 @@ __device__ __forceinline__ void make_shape(Shape<N>& s, const int8_t* lv, int tl
     s.toff[N - 1] = o;
     s.poff[N - 1] = po;
     s.phalf = po;
+    s.dense = 0;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
+        // (the same sizes as make_layout's line-solve region)
+        const bool dn = dense && s.M[i] >= 2 && s.M[i] <= kDenseMaxRows;
         s.plog[i] = lanes_log(s.lv[i], sh, tlog, rlog);
-        s.luS[i] = lu_row_values(s.plog[i]);
+        s.luS[i] = dn ? s.M[i] : lu_row_values(s.plog[i]);
+        if (dn) {
+            s.dense |= 1 << i;
+            lo = (lo + 3) & ~3;
+        }
         s.luoff[i] = lo;
         lo += ((i < N - 1 ? s.M[N - 1] : 1) << s.lv[i]) * s.luS[i];
     }
@@ -661,6 +669,7 @@ __device__ void pcr_setup(const Shape<N>& s, const double* tabd, const Consts<do
                           int rank, int gsize, unsigned gm)
 {
     for (int axis = 0; axis < N; ++axis) {
+        if ((s.dense >> axis) & 1) continue;  // factored by dense_setup
         const int M = s.M[axis];
         const int plog = s.plog[axis];
         const int P = 1 << plog;
@@ -836,6 +845,134 @@ struct NoEpi {
     template <typename T>
     __device__ __forceinline__ void operator()(int, T) const {}
 };
+
+// ------------------------------------------ explicit inverses of short lines
+// For an axis of M = 2..8 rows (mixed-precision warp groups), the inverse of
+// every line class's directional matrix (I - nu dt A_axis), with the folded
+// single-row scalings when the axis is `last`.  One lane per (axis, class)
+// forms the M matrix rows in FP64 (as the line-solve factors are formed),
+// factors them by Thomas elimination in FP32, the precision of the mode's line
+// solves (the matrix is diagonally dominant, its inverse non-negative with row
+// sums at most 1), and solves for the M unit vectors.  Entry (q, col) is
+// stored in row q at position q XOR col, the order in which dense_mix meets
+// the rows of a line.
+template <int N>
+__device__ __noinline__ void dense_setup(const Shape<N>& s, const double* tabd, const Consts<double>& c, float* lu,
+                            int rank, int gsize)
+{
+    int total = 0;  // (axis, class) pairs of the dense axes
+#pragma unroll
+    for (int axis = 0; axis < N; ++axis)
+        if ((s.dense >> axis) & 1) total += (axis < N - 1) ? s.M[N - 1] : 1;
+    for (int w = rank; w < total; w += gsize) {
+        int axis = 0, cls = w;
+        for (; axis < N; ++axis) {
+            if (!((s.dense >> axis) & 1)) continue;
+            const int nc = (axis < N - 1) ? s.M[N - 1] : 1;
+            if (cls < nc) break;
+            cls -= nc;
+        }
+        const int M = s.M[axis];
+        const bool fold = axis == s.last && s.skip;
+        float lo[kDenseMaxRows], inv[kDenseMaxRows], gam[kDenseMaxRows];
+        float gp = 0.f;
+#pragma unroll
+        for (int q = 0; q < kDenseMaxRows; ++q) {
+            if (q < M) {
+                double ad, bd, ud;
+                matrix_row<N>(s, tabd, c, axis, cls, q, ad, bd, ud);
+                if (fold) {
+                    const double f = fold_scale<N>(s, tabd, c, axis, cls, q);
+                    ad *= f;
+                    bd *= f;
+                    ud *= f;
+                }
+                lo[q] = (float)ad;
+                inv[q] = 1.f / ((float)bd - lo[q] * gp);
+                gp = (float)ud * inv[q];
+                gam[q] = gp;
+            }
+        }
+        float* out = lu + s.luoff[axis] + cls * M * M;
+#pragma unroll 1
+        for (int col = 0; col < M; ++col) {
+            // forward elimination into the output slots, then back substitution there
+            float yp = 0.f;
+#pragma unroll
+            for (int q = 0; q < kDenseMaxRows; ++q) {
+                if (q < M) {
+                    yp = ((q == col ? 1.f : 0.f) - lo[q] * yp) * inv[q];
+                    out[q * M + (q ^ col)] = yp;
+                }
+            }
+            float x = 0.f;  // the last row has no upper neighbour (gam = 0 there)
+#pragma unroll
+            for (int q = kDenseMaxRows - 1; q >= 0; --q) {
+                if (q < M) {
+                    float& o = out[q * M + (q ^ col)];
+                    x = o - gam[q] * x;
+                    o = x;
+                }
+            }
+        }
+    }
+}
+
+// Coefficient row of MM floats (16-byte aligned for MM >= 4, 8-byte for 2).
+template <int MM>
+__device__ __forceinline__ void load_row(const float* p, float (&r)[MM])
+{
+    if constexpr (MM == 2) {
+        const float2 v = *reinterpret_cast<const float2*>(p);
+        r[0] = v.x;
+        r[1] = v.y;
+    } else {
+#pragma unroll
+        for (int q = 0; q < MM; q += 4) {
+            const float4 v = *reinterpret_cast<const float4*>(p + q);
+            r[q] = v.x;
+            r[q + 1] = v.y;
+            r[q + 2] = v.z;
+            r[q + 3] = v.w;
+        }
+    }
+}
+
+// The directional solves along an axis of MM rows for the group's values in
+// registers: lane `rank` holds nodes t = rank (x[0]) and, when the grid has
+// more nodes than the group has lanes, t = rank + gsize (x[1]).  Node t gets
+// sum_s Cinv[j][j ^ s] x(t ^ (s << sh)), j its row on the line; the node at
+// XOR distance s << sh sits in lane rank ^ ((s << sh) mod gsize), in the
+// other slot when s << sh reaches gsize.  Every lane of the group takes part
+// (the shuffles); the values of lanes without a node are never read by one
+// that has a node (the XOR of two node indices below L stays below L).
+template <int MM>
+__device__ __forceinline__ void dense_mix(const float* __restrict__ C, int sh, int shV, int mV, bool rate,
+                                          int rank, int gsize, int tlog, bool two, unsigned gm, float (&x)[2])
+{
+    float y[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        if (k == 1 && !two) break;
+        const int t = rank + (k << tlog);
+        const int j = (t >> sh) & (MM - 1);
+        const int cls = rate ? ((t >> shV) & mV) : 0;
+        float r[MM];
+        load_row<MM>(C + (cls * MM + j) * MM, r);
+        float acc = r[0] * x[k];
+#pragma unroll
+        for (int q = 1; q < MM; ++q) {
+            const int d = q << sh;
+            const int lm = d & (gsize - 1);
+            const float mine = (d >> tlog) ? x[k ^ 1] : x[k];
+            const float v = lm ? __shfl_xor_sync(gm, mine, lm, gsize) : mine;
+            acc = fmaf(r[q], v, acc);
+        }
+        y[k] = acc;
+    }
+    x[0] = y[0];
+    if (two) x[1] = y[1];
+}
 
 // ------------------------------------- line solves on grids in global memory
 // The same reduction and elimination as pcr_setup / sweep, for grids whose
@@ -1721,7 +1858,7 @@ __device__ void solve_item_mixed(const SolveArgs& a, const Item& it, unsigned ch
     ActAxes& A = *reinterpret_cast<ActAxes*>(meta + shape_bytes(N));
     // single-row solves are folded into another solve (not for global-memory groups)
     if (rank == 0)
-        make_shape<N>(s, it.lv, tlog, rows_log(KIND), KIND != kMemGroup, KIND != kMemGroup, P.bc != 0);
+        make_shape<N>(s, it.lv, tlog, rows_log(KIND), KIND != kMemGroup, KIND != kMemGroup, P.bc != 0, WARP);
     gsync<WARP>(gm);
     const Layout lay = make_layout(N, it.lv, true, KIND, tlog);
     Consts<double>* cd = reinterpret_cast<Consts<double>*>(base + lay.cd);
@@ -1749,6 +1886,7 @@ __device__ void solve_item_mixed(const SolveArgs& a, const Item& it, unsigned ch
         pcr_setup_mem<N, float>(s, tabd, *cd, lu, reinterpret_cast<double*>(base + lay.scr), rank, gsize, gm);
     } else {
         pcr_setup<N, float, RMAX, float>(s, tabd, *cd, lu, rank, gsize, gm);
+        dense_setup<N>(s, tabd, *cd, lu, rank, gsize);
     }
     gsync<WARP>(gm);  // the FP32 tables and constants are complete
     // 2. H = F(G)/V^2 on the rate grid (payoff differences in FP64), Z from the state or zero
@@ -1801,66 +1939,107 @@ __device__ void solve_item_mixed(const SolveArgs& a, const Item& it, unsigned ch
     // a Dirichlet rate axis of one row leaves no Inner node: F is 0 everywhere
     bool all_dir = false;
     for (int i = 0; i < N - 1; ++i) all_dir |= ((s.dmask >> i) & 1) && s.M[i] == 1;
+    // The group's nodes stay in registers through a phase: lane `rank` holds
+    // t = rank and, when the grid has more nodes than the group has lanes,
+    // t = rank + gsize (a warp group has at least half as many lanes as its
+    // grid has nodes: the host sizes it so).
+    const bool two = L > gsize;
     for (int n = 0; n < a.steps; ++n) {
 #pragma unroll 1
         for (int ph = 0; ph < 4; ++ph) {
-            // a lane's nodes two at a time; a node that is unused or holds
-            // Dirichlet data (eq. bound1_0: its far neighbour is not stored) is
-            // evaluated as node 0 (always Inner when any node is) and discarded
-            for (int tb = rank; tb < L; tb += 2 * gsize) {
-                int t[2] = {tb, tb + gsize};
-                bool use[2];
+            // the stencil for both nodes at once; a node that is unused or
+            // holds Dirichlet data (eq. bound1_0: its far neighbour is not
+            // stored) is evaluated as node 0 (always Inner when any node is)
+            // and discarded
+            int t[2] = {rank, rank + gsize};
+            bool use[2];
 #pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    use[k] = t[k] < L && !dirichlet_node(s, t[k]);
-                    if (!use[k]) t[k] = 0;
-                }
-                int J[2] = {s.padded(t[0]), s.padded(t[1])};
-                float acc[2] = {0.f, 0.f};
-                if ((use[0] || use[1]) && !all_dir) {
-                    if (ph == 0) stencil_act2(A, tabk, cV, t, J, DFSrc{ZZ}, acc, DR, Lp);
-                    else stencil_act2(A, tabk, cV, t, J, ArrSrc<float>{ph == 2 ? K1 : Kw}, acc, DR, Lp);
-                }
+            for (int k = 0; k < 2; ++k) {
+                use[k] = t[k] < L && !dirichlet_node(s, t[k]);
+                if (!use[k]) t[k] = 0;
+            }
+            int J[2] = {s.padded(t[0]), s.padded(t[1])};
+            float acc[2] = {0.f, 0.f};
+            if ((use[0] || use[1]) && !all_dir) {
+                if (ph == 0) stencil_act2(A, tabk, cV, t, J, DFSrc{ZZ}, acc, DR, Lp);
+                else stencil_act2(A, tabk, cV, t, J, ArrSrc<float>{ph == 2 ? K1 : Kw}, acc, DR, Lp);
+            }
+            // the right-hand side of the phase's solves (its own node only):
+            // ph 0: dt F(Y_n); ph 1 and 3: the refinement 2 k - k_prev + theta dt A k;
+            // ph 2: the second stage's right-hand side (kept in K0 for ph 3)
+            float x[2];
 #pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    const int tk = tb + k * gsize;
-                    if (tk >= L) continue;
-                    const int Jk = use[k] ? J[k] : s.padded(tk);
-                    const float vv = v2[(t[k] >> shV) & mV];
-                    float out;
-                    if (ph == 0) {
-                        out = use[k] ? dt * vv * (H[t[k] & Lr1] + acc[k]) : 0.f;
-                        FY[Jk] = out;
-                    } else if (ph == 2) {
-                        out = use[k] ? FY[Jk] + a21dt * vv * acc[k] + (float)kQ21 * K1[Jk] : 0.f;
-                    } else {
-                        out = use[k] ? 2.f * K0[Jk] - Kw[Jk] + thdt * vv * acc[k] : 0.f;
-                    }
-                    K0[Jk] = out;
+            for (int k = 0; k < 2; ++k) {
+                const int tk = rank + k * gsize;
+                x[k] = 0.f;
+                if (tk >= L || !use[k]) continue;
+                const int Jk = J[k];
+                const float vv = v2[(tk >> shV) & mV];
+                if (ph == 0) {
+                    x[k] = dt * vv * (H[tk & Lr1] + acc[k]);
+                    FY[Jk] = x[k];
+                } else if (ph == 1) {
+                    x[k] = 2.f * FY[Jk] - Kw[Jk] + thdt * vv * acc[k];
+                } else if (ph == 2) {
+                    x[k] = FY[Jk] + a21dt * vv * acc[k] + (float)kQ21 * K1[Jk];
+                    K0[Jk] = x[k];
+                } else {
+                    x[k] = 2.f * K0[Jk] - Kw[Jk] + thdt * vv * acc[k];
                 }
             }
-            gsync<WARP>(gm);
-            // directional solves (single-row axes folded into the solve along
-            // `last`): the first from K0 into the phase's target, the rest in place
+            // directional solves in ascending axis order (single-row axes
+            // folded into the solve along `last`): axes of 2..8 rows by their
+            // explicit inverses in registers, longer ones by the line solve
+            // through shared memory, in place in the phase's target
             float* dst = (ph == 1) ? K1 : (ph == 3 ? K0 : Kw);
-            const float* src = K0;
+            bool in_smem = false;  // the values live in dst, not in x
 #pragma unroll 1
             for (int ax = 0; ax < N; ++ax) {
                 if ((s.skip >> ax) & 1) continue;
-                if (ph == 3 && ax == last) {
-                    auto epi = [=](int J, float x) {
-                        Z[J] = fma(kB2, (double)x, fma(kB1, (double)K1[J], Z[J]));
-                        ZZ[J] = ff_axpy(ff_axpy(ZZ[J], (float)kB1, K1[J]), (float)kB2, x);
-                    };
-                    if constexpr (KIND == kMemGroup) sweep_mem<N, float>(s, ax, lu, src, dst, rank, gsize, gm, epi);
-                    else sweep<N, float, RMAX>(s, ax, lu, src, dst, rank, gsize, gm, epi);
+                if ((s.dense >> ax) & 1) {
+                    if (in_smem) {
+#pragma unroll
+                        for (int k = 0; k < 2; ++k) {
+                            const int tk = rank + k * gsize;
+                            if (tk < L) x[k] = dst[s.padded(tk)];
+                        }
+                        in_smem = false;
+                    }
+                    const float* C = lu + s.luoff[ax];
+                    const int sha = s.sh[ax], Ma = s.M[ax];
+                    const bool rate = ax < N - 1;
+                    if (Ma == 2) dense_mix<2>(C, sha, shV, mV, rate, rank, gsize, tlog, two, gm, x);
+                    else if (Ma == 4) dense_mix<4>(C, sha, shV, mV, rate, rank, gsize, tlog, two, gm, x);
+                    else dense_mix<8>(C, sha, shV, mV, rate, rank, gsize, tlog, two, gm, x);
                 } else {
-                    if constexpr (KIND == kMemGroup) sweep_mem<N, float>(s, ax, lu, src, dst, rank, gsize, gm, NoEpi());
-                    else sweep<N, float, RMAX>(s, ax, lu, src, dst, rank, gsize, gm, NoEpi());
+                    if (!in_smem) {
+#pragma unroll
+                        for (int k = 0; k < 2; ++k) {
+                            const int tk = rank + k * gsize;
+                            if (tk < L) dst[s.padded(tk)] = x[k];
+                        }
+                        gsync<WARP>(gm);
+                        in_smem = true;
+                    }
+                    sweep<N, float, RMAX>(s, ax, lu, dst, dst, rank, gsize, gm, NoEpi());
+                    gsync<WARP>(gm);
                 }
-                gsync<WARP>(gm);
-                src = dst;
             }
+            // the phase's result, and at the end of a step the update
+            // Z_{n+1} = Z_n + b1 k1 + b2 k2 (FP64 and its float-float copy)
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int tk = rank + k * gsize;
+                if (tk >= L) continue;
+                const int Jk = s.padded(tk);
+                const float xk = in_smem ? dst[Jk] : x[k];
+                if (!in_smem) dst[Jk] = xk;
+                if (ph == 3) {
+                    Z[Jk] = fma(kB2, (double)xk, fma(kB1, (double)K1[Jk], Z[Jk]));
+                    ZZ[Jk] = ff_axpy(ff_axpy(ZZ[Jk], (float)kB1, K1[Jk]), (float)kB2, xk);
+                }
+            }
+            gsync<WARP>(gm);
         }
     }
 
