@@ -133,7 +133,10 @@ def profile_once(args):
         return
     wl = WORKLOADS[args.workload]
     B = args.batch or wl["batch"]
-    b = L.Batch(workload_batch(args.workload, B))
+    insts = workload_batch(args.workload, B)
+    if args.global_grids:
+        insts = [dict(x, global_grids=True) for x in insts]
+    b = L.Batch(insts)
     b.set_kappa_max(0.0)
     out = torch.zeros(B, dtype=torch.float64, device="cuda")
     b.run(out.data_ptr())

@@ -174,9 +174,16 @@ AMFRW_HD Layout make_layout(int N, const int8_t* lv, bool mixed, int kind, int t
     y.npay = 2 * npay;
     int llog = 0;
     for (int i = 0; i < N; ++i) llog += lv[i];
+    // Mixed-precision warp groups fold the single-row axes into another
+    // axis's solve (all rate axes of one row; the V axis of one row when a
+    // rate axis has more) and store no factors for them.
+    const bool dense = mixed && kind == kWarpGroup;
+    bool rate_rows = false;
+    for (int i = 0; i < N - 1; ++i) rate_rows |= lv[i] > 0;
     int nlu = 0;
     for (int i = 0; i < N; ++i) {
         const int rows = (i < N - 1 ? MV : 1) << lv[i];  // classes x rows
+        if (dense && lv[i] == 0 && (i < N - 1 || rate_rows)) continue;
         if (dense_axis(kind, mixed, 1 << lv[i])) {
             nlu = (nlu + 3) & ~3;
             nlu += rows << lv[i];

@@ -104,20 +104,6 @@ __device__ __forceinline__ void make_shape(Shape<N>& s, const int8_t* lv, int tl
     s.toff[N - 1] = o;
     s.poff[N - 1] = po;
     s.phalf = po;
-    s.dense = 0;
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-        // (the same sizes as make_layout's line-solve region)
-        const bool dn = dense && s.M[i] >= 2 && s.M[i] <= kDenseMaxRows;
-        s.plog[i] = lanes_log(s.lv[i], sh, tlog, rlog);
-        s.luS[i] = dn ? s.M[i] : lu_row_values(s.plog[i]);
-        if (dn) {
-            s.dense |= 1 << i;
-            lo = (lo + 3) & ~3;
-        }
-        s.luoff[i] = lo;
-        lo += ((i < N - 1 ? s.M[N - 1] : 1) << s.lv[i]) * s.luS[i];
-    }
     s.skip = 0;
     s.last = N - 1;
     int lastr = -1;  // the last rate axis with more than one row
@@ -129,6 +115,21 @@ __device__ __forceinline__ void make_shape(Shape<N>& s, const int8_t* lv, int tl
     if (fold && fold_v && s.M[N - 1] == 1 && lastr >= 0) {
         s.skip |= 1 << (N - 1);
         s.last = lastr;
+    }
+    s.dense = 0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        // (the same sizes as make_layout's line-solve region; with `dense`
+        // the folded single-row axes, never solved on their own, get none)
+        const bool dn = dense && s.M[i] >= 2 && s.M[i] <= kDenseMaxRows;
+        s.plog[i] = lanes_log(s.lv[i], sh, tlog, rlog);
+        s.luS[i] = dn ? s.M[i] : lu_row_values(s.plog[i]);
+        if (dn) {
+            s.dense |= 1 << i;
+            lo = (lo + 3) & ~3;
+        }
+        s.luoff[i] = lo;
+        if (!(dense && ((s.skip >> i) & 1))) lo += ((i < N - 1 ? s.M[N - 1] : 1) << s.lv[i]) * s.luS[i];
     }
 }
 
@@ -669,7 +670,8 @@ __device__ void pcr_setup(const Shape<N>& s, const double* tabd, const Consts<do
                           int rank, int gsize, unsigned gm)
 {
     for (int axis = 0; axis < N; ++axis) {
-        if ((s.dense >> axis) & 1) continue;  // factored by dense_setup
+        // axes folded into another solve have no factors; dense_setup factors the dense ones
+        if (((s.skip | s.dense) >> axis) & 1) continue;
         const int M = s.M[axis];
         const int plog = s.plog[axis];
         const int P = 1 << plog;
