@@ -214,6 +214,20 @@ InstDev to_device(const amfrw_params* p)
     I.theta = p->theta;
     I.nu = p->nu_amf;
     I.dt = p->T / (double)p->n_steps;
+    // level-free constant factors, in the operation order of the kernels'
+    // per-grid formulas with h replaced by Fmax (products by powers of two
+    // are exact, so the scaled values equal the direct ones bit for bit)
+    const int N = I.N;
+    const double Vm = I.Fmax[N - 1];
+    I.cVb = 0.5 * I.sigma * I.sigma / (Vm * Vm);
+    for (int i = 0; i < N - 1; ++i) {
+        const double Fm = I.Fmax[i];
+        I.dcb[i] = 0.5 * I.alpha[i] * I.alpha[i] * I.rho[i * kMaxDim + i] / (Fm * Fm);
+        I.smb[i] = I.sigma * I.phi[i] / (4.0 * Fm * Vm);
+        for (int k = i + 1; k < N - 1; ++k)
+            I.rmb[upair(i, k)] = I.rho[i * kMaxDim + k] / (4.0 * Fm * I.Fmax[k]);
+    }
+    for (int i = 0; i < N; ++i) I.g2b[i] = 1.0 / (2.0 * I.Fmax[i]);
     return I;
 }
 

@@ -24,6 +24,15 @@ struct InstDev {
     double rho[kMaxDim * kMaxDim];  // rate correlations, leading dimension 8
     double sigma, beta, V0, K, T, discount, theta, nu, dt;
     double pad2;
+    // The level-free factors of a grid's constants, computed once per
+    // instance: h_i = Fmax_i 2^-l_i exactly, so every constant of a grid is
+    // one of these times an exact power of two (the same FP64 value as
+    // dividing by the grid's h directly).
+    double cVb;                                // sigma^2 / (2 Vmax^2), times 4^l_V
+    double dcb[kMaxDim];                       // alpha_a^2 rho_aa / (2 Fmax_a^2), times 4^l_a
+    double rmb[kMaxDim * (kMaxDim - 1) / 2];   // rho_ik / (4 Fmax_i Fmax_k), times 2^(l_i + l_k)
+    double smb[kMaxDim];                       // sigma phi_i / (4 Fmax_i Vmax), times 2^(l_i + l_V)
+    double g2b[kMaxDim];                       // 1 / (2 Fmax_i), times 2^l_i
 };
 
 // One component grid of one instance: the unit of work of the solver.

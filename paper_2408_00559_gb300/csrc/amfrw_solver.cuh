@@ -1208,54 +1208,61 @@ __device__ __forceinline__ void gsync(unsigned gm)
 }
 
 // --------------------------------------------------------- table building
+// Exact power of two 2^e (|e| < 1023).
+__device__ __forceinline__ double pow2(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
+
+// Coefficient and payoff tables of the grid and its constants.  The table
+// entries of all axes are spread over the group's lanes at once (an entry
+// divides once and takes a square root), and each constant is the instance's
+// level-free factor times an exact power of two (no division per grid).
 template <int N>
 __device__ void build_tables(const Shape<N>& s, const InstDev& P, double* tabd, double* pay,
                              Consts<double>* cd, int rank, int gsize)
 {
     const double beta = P.beta;
-    for (int a = 0; a < N - 1; ++a) {
+    const bool half = beta == 0.5;  // F^beta by a square root (the usual SABR choice)
+    int nrate = 0;                  // rate entries: j = 0..M_a per axis
+#pragma unroll
+    for (int a = 0; a < N - 1; ++a) nrate += s.M[a] + 1;
+    const int MV = s.M[N - 1];
+    for (int w = rank; w < nrate + MV; w += gsize) {
+        if (w >= nrate) {
+            const int jj = w - nrate + 1;
+            const double V = (double)jj * (P.Fmax[N - 1] / (double)MV);
+            tabd[s.toff[N - 1] + jj - 1] = V * V;
+            continue;
+        }
+        int a = 0, jj = w;
+        while (jj > s.M[a]) {
+            jj -= s.M[a] + 1;
+            ++a;
+        }
         const int M = s.M[a];
         const double h = P.Fmax[a] / (double)M;
         const double al = P.alpha[a], ta = P.tau[a];
-        const double dcoef = 0.5 * al * al * P.rho[a * kMaxDim + a] / (h * h);
-        for (int jj = rank; jj <= M; jj += gsize) {
-            const double F = (double)jj * h;
-            const double bF = 1.0 / (1.0 + ta * F);  // discount factor of the accrual period
-            pay[s.poff[a] + jj] = (P.payoff == 0) ? (F - P.K) : ta * (F - P.K);
-            pay[s.phalf + s.poff[a] + jj] = bF;
-            if (jj >= 1) {
-                // F^beta and F^(2 beta); beta = 1/2 (the usual SABR choice) by a square root
-                const bool half = beta == 0.5;
-                const double Fb = half ? sqrt(F) : pow(F, beta);
-                const double F2b = half ? F : pow(F, 2.0 * beta);
-                tabd[s.toff[a] + jj - 1] = dcoef * F2b;
-                tabd[s.toff[a] + M + jj - 1] = al * Fb;
-                tabd[s.toff[a] + 2 * M + jj - 1] = al * ta * Fb * bF;
-            }
+        const double F = (double)jj * h;
+        const double bF = 1.0 / (1.0 + ta * F);  // discount factor of the accrual period
+        pay[s.poff[a] + jj] = (P.payoff == 0) ? (F - P.K) : ta * (F - P.K);
+        pay[s.phalf + s.poff[a] + jj] = bF;
+        if (jj >= 1) {
+            const double dcoef = P.dcb[a] * pow2(2 * s.lv[a]);  // alpha^2 rho_aa / (2 h^2)
+            const double Fb = half ? sqrt(F) : pow(F, beta);
+            const double F2b = half ? F : pow(F, 2.0 * beta);
+            tabd[s.toff[a] + jj - 1] = dcoef * F2b;
+            tabd[s.toff[a] + M + jj - 1] = al * Fb;
+            tabd[s.toff[a] + 2 * M + jj - 1] = al * ta * Fb * bF;
         }
     }
-    {
-        const int MV = s.M[N - 1];
-        const double hV = P.Fmax[N - 1] / (double)MV;
-        for (int jj = 1 + rank; jj <= MV; jj += gsize) {
-            const double V = (double)jj * hV;
-            tabd[s.toff[N - 1] + jj - 1] = V * V;
-        }
-    }
-    // the constants, one entry per lane at a time (each entry divides once)
+    // the constants, one entry per lane at a time
     constexpr int kPairs = kMaxDim * (kMaxDim - 1) / 2, kTri = kMaxDim * (kMaxDim + 1) / 2;
     constexpr int kConsts = 1 + kPairs + kTri + 2 * kMaxDim;
-    auto hh = [&](int i) {  // h_i = Fmax_i / M_i, by an exact power of two
-        return P.Fmax[i] * __longlong_as_double((long long)(1023 - s.lv[i]) << 52);
-    };
     for (int q = rank; q < kConsts; q += gsize) {
         if (q == 0) {
-            const double hV = hh(N - 1);
-            cd->cV = 0.5 * P.sigma * P.sigma / (hV * hV);
+            cd->cV = P.cVb * pow2(2 * s.lv[N - 1]);  // sigma^2 / (2 h_V^2)
             cd->dt = P.dt;
             cd->thdt = P.theta * P.dt;
             cd->nudt = P.nu * P.dt;
-        } else if (q <= kPairs) {  // rm[upair(i, k)], i < k
+        } else if (q <= kPairs) {  // rm[upair(i, k)] = rho_ik / (4 h_i h_k), i < k
             int i = 0, r = q - 1;
             while (r >= kMaxDim - 1 - i) {
                 r -= kMaxDim - 1 - i;
@@ -1263,7 +1270,7 @@ __device__ void build_tables(const Shape<N>& s, const InstDev& P, double* tabd, 
             }
             const int k = i + 1 + r;
             const bool ok = i < N - 1 && k < N - 1;
-            cd->rm[upair(i, k)] = ok ? P.rho[i * kMaxDim + k] / (4.0 * hh(i) * hh(k)) : 0.0;
+            cd->rm[upair(i, k)] = ok ? P.rmb[upair(i, k)] * pow2(s.lv[i] + s.lv[k]) : 0.0;
         } else if (q <= kPairs + kTri) {  // rh[ltri(i, r)], r <= i
             int i = 0, r = q - 1 - kPairs;
             while (r > i) {
@@ -1271,12 +1278,12 @@ __device__ void build_tables(const Shape<N>& s, const InstDev& P, double* tabd, 
                 ++i;
             }
             cd->rh[ltri(i, r)] = (i < N - 1) ? P.rho[i * kMaxDim + r] : 0.0;
-        } else if (q <= kPairs + kTri + kMaxDim) {
+        } else if (q <= kPairs + kTri + kMaxDim) {  // sigma phi_i / (4 h_i h_V)
             const int i = q - 1 - kPairs - kTri;
-            cd->sm[i] = (i < N - 1) ? P.sigma * P.phi[i] / (4.0 * hh(i) * hh(N - 1)) : 0.0;
-        } else {
+            cd->sm[i] = (i < N - 1) ? P.smb[i] * pow2(s.lv[i] + s.lv[N - 1]) : 0.0;
+        } else {  // 1 / (2 h_i)
             const int i = q - 1 - kPairs - kTri - kMaxDim;
-            cd->g2[i] = (i < N) ? 1.0 / (2.0 * hh(i)) : 0.0;
+            cd->g2[i] = (i < N) ? P.g2b[i] * pow2(s.lv[i]) : 0.0;
         }
     }
 }
