@@ -227,7 +227,10 @@ InstDev to_device(const amfrw_params* p)
         for (int k = i + 1; k < N - 1; ++k)
             I.rmb[upair(i, k)] = I.rho[i * kMaxDim + k] / (4.0 * Fm * I.Fmax[k]);
     }
-    for (int i = 0; i < N; ++i) I.g2b[i] = 1.0 / (2.0 * I.Fmax[i]);
+    for (int i = 0; i < N; ++i) {
+        I.g2b[i] = 1.0 / (2.0 * I.Fmax[i]);
+        I.xs[i] = ((i < N - 1) ? I.F0[i] : I.V0) / I.Fmax[i];
+    }
     return I;
 }
 

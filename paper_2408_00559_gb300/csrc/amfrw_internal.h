@@ -33,6 +33,7 @@ struct InstDev {
     double rmb[kMaxDim * (kMaxDim - 1) / 2];   // rho_ik / (4 Fmax_i Fmax_k), times 2^(l_i + l_k)
     double smb[kMaxDim];                       // sigma phi_i / (4 Fmax_i Vmax), times 2^(l_i + l_V)
     double g2b[kMaxDim];                       // 1 / (2 Fmax_i), times 2^l_i
+    double xs[kMaxDim];                        // spot over Fmax: F_i(0) / Fmax_i, V0 / Vmax (times M_i: x*/h_i)
 };
 
 // One component grid of one instance: the unit of work of the solver.
