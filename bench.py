@@ -585,6 +585,8 @@ def run_ours(args, rank, world, local_rank):
     kernel_ms = float(np.mean([sum(ms for (_, ms, _) in kt) for kt in ktimes]))
     roof = roofline_entry(insts, kernel_ms, peak64, peak32, wl["mixed"])
     roof["solver_launches_per_batch"] = launches_per_batch
+    roof["launch_ms"] = [{"N": int(kt[0]), "ms": round(float(np.mean([k[q][1] for k in ktimes])), 3)}
+                         for q, kt in enumerate(ktimes[0])]
     if name == "c4" and B == 256 and launches_per_batch == 3 and not args.global_grids:
         roof["traffic"] = C4_DRAM_BYTES_PER_BATCH
         roof["traffic_note"] = ("DRAM bytes of the batch's three solver launches, one ncu capture: "

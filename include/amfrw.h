@@ -196,13 +196,13 @@ int amfrw_batch_launches(const amfrw_batch *b, int32_t *n_launches);
 
 /* Kernel timing (tracing).  With timing on, every amfrw_batch_run records a
  * CUDA event pair around each solver launch: one persistent multi-class
- * launch per precision for all grids of at most 64 Inner nodes (when that
- * strategy is selected), and one launch per remaining (N, precision, grid
- * class).  amfrw_batch_kernel_times synchronises and writes, for the last
- * run, the device milliseconds of each solver launch to ms_out[0..*n_out-1]
- * (at most cap entries), the Inner-node-steps it advanced (sum over its grids
- * of Inner nodes x steps) to node_steps_out (may be NULL) and its N (0 for a
- * multi-class launch) to dims_out (may be NULL). */
+ * launch per (N, precision) for all grids of at most 64 Inner nodes (when
+ * that strategy is selected), and one launch per remaining (N, precision,
+ * grid class).  amfrw_batch_kernel_times synchronises and writes, for the
+ * last run, the device milliseconds of each solver launch to
+ * ms_out[0..*n_out-1] (at most cap entries), the Inner-node-steps it advanced
+ * (sum over its grids of Inner nodes x steps) to node_steps_out (may be NULL)
+ * and its N to dims_out (may be NULL). */
 int amfrw_batch_enable_timing(amfrw_batch *b, int32_t on);
 int amfrw_batch_kernel_times(amfrw_batch *b, float *ms_out, double *node_steps_out,
                              int32_t *dims_out, int32_t cap, int32_t *n_out);

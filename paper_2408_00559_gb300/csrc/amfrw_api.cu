@@ -1459,7 +1459,7 @@ int amfrw_batch_kernel_times(amfrw_batch* b, float* ms_out, double* node_steps_o
             const LaunchClass& L = P.classes[c];
             for (int k = L.item_begin; k < L.item_begin + L.item_count; ++k)
                 s += (double)P.items[k].L * (double)P.insts[P.items[k].inst].n_steps;
-            dim = (cls.size() == 1) ? L.N : 0;
+            dim = L.N;  // a launch's classes share N
         }
         if (node_steps_out) node_steps_out[r] = s;
         if (dims_out) dims_out[r] = dim;

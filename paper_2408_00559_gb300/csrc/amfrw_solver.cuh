@@ -1997,8 +1997,10 @@ __device__ void solve_item_mixed(const SolveArgs& a, const Item& it, unsigned ch
                 if (!use[k]) t[k] = 0;
             }
             int J[2] = {s.padded(t[0]), s.padded(t[1])};
-            float acc[2] = {0.f, 0.f};
-            if ((use[0] || use[1]) && !all_dir) {
+            float acc[2];
+            const bool eval = (use[0] || use[1]) && !all_dir;
+            acc[0] = acc[1] = 0.f;
+            if (eval) {
                 if (ph == 0) stencil_act2(A, tabk, cV, t, J, DFSrc{ZZ}, acc, DR, Lp);
                 else stencil_act2(A, tabk, cV, t, J, ArrSrc<float>{ph == 2 ? K1 : Kw}, acc, DR, Lp);
             }
