@@ -72,9 +72,10 @@ WORKLOADS = {
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of the solver launches of one 256-instance batched
 # mixed-precision batch in its multi-class configuration (one launch per N):
-# one ncu capture, dram__bytes_read.sum 540 416 + 1 752 064 + 7 318 016 and
-# dram__bytes_write.sum 0 + 0 + 45 548 288 for N = 4, 6, 8.
-C4_DRAM_BYTES_PER_BATCH = 540416 + 1752064 + 7318016 + 45548288
+# one ncu capture, dram__bytes_read.sum 680 448 + 4 588 544 + 12 539 392 and
+# dram__bytes_write.sum 0 + 292 096 + 200 052 224 for N = 4, 6, 8 (the writes:
+# local-memory stack frames of the per-grid setup calls written back from L2).
+C4_DRAM_BYTES_PER_BATCH = 680448 + 4588544 + 12539392 + 292096 + 200052224
 
 
 def parse():

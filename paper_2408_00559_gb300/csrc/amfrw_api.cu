@@ -594,9 +594,11 @@ int build_warp_launches(Plan& P)
             d.glog = L.glog;
             d.item_begin = L.item_begin;
             d.item_count = L.item_count;
-            d.smem_group = L.smem_group;
             d.qidx = c;
-            // the group's shared memory for a width of 2^g lanes
+            // the group's shared memory for a width of 2^g lanes, padded so
+            // that the groups sharing a warp start 128 / (groups per warp)
+            // bytes apart modulo 128: their lanes, which touch nearby words of
+            // their own grids, then fall into different banks
             auto group_smem = [&](int g) {
                 int sg = 0;
                 for (int q = L.item_begin; q < L.item_begin + L.item_count; ++q) {
@@ -604,15 +606,14 @@ int build_warp_launches(Plan& P)
                         continue;  // equal shapes are adjacent
                     sg = std::max(sg, make_layout(L.N, P.items[q].lv, L.mixed, kWarpGroup, g).total);
                 }
+                const int gpw = 32 >> g;
+                if (gpw > 1) sg += ((128 / gpw) - sg % 128 + 128) % 128;
                 return sg;
             };
             // the tuned width: more lanes per grid, so more lanes per line (one
             // more PCR level, fewer Thomas rows) and fewer nodes per lane
-            const int g0 = std::min(5, d.glog + P.glog_delta);
-            if (g0 != d.glog) {
-                d.glog = g0;
-                d.smem_group = group_smem(g0);
-            }
+            d.glog = std::min(5, d.glog + P.glog_delta);
+            d.smem_group = group_smem(d.glog);
             while (d.glog < 5 && ((int64_t)d.smem_group << (5 - d.glog)) > budget) {
                 ++d.glog;
                 d.smem_group = group_smem(d.glog);
