@@ -179,8 +179,26 @@ void amfrw_problem_destroy(amfrw_problem *h);
 
 /* Price n independent instances in one go: upload, one persistent launch per
  * kernel class over all their component grids, combination, download.
- * prices_out: host array [n].  Synchronises.  Errors as create/combine. */
+ * prices_out: host array [n].  Synchronises.  Errors as create/combine.
+ * Plan reuse: the calling thread keeps the batch of its last call (grid
+ * list, device buffers, captured graph; about what amfrw_batch_create
+ * allocates).  A following call on the same device and stream whose
+ * instances have, one by one, the same n_rates, payoff, n_steps, level, psi,
+ * full_grid, precision and flags validates its parameters, uploads only the
+ * instance records and replays the graph; any other call releases it and
+ * plans afresh.  amfrw_solve_batch_release frees it (so does thread exit).
+ * After an ECUDA error nothing is kept. */
 int amfrw_solve_batch(const amfrw_params *ps, int32_t n, double *prices_out, void *cuda_stream);
+
+/* Bytes the calling thread's last amfrw_solve_batch call copied host->device
+ * (everything a fresh plan uploads, or the instance records alone when the
+ * plan was reused) and device->host (prices and the non-finite flag); 0
+ * before any call.  Errors: EINVAL (NULL). */
+int amfrw_solve_batch_io(int64_t *h2d_bytes, int64_t *d2h_bytes);
+
+/* Free the plan amfrw_solve_batch keeps for the calling thread (no-op if
+ * none). */
+void amfrw_solve_batch_release(void);
 
 /* The same split in two: amfrw_batch_create validates, enumerates and uploads
  * everything once; amfrw_batch_run prices all instances with device-resident

@@ -36,7 +36,8 @@ EXPORTS = [
     "amfrw_surrogate_save",
     "amfrw_surrogate_load", "amfrw_surrogate_params", "amfrw_surrogate_grad",
     "amfrw_surrogate_destroy", "amfrw_surrogate_last_error", "amfrw_peak_probe",
-    "amfrw_batch_set_kappa_max", "amfrw_batch_promoted",
+    "amfrw_batch_set_kappa_max", "amfrw_batch_promoted", "amfrw_solve_batch_io",
+    "amfrw_solve_batch_release",
 ]
 SURROGATE_PARAMS = 136193
 
@@ -84,6 +85,9 @@ def lib():
         L.amfrw_problem_destroy.argtypes = [vp]
         L.amfrw_problem_destroy.restype = None
         L.amfrw_solve_batch.argtypes = [pp, C.c_int32, C.POINTER(C.c_double), vp]
+        L.amfrw_solve_batch_io.argtypes = [C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+        L.amfrw_solve_batch_release.argtypes = []
+        L.amfrw_solve_batch_release.restype = None
         L.amfrw_batch_create.argtypes = [pp, C.c_int32, vp, C.POINTER(vp)]
         L.amfrw_batch_run.argtypes = [vp, vp]
         L.amfrw_batch_launches.argtypes = [vp, C.POINTER(C.c_int32)]
@@ -246,6 +250,18 @@ def solve_batch(insts: list[dict], stream=None) -> np.ndarray:
     _check(lib().amfrw_solve_batch(m.arr, len(insts), _dp(out), _stream_ptr(stream)),
            "amfrw_solve_batch")
     return out
+
+
+def solve_batch_io() -> tuple[int, int]:
+    """amfrw_solve_batch_io: (host->device, device->host) bytes of this thread's last solve_batch."""
+    h, d = C.c_int64(), C.c_int64()
+    _check(lib().amfrw_solve_batch_io(C.byref(h), C.byref(d)), "amfrw_solve_batch_io")
+    return h.value, d.value
+
+
+def solve_batch_release() -> None:
+    """amfrw_solve_batch_release: free the plan solve_batch keeps for this thread."""
+    lib().amfrw_solve_batch_release()
 
 
 class Batch:

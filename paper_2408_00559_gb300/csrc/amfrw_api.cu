@@ -1488,14 +1488,122 @@ int amfrw_batch_launches(const amfrw_batch* b, int32_t* n_launches)
 
 void amfrw_batch_destroy(amfrw_batch* b) { delete b; }
 
+}  // extern "C"
+
+namespace {
+
+// amfrw_solve_batch keeps, per calling thread, the batch of its last call:
+// grid list, device buffers and captured graph depend only on the instances'
+// shapes, the stream and the device, so a following call with the same
+// shapes validates and uploads the new parameter records and replays the
+// graph.  Released by amfrw_solve_batch_release, by a call with other
+// shapes, or at thread exit.
+struct SolveKey {
+    int32_t n_rates, payoff, n_steps, level, psi, full_grid, precision, flags;
+    bool operator==(const SolveKey& o) const { return memcmp(this, &o, sizeof(SolveKey)) == 0; }
+};
+
+struct SolveCache {
+    amfrw_batch* b = nullptr;
+    int dev = -1;
+    void* stream = nullptr;
+    std::vector<SolveKey> key;
+    InstDev* stage = nullptr;  // pinned copy of the instance records (both plans)
+    int64_t h2d = 0, d2h = 0;  // bytes the last call copied
+    void drop()
+    {
+        if (b) amfrw_batch_destroy(b);
+        if (stage) cudaFreeHost(stage);
+        b = nullptr;
+        stage = nullptr;
+        key.clear();
+    }
+    ~SolveCache() { drop(); }
+};
+thread_local SolveCache g_solve_cache;
+
+SolveKey solve_key(const amfrw_params& p)
+{
+    SolveKey k;
+    memset(&k, 0, sizeof(k));
+    k.n_rates = p.n_rates;
+    k.payoff = p.payoff;
+    k.n_steps = p.n_steps;
+    k.level = p.level;
+    k.psi = p.psi;
+    k.full_grid = p.full_grid != 0;
+    k.precision = p.precision;
+    k.flags = p.flags;
+    return k;
+}
+
+// New parameter records into a plan whose grids are those of `ps`
+// (precision forced to FP64 for the re-solve plan), copied to the device
+// from the pinned array `stage` [n].
+int refresh_insts(Plan& P, const amfrw_params* ps, int n, bool fp64, InstDev* stage, int64_t& bytes)
+{
+    for (int i = 0; i < n; ++i) {
+        amfrw_params q = ps[i];
+        if (fp64) q.precision = AMFRW_FP64;
+        InstDev I = to_device(&q);
+        I.grid_begin = P.insts[(size_t)i].grid_begin;
+        I.grid_count = P.insts[(size_t)i].grid_count;
+        P.insts[(size_t)i] = I;
+        stage[i] = I;
+    }
+    CUDA_TRY(cudaMemcpyAsync(P.d_insts, stage, sizeof(InstDev) * (size_t)n, cudaMemcpyHostToDevice, P.stream));
+    bytes += (int64_t)(sizeof(InstDev) * (size_t)n);
+    return AMFRW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 int amfrw_solve_batch(const amfrw_params* ps, int32_t n, double* prices_out, void* cuda_stream)
 {
     if (!prices_out) return fail(AMFRW_EINVAL, "prices_out is NULL");
-    amfrw_batch* b = nullptr;
-    int st = amfrw_batch_create(ps, n, cuda_stream, &b);
-    if (st != AMFRW_OK) return st;
-    Plan& P = b->plan;
-    st = amfrw_batch_run(b, P.d_prices);
+    if (n < 1 || !ps) return fail(AMFRW_EINVAL, "need at least one instance and a params array");
+    SolveCache& C = g_solve_cache;
+    std::vector<SolveKey> key((size_t)n);
+    for (int i = 0; i < n; ++i) key[(size_t)i] = solve_key(ps[i]);
+    int64_t h2d = 0;
+    int st = AMFRW_OK;
+    // (no CUDA call before the parameters are validated: a fresh plan
+    // validates first, and a kept plan exists only after a CUDA device did)
+    int dev = -1;
+    if (C.b) CUDA_TRY(cudaGetDevice(&dev));
+    const bool hit = C.b && C.dev == dev && C.stream == cuda_stream && C.key == key;
+    if (hit) {
+        for (int i = 0; i < n && st == AMFRW_OK; ++i) {
+            st = validate(ps + i);
+            if (st != AMFRW_OK) g_last_error = "instance " + std::to_string(i) + ": " + g_last_error;
+        }
+        if (st != AMFRW_OK) return st;
+        if (!C.stage && cudaMallocHost(&C.stage, 2 * sizeof(InstDev) * (size_t)n) != cudaSuccess) {
+            C.stage = nullptr;
+            C.drop();
+            return fail(AMFRW_ENOMEM, "pinned host allocation failed");
+        }
+        st = refresh_insts(C.b->plan, ps, n, false, C.stage, h2d);
+        if (st == AMFRW_OK && C.b->promo) st = refresh_insts(*C.b->promo, ps, n, true, C.stage + n, h2d);
+        if (st != AMFRW_OK) {
+            C.drop();
+            return st;
+        }
+    } else {
+        C.drop();
+        st = amfrw_batch_create(ps, n, cuda_stream, &C.b);
+        if (st != AMFRW_OK) return st;
+        CUDA_TRY(cudaGetDevice(&dev));
+        C.dev = dev;
+        C.stream = cuda_stream;
+        C.key = std::move(key);
+        int64_t d2h_unused = 0;
+        amfrw_batch_io_bytes(C.b, &h2d, &d2h_unused);
+    }
+    Plan& P = C.b->plan;
+    st = amfrw_batch_run(C.b, P.d_prices);
     if (st == AMFRW_OK) {
         int32_t flag = 0;
         cudaError_t e1 = cudaMemcpyAsync(prices_out, P.d_prices, sizeof(double) * n, cudaMemcpyDeviceToHost, P.stream);
@@ -1506,9 +1614,21 @@ int amfrw_solve_batch(const amfrw_params* ps, int32_t n, double* prices_out, voi
         else if (flag)
             st = fail(AMFRW_ENONFINITE, "a combined price is not finite");
     }
-    amfrw_batch_destroy(b);
+    C.h2d = h2d;
+    C.d2h = (int64_t)(sizeof(double) * (size_t)n + sizeof(int32_t));
+    if (st == AMFRW_ECUDA) C.drop();  // keep nothing whose state is unknown
     return st;
 }
+
+int amfrw_solve_batch_io(int64_t* h2d_bytes, int64_t* d2h_bytes)
+{
+    if (!h2d_bytes || !d2h_bytes) return fail(AMFRW_EINVAL, "NULL argument");
+    *h2d_bytes = g_solve_cache.h2d;
+    *d2h_bytes = g_solve_cache.d2h;
+    return AMFRW_OK;
+}
+
+void amfrw_solve_batch_release(void) { g_solve_cache.drop(); }
 
 }  // extern "C"
 

@@ -80,6 +80,8 @@ def test_rejects_oversized_grid(L):
 
 def test_rejects_null_arguments(L):
     assert L.amfrw_solve_batch(None, 1, None, None) == 1
+    assert L.amfrw_solve_batch_io(None, None) == 1
+    L.amfrw_solve_batch_release()  # nothing kept: a no-op
     assert L.amfrw_batch_run(None, None) == 1
     assert L.amfrw_step(None, 1) == 1
     out = C.c_void_p(1)
