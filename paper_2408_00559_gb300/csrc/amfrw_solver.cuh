@@ -1345,6 +1345,83 @@ __device__ __forceinline__ void sweeps_into(const Shape<N>& s, const TK* lu, con
     }
 }
 
+// Multilinear interpolation at the spot x* = (F_1(0), ..., V0) of Y = G + Z
+// (Sec. 5.1).  The 2^N corners of the containing cell are shared among up to
+// 32 lanes of the group (a whole warp group, or the first warp of a CTA),
+// which sum them by a shuffle reduction; corners of weight zero are skipped.
+template <int N, bool WARP>
+__device__ __forceinline__ void interp_spot(const Shape<N>& s, const InstDev& P, const double* pay,
+                                            const double* Z, double* u_out, int rank, int gsize, unsigned gm)
+{
+    const int il = gsize < 32 ? gsize : 32;
+    if (rank < il) {
+        int c[N];
+        double w[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            const double sx = P.xs[i] * (double)s.M[i];  // x / h_i, h_i = Fmax_i / M_i
+            int ci = (int)floor(sx);
+            ci = ci > s.M[i] - 1 ? s.M[i] - 1 : ci;
+            ci = ci < 0 ? 0 : ci;
+            c[i] = ci;
+            w[i] = sx - (double)ci;
+        }
+        // Corner `corner` goes to lane corner mod il, so a lane's corners
+        // share their lowest lb bits: the weight product, the payoff's
+        // running discount product and sum, and the node offset over those
+        // axes are formed once per lane, in the same order as per corner.
+        const int lb = 31 - __clz(il);
+        double wl = 1.0, Pl = 1.0, Sl = 0.0;
+        int tl = 0;
+        bool ol = false;
+        const double* Bv = pay + s.phalf;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            if (i < lb) {
+                const int bit = (rank >> i) & 1;
+                const int jj = c[i] + bit;
+                wl *= bit ? w[i] : 1.0 - w[i];
+                ol |= jj == 0;
+                tl += (jj - 1) << s.sh[i];
+                if (i < N - 1) {
+                    Pl *= Bv[s.poff[i] + jj];
+                    Sl = fma(pay[s.poff[i] + jj], Pl, Sl);
+                }
+            }
+        }
+        const int j0l = c[0] + (rank & 1);  // the caplet's rate index when axis 0 is a lane bit
+        double u = 0.0;
+        for (int corner = rank; corner < (1 << N); corner += il) {
+            double wt = wl, Pc = Pl, Sc = Sl;
+            int t = tl;
+            bool outer = ol;
+            int j0 = j0l;
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                if (i >= lb) {
+                    const int bit = (corner >> i) & 1;
+                    const int jj = c[i] + bit;
+                    wt *= bit ? w[i] : 1.0 - w[i];
+                    outer |= jj == 0;
+                    t += (jj - 1) << s.sh[i];
+                    if (i == 0) j0 = jj;
+                    if (i < N - 1) {
+                        Pc *= Bv[s.poff[i] + jj];
+                        Sc = fma(pay[s.poff[i] + jj], Pc, Sc);
+                    }
+                }
+            }
+            if (wt == 0.0) continue;
+            const double zv = outer ? 0.0 : Z[s.padded(t)];
+            const double g = (P.payoff == 0) ? fmax(pay[s.poff[0] + j0], 0.0) : fmax(Sc, 0.0);
+            u += wt * (g + zv);
+        }
+        const unsigned im = WARP ? gm : 0xffffffffu;
+        for (int off = il >> 1; off > 0; off >>= 1) u += __shfl_xor_sync(im, u, off, il);
+        if (rank == 0) *u_out = u;
+    }
+}
+
 // ------------------------------------------------------------- one grid
 template <int N, bool MIXED, int KIND>
 __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* base, int rank,
@@ -1604,77 +1681,8 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
             a.state[it.state_off + t] = payoff_at<N>(s, pay, P.payoff, j) + Z[s.padded(t)];
         }
     }
-    // 4. multilinear interpolation at the spot x* = (F_1(0), ..., V0).  The
-    // 2^N corners of the containing cell are shared among up to 32 lanes of
-    // the group (a whole warp group, or the first warp of a CTA), which sum
-    // them by a shuffle reduction; corners of weight zero are skipped.
-    const int il = gsize < 32 ? gsize : 32;
-    if (rank < il) {
-        int c[N];
-        double w[N];
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-            const double sx = P.xs[i] * (double)s.M[i];  // x / h_i, h_i = Fmax_i / M_i
-            int ci = (int)floor(sx);
-            ci = ci > s.M[i] - 1 ? s.M[i] - 1 : ci;
-            ci = ci < 0 ? 0 : ci;
-            c[i] = ci;
-            w[i] = sx - (double)ci;
-        }
-        // Corner `corner` goes to lane corner mod il, so a lane's corners
-        // share their lowest lb bits: the weight product, the payoff's
-        // running discount product and sum, and the node offset over those
-        // axes are formed once per lane, in the same order as per corner.
-        const int lb = 31 - __clz(il);
-        double wl = 1.0, Pl = 1.0, Sl = 0.0;
-        int tl = 0;
-        bool ol = false;
-        const double* Bv = pay + s.phalf;
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-            if (i < lb) {
-                const int bit = (rank >> i) & 1;
-                const int jj = c[i] + bit;
-                wl *= bit ? w[i] : 1.0 - w[i];
-                ol |= jj == 0;
-                tl += (jj - 1) << s.sh[i];
-                if (i < N - 1) {
-                    Pl *= Bv[s.poff[i] + jj];
-                    Sl = fma(pay[s.poff[i] + jj], Pl, Sl);
-                }
-            }
-        }
-        const int j0l = c[0] + (rank & 1);  // the caplet's rate index when axis 0 is a lane bit
-        double u = 0.0;
-        for (int corner = rank; corner < (1 << N); corner += il) {
-            double wt = wl, Pc = Pl, Sc = Sl;
-            int t = tl;
-            bool outer = ol;
-            int j0 = j0l;
-#pragma unroll
-            for (int i = 0; i < N; ++i) {
-                if (i >= lb) {
-                    const int bit = (corner >> i) & 1;
-                    const int jj = c[i] + bit;
-                    wt *= bit ? w[i] : 1.0 - w[i];
-                    outer |= jj == 0;
-                    t += (jj - 1) << s.sh[i];
-                    if (i == 0) j0 = jj;
-                    if (i < N - 1) {
-                        Pc *= Bv[s.poff[i] + jj];
-                        Sc = fma(pay[s.poff[i] + jj], Pc, Sc);
-                    }
-                }
-            }
-            if (wt == 0.0) continue;
-            const double zv = outer ? 0.0 : Z[s.padded(t)];
-            const double g = (P.payoff == 0) ? fmax(pay[s.poff[0] + j0], 0.0) : fmax(Sc, 0.0);
-            u += wt * (g + zv);
-        }
-        const unsigned im = WARP ? gm : 0xffffffffu;
-        for (int off = il >> 1; off > 0; off >>= 1) u += __shfl_xor_sync(im, u, off, il);
-        if (rank == 0) a.u_out[it.out_idx] = u;
-    }
+    // 4. multilinear interpolation at the spot
+    interp_spot<N, WARP>(s, P, pay, Z, a.u_out + it.out_idx, rank, gsize, gm);
     gsync<WARP>(gm);  // the group's shared memory is reused by its next grid
 }
 
@@ -1824,55 +1832,6 @@ __device__ __forceinline__ void stencil_act2(const ActAxes& A, const float* __re
     }
 }
 
-// Multilinear interpolation at the spot x* = (F_1(0), ..., V0) of Y = G + Z
-// (Sec. 5.1).  The 2^N corners of the containing cell are shared among up to
-// 32 lanes of the group (a whole warp group, or the first warp of a CTA),
-// which sum them by a shuffle reduction; corners of weight zero are skipped.
-template <int N, bool WARP>
-__device__ __forceinline__ void interp_spot(const Shape<N>& s, const InstDev& P, const double* pay,
-                                            const double* Z, double* u_out, int rank, int gsize, unsigned gm)
-{
-    const int il = gsize < 32 ? gsize : 32;
-    if (rank < il) {
-        int c[N];
-        double w[N];
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-            const double x = (i < N - 1) ? P.F0[i] : P.V0;
-            const double sx = x / P.Fmax[i] * (double)s.M[i];  // x / h_i, h_i = Fmax_i / M_i
-            int ci = (int)floor(sx);
-            ci = ci > s.M[i] - 1 ? s.M[i] - 1 : ci;
-            ci = ci < 0 ? 0 : ci;
-            c[i] = ci;
-            w[i] = sx - (double)ci;
-        }
-        double u = 0.0;
-        for (int corner = rank; corner < (1 << N); corner += il) {
-            double wt = 1.0;
-            int jj[N];
-            bool outer = false;
-#pragma unroll
-            for (int i = 0; i < N; ++i) {
-                const int bit = (corner >> i) & 1;
-                wt *= bit ? w[i] : 1.0 - w[i];
-                jj[i] = c[i] + bit;
-                outer |= jj[i] == 0;
-            }
-            if (wt == 0.0) continue;
-            double zv = 0.0;
-            if (!outer) {
-                int t = 0;
-#pragma unroll
-                for (int i = 0; i < N; ++i) t += (jj[i] - 1) << s.sh[i];
-                zv = Z[s.padded(t)];
-            }
-            u += wt * (payoff_at<N>(s, pay, P.payoff, jj) + zv);
-        }
-        const unsigned im = WARP ? gm : 0xffffffffu;
-        for (int off = il >> 1; off > 0; off >>= 1) u += __shfl_xor_sync(im, u, off, il);
-        if (rank == 0) *u_out = u;
-    }
-}
 
 // One grid in mixed precision: the F evaluations and line solves in FP32 on
 // the increments, Z accumulated in FP64 beside its hi/lo float pair, F of the
