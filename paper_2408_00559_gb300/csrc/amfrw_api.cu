@@ -398,7 +398,7 @@ int plan_host(const amfrw_params* ps, int n, bool keep_state, Plan& P)
                                          warp ? warp_group_log(llog, mixed) : 5);
                 // grids beyond shared memory, or with lines longer than the register
                 // sweeps take, keep their state in global memory
-                if (force_mem || lay.total > smem_cap || (!warp && maxlv > 5 + kRowsLogCta)) {
+                if (force_mem || lay.total > smem_cap || (!warp && maxlv > 5 + rows_log(kCtaGroup, mixed))) {
                     kind = kMemGroup;
                     lay = make_layout(N, g.lv, mixed, kind, log2i(kMemBlock));
                 }
@@ -514,7 +514,7 @@ int plan_host(const amfrw_params* ps, int n, bool keep_state, Plan& P)
             c.smem = (size_t)gmax;
             for (size_t q = k; q < e; ++q) {
                 Layout lay = make_layout(c.N, all[q].it.lv, c.mixed, kCtaGroup, log2i(b));
-                lumax = std::max<int64_t>(lumax, (int64_t)lay.nlu * (c.mixed ? 4 : 8));
+                lumax = std::max<int64_t>(lumax, (int64_t)lay.gbytes);
             }
         } else {  // global-memory groups: each block's slice holds a whole grid state
             c.block = kMemBlock;
@@ -1700,6 +1700,23 @@ int noalloc_run(const amfrw_params* ps, int n, double* d_prices_out, cudaStream_
     const int64_t o_flag = align256(o_queue + (int64_t)(sizeof(int32_t) * P.classes.size()));
     const int64_t o_desc = align256(o_flag + (int64_t)sizeof(int32_t));
     const int64_t o_lu = align256(o_desc + (int64_t)(sizeof(ClassDesc) * P.n_cdesc));
+    // the per-block slices of the CTA and global-memory classes (factors,
+    // states) take what the array has left: a class that wants more blocks
+    // than fit runs fewer (each block pulls grids from the class's queue
+    // until it is empty), down to one block per class
+    const int64_t room = (int64_t)AMFRW_NOALLOC_SCRATCH_BYTES - o_lu;
+    if (P.lu_scratch_len > room && room > 0) {
+        int64_t off = 0;
+        for (LaunchClass& c : P.classes) {
+            if (c.lu_stride > 0) {
+                const int64_t fit = (int64_t)((double)c.grid * (double)room / (double)P.lu_scratch_len);
+                c.grid = (int)std::max<int64_t>(1, std::min<int64_t>(c.grid, fit));
+            }
+            c.lu_offset = off;
+            off += c.lu_stride * c.grid;
+        }
+        P.lu_scratch_len = off;
+    }
     const int64_t total = o_lu + P.lu_scratch_len;
     if (total > (int64_t)AMFRW_NOALLOC_SCRATCH_BYTES)
         return fail(AMFRW_ETOOBIG, "problem needs " + std::to_string(total) +

@@ -52,6 +52,9 @@ struct Item {
 // this one function so they cannot disagree.
 struct Layout {
     int32_t meta, cd, cf, tabd, tabf, pay, lu, Z, ZZ, H, DR, FY, K1, K0, Kw, D, C, scr, total;
+    // CTA groups: bytes of the block's slice of global scratch (line-solve
+    // factors, and in mixed precision Z and dt F(Y_n) at offsets gZ, gFY)
+    int32_t gbytes, gZ, gFY;
     int32_t L, Lp, Lr, ntab, npay, nlu, ncoef;
 };
 
@@ -120,14 +123,19 @@ constexpr int kCtaGroup = 1;
 constexpr int kMemGroup = 2;
 
 // Rows of a line per lane in a line solve: at most 2 for warp groups (grids of
-// at most 64 Inner nodes), at most 8 for CTA groups (rows held in registers);
-// unbounded for global-memory groups (rows streamed from memory).
+// at most 64 Inner nodes), at most 8 for FP64 CTA groups and 4 for
+// mixed-precision ones (rows held in registers; mixed-precision CTA groups
+// run two blocks per SM, so 128 registers a thread), hence lines of at most
+// 256 / 128 rows there; unbounded for global-memory groups (rows streamed
+// from memory).
 constexpr int kRowsLogWarp = 1;
 constexpr int kRowsLogCta = 3;
+constexpr int kRowsLogCtaMixed = 2;
 constexpr int kRowsLogMem = 24;
-AMFRW_HD int rows_log(int kind)
+AMFRW_HD int rows_log(int kind, bool mixed = false)
 {
-    return kind == kWarpGroup ? kRowsLogWarp : (kind == kCtaGroup ? kRowsLogCta : kRowsLogMem);
+    return kind == kWarpGroup ? kRowsLogWarp
+                              : (kind == kCtaGroup ? (mixed ? kRowsLogCtaMixed : kRowsLogCta) : kRowsLogMem);
 }
 
 // Lanes per line (as log2) for the directional solves along an axis with
@@ -160,6 +168,13 @@ AMFRW_HD bool dense_axis(int kind, bool mixed, int M)
     return mixed && kind == kWarpGroup && M >= 2 && M <= kDenseMaxRows;
 }
 
+// Rows of axis 0 get one padding slot each (lines along axis 0 then start in
+// different banks) when they have at least this many nodes.  Mixed-precision
+// CTA groups pad only rows of 4 or more, which keeps a 4096-node grid within
+// half an SM's shared memory (two resident CTAs); the others pad every row of
+// 2 or more.
+AMFRW_HD int pad_rows_min(bool lean) { return lean ? 4 : 2; }
+
 // kind: the work-group kind.  Warp and global-memory groups keep the
 // line-solve factors inside the layout; CTA groups in the group's slice of a
 // global scratch array.  Global-memory groups also get FP64 scratch for the
@@ -176,7 +191,8 @@ AMFRW_HD Layout make_layout(int N, const int8_t* lv, bool mixed, int kind, int t
     }
     const int MV = 1 << lv[N - 1];
     const int M0 = 1 << lv[0];
-    const int pad = M0 > 1 ? 1 : 0;
+    const bool lean = mixed && kind == kCtaGroup;
+    const int pad = M0 >= pad_rows_min(lean) ? 1 : 0;
     y.L = L;
     y.Lp = L + (pad ? (L >> lv[0]) : 0);
     y.Lr = L >> lv[N - 1];
@@ -198,11 +214,12 @@ AMFRW_HD Layout make_layout(int N, const int8_t* lv, bool mixed, int kind, int t
             nlu = (nlu + 3) & ~3;
             nlu += rows << lv[i];
         } else {
-            nlu += rows * lu_row_values(lanes_log(lv[i], llog, tlog, rows_log(kind)));
+            nlu += rows * lu_row_values(lanes_log(lv[i], llog, tlog, rows_log(kind, mixed)));
         }
     }
     const bool lu_in = kind != kCtaGroup;
     y.nlu = nlu;
+    const int sk = mixed ? 4 : 8;  // bytes of a factor value
     int o = 0;
     if (mixed) {
         // The FP64 constants and tables serve the per-grid setup only (tables,
@@ -213,7 +230,7 @@ AMFRW_HD Layout make_layout(int N, const int8_t* lv, bool mixed, int kind, int t
         y.tabf = o; o = align16(o + 4 * y.ntab);
         y.pay = o;  o = align16(o + 8 * y.npay);
         y.lu = o;   o = align16(o + (lu_in ? 4 * y.nlu : 0));
-        y.Z = o;    o = align16(o + 8 * y.Lp);
+        y.Z = o;    o = align16(o + (lean ? 0 : 8 * y.Lp));
         y.ZZ = o;   o = align16(o + 8 * y.Lp);
         y.H = o;    o = align16(o + 4 * y.Lr);
         // warp groups: per node, the drift coefficient of every refined rate
@@ -225,7 +242,7 @@ AMFRW_HD Layout make_layout(int N, const int8_t* lv, bool mixed, int kind, int t
         int a = o, b = o;
         y.cd = a;   a = align16(a + (int)sizeof(Consts<double>));
         y.tabd = a; a = align16(a + 8 * y.ntab);
-        y.FY = b;   b = align16(b + 4 * y.Lp);
+        y.FY = b;   b = align16(b + (lean ? 0 : 4 * y.Lp));
         y.K1 = b;   b = align16(b + 4 * y.Lp);
         y.K0 = b;   b = align16(b + 4 * y.Lp);
         y.Kw = b;   b = align16(b + 4 * y.Lp);
@@ -262,6 +279,16 @@ AMFRW_HD Layout make_layout(int N, const int8_t* lv, bool mixed, int kind, int t
     }
     y.scr = o;  o = align16(o + (kind == kMemGroup ? 3 * 8 * rmax : 0));
     y.total = o;
+    // the global slice of a CTA group: factors, then (mixed) Z and dt F(Y_n)
+    y.gbytes = y.gZ = y.gFY = 0;
+    if (kind == kCtaGroup) {
+        int g = (nlu * sk + 255) & ~255;
+        if (lean) {
+            y.gZ = g;   g += (8 * y.Lp + 255) & ~255;
+            y.gFY = g;  g += (4 * y.Lp + 255) & ~255;
+        }
+        y.gbytes = g;
+    }
     return y;
 }
 

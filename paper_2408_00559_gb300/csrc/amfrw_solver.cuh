@@ -71,7 +71,7 @@ struct Shape {
 
 template <int N>
 __device__ __forceinline__ void make_shape(Shape<N>& s, const int8_t* lv, int tlog, int rlog, bool fold,
-                                           bool fold_v, bool dirichlet, bool dense = false)
+                                           bool fold_v, bool dirichlet, bool dense = false, int padmin = 2)
 {
     int sh = 0;
 #pragma unroll
@@ -85,7 +85,7 @@ __device__ __forceinline__ void make_shape(Shape<N>& s, const int8_t* lv, int tl
     s.dmask = dirichlet ? (1 << (N - 1)) - 1 : 0;
     s.L = 1 << sh;
     s.Lr = s.L >> s.lv[N - 1];
-    s.pad = s.M[0] > 1 ? 1 : 0;
+    s.pad = s.M[0] >= padmin ? 1 : 0;  // (make_layout's rule: pad_rows_min)
     int r = s.M[0] + s.pad;
     s.Sp[0] = 1;
 #pragma unroll
@@ -1191,7 +1191,8 @@ __device__ __forceinline__ void lsweep(const Shape<N>& s, int axis, const T* __r
                                        const T* src, T* dst, int rank, int gsize, unsigned gm,
                                        Epi epi)
 {
-    constexpr int RM = 1 << (KIND == kWarpGroup ? kRowsLogWarp : kRowsLogCta);
+    constexpr int RM = 1 << (KIND == kWarpGroup ? kRowsLogWarp
+                                                : (std::is_same<T, float>::value ? kRowsLogCtaMixed : kRowsLogCta));
     if constexpr (KIND == kMemGroup)
         sweep_mem<N, T>(s, axis, lu, src, dst, rank, gsize, gm, epi);
     else if constexpr (N <= 4)
@@ -1430,7 +1431,7 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
     using TK = typename std::conditional<MIXED, float, double>::type;
     constexpr bool WARP = KIND == kWarpGroup;
     const InstDev& P = a.insts[it.inst];
-    constexpr int RMAX = 1 << (WARP ? kRowsLogWarp : kRowsLogCta);
+    constexpr int RMAX = 1 << (WARP ? kRowsLogWarp : (MIXED ? kRowsLogCtaMixed : kRowsLogCta));
     const int tlog = 31 - __clz(gsize);
     const unsigned gm = WARP ? group_mask(tlog) : 0xffffffffu;
     Shape<N> s;
@@ -1438,7 +1439,11 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
     // groups); into a rate-axis solve only where the register sweep is called
     // out of line (N <= 4), since the epilogue then moves to a runtime axis
     constexpr bool kFoldV = N <= 4 && KIND != kMemGroup;
-    make_shape<N>(s, it.lv, tlog, rows_log(KIND), KIND != kMemGroup, kFoldV, P.bc != 0);
+    // mixed-precision CTA groups keep Z and dt F(Y_n) in their block's global
+    // slice and pad fewer rows, so that two CTAs fit an SM's shared memory
+    constexpr bool LEAN = MIXED && KIND == kCtaGroup;
+    make_shape<N>(s, it.lv, tlog, rows_log(KIND, MIXED), KIND != kMemGroup, kFoldV, P.bc != 0, false,
+                  pad_rows_min(LEAN));
     const int last = kFoldV ? s.last : N - 1;  // the axis whose solve carries the epilogues
     const Layout lay = make_layout(N, it.lv, MIXED, KIND, tlog);
     Consts<double>* cd = reinterpret_cast<Consts<double>*>(base + lay.cd);
@@ -1450,13 +1455,12 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
     // warp groups keep the Thomas factors on chip; a CTA group (grids of more
     // than 64 Inner nodes) keeps them in its block's slice of global scratch,
     // read through L1; a global-memory group has them in its layout
-    TK* lu = KIND != kCtaGroup
-                 ? reinterpret_cast<TK*>(base + lay.lu)
-                 : reinterpret_cast<TK*>(a.lu_scratch + (size_t)blockIdx.x * (size_t)a.lu_stride);
-    double* Z = reinterpret_cast<double*>(base + lay.Z);
+    unsigned char* gslice = a.lu_scratch + (size_t)blockIdx.x * (size_t)a.lu_stride;
+    TK* lu = KIND != kCtaGroup ? reinterpret_cast<TK*>(base + lay.lu) : reinterpret_cast<TK*>(gslice);
+    double* Z = LEAN ? reinterpret_cast<double*>(gslice + lay.gZ) : reinterpret_cast<double*>(base + lay.Z);
     float2* ZZ = reinterpret_cast<float2*>(base + lay.ZZ);
     TK* H = reinterpret_cast<TK*>(base + lay.H);
-    float* FY = reinterpret_cast<float*>(base + lay.FY);
+    float* FY = LEAN ? reinterpret_cast<float*>(gslice + lay.gFY) : reinterpret_cast<float*>(base + lay.FY);
     TK* K1 = reinterpret_cast<TK*>(base + lay.K1);
     TK* K0 = reinterpret_cast<TK*>(base + lay.K0);
     TK* Kw = reinterpret_cast<TK*>(base + lay.Kw);
@@ -1848,14 +1852,14 @@ __device__ void solve_item_mixed(const SolveArgs& a, const Item& it, unsigned ch
 {
     constexpr bool WARP = KIND == kWarpGroup;
     const InstDev& P = a.insts[it.inst];
-    constexpr int RMAX = 1 << (WARP ? kRowsLogWarp : kRowsLogCta);
+    constexpr int RMAX = 1 << (WARP ? kRowsLogWarp : kRowsLogCtaMixed);
     const int tlog = 31 - __clz(gsize);
     const unsigned gm = WARP ? group_mask(tlog) : 0xffffffffu;
     Shape<N>& s = *reinterpret_cast<Shape<N>*>(meta);
     ActAxes& A = *reinterpret_cast<ActAxes*>(meta + shape_bytes(N));
     // single-row solves are folded into another solve (not for global-memory groups)
     if (rank == 0)
-        make_shape<N>(s, it.lv, tlog, rows_log(KIND), KIND != kMemGroup, KIND != kMemGroup, P.bc != 0, WARP);
+        make_shape<N>(s, it.lv, tlog, rows_log(KIND, true), KIND != kMemGroup, KIND != kMemGroup, P.bc != 0, WARP);
     gsync<WARP>(gm);
     const Layout lay = make_layout(N, it.lv, true, KIND, tlog);
     Consts<double>* cd = reinterpret_cast<Consts<double>*>(base + lay.cd);
@@ -2062,7 +2066,7 @@ __device__ void solve_item_mixed(const SolveArgs& a, const Item& it, unsigned ch
 // then moves on, so classes of uneven instances share one launch and no warp
 // waits for another.
 template <int N, bool MIXED, int KIND>
-__global__ void __launch_bounds__(KIND == kWarpGroup ? 128 : kCtaMaxThreads, KIND == kWarpGroup ? (MIXED ? kWarpBlocksMixed : 3) : (KIND == kMemGroup ? 2 : 1)) solve_kernel(SolveArgs a)
+__global__ void __launch_bounds__(KIND == kWarpGroup ? 128 : kCtaMaxThreads, KIND == kWarpGroup ? (MIXED ? kWarpBlocksMixed : 3) : ((KIND == kMemGroup || MIXED) ? 2 : 1)) solve_kernel(SolveArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     if constexpr (KIND == kWarpGroup) {
