@@ -77,6 +77,12 @@ L2_FLUSH_BYTES = 256 << 20
 # one ncu capture, dram__bytes_read.sum 680 448 + 4 588 544 + 12 539 392 and
 # dram__bytes_write.sum 0 + 292 096 + 200 052 224 for N = 4, 6, 8 (the writes:
 # local-memory stack frames of the per-grid setup calls written back from L2).
+# Surrogate fallback calibration: the ensemble spread is scaled so that on a
+# held-out set of solver prices this quantile of the answered queries lies
+# within the 1e-3 bound (the rest fall back to the solver).
+CALIB_Q = 0.999
+CALIB_N = 16384
+
 C4_DRAM_BYTES_PER_BATCH = 680448 + 4588544 + 12539392 + 292096 + 200052224
 
 
@@ -793,7 +799,8 @@ def surrogate_measure(args, L, torch, stream, dev, note):
     train = [W.c5_instance_from(f, **kw) for f in F_train]
     y_train = solve_chunked(train)
     note(f"surrogate: {len(train)} training prices solved")
-    F_audit = W.c5_features(4096, 10_000_000, box=box)
+    # calibration set: large enough that its 0.999 quantile rests on ~16 points
+    F_audit = W.c5_features(CALIB_N, 10_000_000, box=box)
     audit = [W.c5_instance_from(f, **kw) for f in F_audit]
     y_audit = solve_chunked(audit)
     t_data = time.perf_counter() - t0
@@ -802,7 +809,7 @@ def surrogate_measure(args, L, torch, stream, dev, note):
     loss = s.fit(train, y_train, epochs=args.epochs, lr=3e-3)
     t_fit = time.perf_counter() - t0
     note(f"surrogate fit: loss {loss:.2e} in {t_fit:.1f} s")
-    calib = s.calibrate(audit, y_audit, rel_bound=1e-3, quantile=0.99)
+    calib = s.calibrate(audit, y_audit, rel_bound=1e-3, quantile=CALIB_Q)
     del train, audit
 
     # the solver alone on the same family (amfrw_batch, inputs resident, graph replay)
@@ -858,7 +865,7 @@ def surrogate_measure(args, L, torch, stream, dev, note):
                     {"queries": int(m.sum()), "fallback": float(fell_all[m].mean())}
     # accuracy of answered queries: a sample judged by the solver
     p, fell, Fk = p_first
-    idx = np.flatnonzero(~fell)[:2048]
+    idx = np.flatnonzero(~fell)[:8192]
     y_chk = solve_chunked([W.c5_instance_from(f, **kw) for f in Fk[idx]]) if idx.size else np.zeros(0)
     rel = np.abs(p[idx] - y_chk) / np.abs(y_chk) if idx.size else np.zeros(0)
     s.close()
@@ -873,7 +880,7 @@ def surrogate_measure(args, L, torch, stream, dev, note):
             "answered_checked": int(idx.size), "answered_max_rel_err": float(rel.max()) if idx.size else None,
             "answered_within_bound": float(np.mean(rel <= 1e-3)) if idx.size else None,
             "answered_median_rel_err": float(np.median(rel)) if idx.size else None,
-            "rel_bound": 1e-3, "calib_quantile": 0.99, "calibration": calib,
+            "rel_bound": 1e-3, "calib_quantile": CALIB_Q, "calibration_points": CALIB_N, "calibration": calib,
             "train": args.train, "epochs": args.epochs, "members": args.members, "train_loss": loss,
             "data_generation_s": t_data, "fit_s": t_fit, "serve_s": dt,
             "e2e_bytes": {"h2d_per_query": 8 * 4, "d2h_per_query": 12}}
@@ -902,7 +909,7 @@ def run_surrogate(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (network) + f32/f64 (fallback solver)",
         "data": "synthetic",
         "config": {"workload": C5_DESC, "queries_per_step": r["queries_per_step"], "train": args.train,
-                   "epochs": args.epochs, "members": args.members, "rel_bound": 1e-3, "calib_quantile": 0.99,
+                   "epochs": args.epochs, "members": args.members, "rel_bound": 1e-3, "calib_quantile": CALIB_Q,
                    "l2": "queries stream from host memory; every chunk is new data"},
         "surrogate": r,
         "e2e": {"value": r["value"], "unit": "queries/s", "h2d_bytes_per_step": r["queries_per_step"] * 8 * 4,
