@@ -44,6 +44,7 @@ CASES = [
     (6, 2, 1, False, "mixed", False, "swaption"),
     (8, 3, 0, False, "mixed", False, "swaption"),
     (4, 7, 0, False, "fp64", False, "swaption"),  # grids beyond 64 nodes: whole-block groups
+    (4, 7, 0, False, "mixed", False, "swaption"),  # the same in mixed precision (Z in the block's global slice)
 ]
 
 

@@ -146,6 +146,25 @@ def test_step_is_resumable():
     assert abs(a.combine() - b.combine()) <= 1e-14 * max(1.0, abs(a.combine()))
 
 
+@pytest.mark.parametrize("case", [(4, 3), (4, 7)], ids=["warp_groups", "cta_groups"])
+def test_mixed_step_is_resumable(case):
+    """Mixed precision across amfrw_step calls: the state keeps Y in FP64 and
+    the next call rebuilds Z and its float pair from it (CTA groups keep Z in
+    their block's global slice), so the split run follows the uninterrupted
+    one to far below the mode's FP32 rounding."""
+    N, n = case
+    inst = W.small_instance(N, n, steps=8, seed=13, precision="mixed")
+    a = B.Problem(inst)
+    a.step(8)
+    b = B.Problem(inst)
+    b.step(3)
+    b.step(5)
+    pa, pb = a.combine(), b.combine()
+    assert abs(pa - pb) <= 1e-9 * abs(pa), (pa, pb)
+    po = O.price(inst, n, 0)
+    assert abs(pb - po) <= TOLMIX_PRICE * abs(po), (pb, po)
+
+
 def test_batch_equals_single_problems_and_is_deterministic():
     insts = W.batch("c2", 6)
     p1 = B.solve_batch(insts)
