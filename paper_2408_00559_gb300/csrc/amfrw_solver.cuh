@@ -1837,29 +1837,30 @@ __device__ __forceinline__ void stencil_act2(const ActAxes& A, const float* __re
 }
 
 
-// One grid in mixed precision: the F evaluations and line solves in FP32 on
-// the increments, Z accumulated in FP64 beside its hi/lo float pair, F of the
-// payoff (H), the interpolation and the state in FP64.  Each step runs four
-// phases, each one F evaluation followed by the directional solves:
-//   0: K0 = dt F(Y_n) (kept as FY),            solves K0 -> Kw
-//   1: K0 = 2 K0 - Kw + theta dt F_0(Kw),      solves K0 -> K1
-//   2: K0 = FY + a21 dt F_0(K1) + q21 K1,      solves K0 -> Kw
-//   3: K0 = 2 K0 - Kw + theta dt F_0(Kw),      solves K0 in place, then
-//      Y_{n+1} = Y_n + b1 K1 + b2 K2 in the epilogue of the last solve.
+// One grid of a mixed-precision warp group: the F evaluations and line
+// solves in FP32 on the increments, Z accumulated in FP64 beside its hi/lo
+// float pair, F of the payoff (H), the interpolation and the state in FP64.
+// Each step runs four phases, each one F evaluation (right-hand side r)
+// followed by the directional solves of r:
+//   0: r = dt F(Y_n) (kept as FY),              solved into Kw
+//   1: r = 2 FY - Kw + theta dt F_0(Kw),        solved into K1
+//   2: r = FY + a21 dt F_0(K1) + q21 K1 (kept in K0), solved into Kw
+//   3: r = 2 K0 - Kw + theta dt F_0(Kw),        solved into K0, then
+//      Y_{n+1} = Y_n + b1 K1 + b2 K2 (eq. coef_W2).
 template <int N, int KIND>
 __device__ void solve_item_mixed(const SolveArgs& a, const Item& it, unsigned char* base, unsigned char* meta,
                                  int rank, int gsize)
 {
-    constexpr bool WARP = KIND == kWarpGroup;
+    static_assert(KIND == kWarpGroup, "the register-resident phases need at most two nodes per lane");
+    constexpr bool WARP = true;
     const InstDev& P = a.insts[it.inst];
     constexpr int RMAX = 1 << (WARP ? kRowsLogWarp : kRowsLogCtaMixed);
     const int tlog = 31 - __clz(gsize);
     const unsigned gm = WARP ? group_mask(tlog) : 0xffffffffu;
     Shape<N>& s = *reinterpret_cast<Shape<N>*>(meta);
     ActAxes& A = *reinterpret_cast<ActAxes*>(meta + shape_bytes(N));
-    // single-row solves are folded into another solve (not for global-memory groups)
-    if (rank == 0)
-        make_shape<N>(s, it.lv, tlog, rows_log(KIND, true), KIND != kMemGroup, KIND != kMemGroup, P.bc != 0, WARP);
+    // single-row solves are folded into another solve
+    if (rank == 0) make_shape<N>(s, it.lv, tlog, rows_log(KIND, true), true, true, P.bc != 0, true);
     gsync<WARP>(gm);
     const Layout lay = make_layout(N, it.lv, true, KIND, tlog);
     Consts<double>* cd = reinterpret_cast<Consts<double>*>(base + lay.cd);
@@ -1867,9 +1868,7 @@ __device__ void solve_item_mixed(const SolveArgs& a, const Item& it, unsigned ch
     double* tabd = reinterpret_cast<double*>(base + lay.tabd);
     float* tabk = reinterpret_cast<float*>(base + lay.tabf);
     double* pay = reinterpret_cast<double*>(base + lay.pay);
-    float* lu = KIND != kCtaGroup
-                    ? reinterpret_cast<float*>(base + lay.lu)
-                    : reinterpret_cast<float*>(a.lu_scratch + (size_t)blockIdx.x * (size_t)a.lu_stride);
+    float* lu = reinterpret_cast<float*>(base + lay.lu);
     double* Z = reinterpret_cast<double*>(base + lay.Z);
     float2* ZZ = reinterpret_cast<float2*>(base + lay.ZZ);
     float* H = reinterpret_cast<float*>(base + lay.H);
@@ -1883,12 +1882,8 @@ __device__ void solve_item_mixed(const SolveArgs& a, const Item& it, unsigned ch
     gsync<WARP>(gm);
     for (int q = rank; q < lay.ntab; q += gsize) tabk[q] = (float)tabd[q];
     if (rank == 0) convert_consts<float>(*cd, ck);
-    if constexpr (KIND == kMemGroup) {
-        pcr_setup_mem<N, float>(s, tabd, *cd, lu, reinterpret_cast<double*>(base + lay.scr), rank, gsize, gm);
-    } else {
-        pcr_setup<N, float, RMAX, float>(s, tabd, *cd, lu, rank, gsize, gm);
-        dense_setup<N>(s, tabd, *cd, lu, rank, gsize);
-    }
+    pcr_setup<N, float, RMAX, float>(s, tabd, *cd, lu, rank, gsize, gm);
+    dense_setup<N>(s, tabd, *cd, lu, rank, gsize);
     gsync<WARP>(gm);  // the FP32 tables and constants are complete
     // 2. H = F(G)/V^2 on the rate grid (payoff differences in FP64), Z from the state or zero
     for (int tr = rank; tr < s.Lr; tr += gsize) {
