@@ -1391,15 +1391,20 @@ __device__ __forceinline__ void interp_spot(const Shape<N>& s, const InstDev& P,
             }
         }
         const int j0l = c[0] + (rank & 1);  // the caplet's rate index when axis 0 is a lane bit
+        // When V's bit is one the lane loops over, the two V corners of a
+        // rate corner share its payoff (g does not depend on V): the loop
+        // runs over the rate bits and visits both V corners inside.
+        const bool vloop = N - 1 >= lb;
+        const int nbits = vloop ? N - 1 : N;
         double u = 0.0;
-        for (int corner = rank; corner < (1 << N); corner += il) {
+        for (int corner = rank; corner < (1 << nbits); corner += il) {
             double wt = wl, Pc = Pl, Sc = Sl;
             int t = tl;
             bool outer = ol;
             int j0 = j0l;
 #pragma unroll
             for (int i = 0; i < N; ++i) {
-                if (i >= lb) {
+                if (i >= lb && i < nbits) {
                     const int bit = (corner >> i) & 1;
                     const int jj = c[i] + bit;
                     wt *= bit ? w[i] : 1.0 - w[i];
@@ -1412,10 +1417,21 @@ __device__ __forceinline__ void interp_spot(const Shape<N>& s, const InstDev& P,
                     }
                 }
             }
-            if (wt == 0.0) continue;
-            const double zv = outer ? 0.0 : Z[s.padded(t)];
             const double g = (P.payoff == 0) ? fmax(pay[s.poff[0] + j0], 0.0) : fmax(Sc, 0.0);
-            u += wt * (g + zv);
+            if (!vloop) {
+                if (wt == 0.0) continue;
+                const double zv = outer ? 0.0 : Z[s.padded(t)];
+                u += wt * (g + zv);
+                continue;
+            }
+#pragma unroll
+            for (int bit = 0; bit < 2; ++bit) {
+                const int jj = c[N - 1] + bit;
+                const double wv = wt * (bit ? w[N - 1] : 1.0 - w[N - 1]);
+                if (wv == 0.0) continue;
+                const double zv = (outer || jj == 0) ? 0.0 : Z[s.padded(t + ((jj - 1) << s.sh[N - 1]))];
+                u += wv * (g + zv);
+            }
         }
         const unsigned im = WARP ? gm : 0xffffffffu;
         for (int off = il >> 1; off > 0; off >>= 1) u += __shfl_xor_sync(im, u, off, il);
