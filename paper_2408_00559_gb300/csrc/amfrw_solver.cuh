@@ -419,6 +419,10 @@ __device__ __noinline__ float payoff_H_fast(const Shape<N>& s, const double* pay
     float acc = 0.f;
 #pragma unroll
     for (int i = 0; i < n; ++i) acc += tab[s.toff[i] + j[i] - 1] * lap[i];
+    int kend = -1;  // the last rate off its upper face: no cross term lies beyond it
+#pragma unroll
+    for (int k = 0; k < n; ++k)
+        if (j[k] != s.nf[k]) kend = k;
 #pragma unroll
     for (int i = 0; i < n; ++i) {
         float inner = 0.f;
@@ -427,6 +431,7 @@ __device__ __noinline__ float payoff_H_fast(const Shape<N>& s, const double* pay
             double Q = 1.0, U = 0.0;  // Q_ik, U_ik for the current k
 #pragma unroll
             for (int k = i + 1; k < n; ++k) {
+                if (k > kend) break;
                 if (j[k] != s.nf[k]) {
                     const int ok = s.poff[k] + j[k];
                     const double wp = U + Q * Bv[ok + 1] * (A[ok + 1] + T[k + 1]);
@@ -1231,7 +1236,7 @@ __device__ void build_tables(const Shape<N>& s, const InstDev& P, double* tabd, 
     for (int w = rank; w < nrate + MV; w += gsize) {
         if (w >= nrate) {
             const int jj = w - nrate + 1;
-            const double V = (double)jj * (P.Fmax[N - 1] / (double)MV);
+            const double V = (double)jj * (P.Fmax[N - 1] * pow2(-s.lv[N - 1]));  // h_V = Vmax / M_V exactly
             tabd[s.toff[N - 1] + jj - 1] = V * V;
             continue;
         }
@@ -1241,7 +1246,7 @@ __device__ void build_tables(const Shape<N>& s, const InstDev& P, double* tabd, 
             ++a;
         }
         const int M = s.M[a];
-        const double h = P.Fmax[a] / (double)M;
+        const double h = P.Fmax[a] * pow2(-s.lv[a]);  // Fmax / M exactly (M = 2^lv)
         const double al = P.alpha[a], ta = P.tau[a];
         const double F = (double)jj * h;
         const double bF = 1.0 / (1.0 + ta * F);  // discount factor of the accrual period
@@ -1291,18 +1296,25 @@ __device__ void build_tables(const Shape<N>& s, const InstDev& P, double* tabd, 
     }
 }
 
+// The FP32 (or FP64) copy of the constants, one entry per lane at a time.
 template <typename T>
-__device__ void convert_consts(const Consts<double>& a, Consts<T>* b)
+__device__ void convert_consts(const Consts<double>& a, Consts<T>* b, int rank, int gsize)
 {
-    b->cV = (T)a.cV;
-    b->dt = (T)a.dt;
-    b->thdt = (T)a.thdt;
-    b->nudt = (T)a.nudt;
-    for (int q = 0; q < kMaxDim * (kMaxDim - 1) / 2; ++q) b->rm[q] = (T)a.rm[q];
-    for (int q = 0; q < kMaxDim * (kMaxDim + 1) / 2; ++q) b->rh[q] = (T)a.rh[q];
-    for (int i = 0; i < kMaxDim; ++i) {
-        b->sm[i] = (T)a.sm[i];
-        b->g2[i] = (T)a.g2[i];
+    constexpr int kP = kMaxDim * (kMaxDim - 1) / 2, kT = kMaxDim * (kMaxDim + 1) / 2;
+    for (int q = rank; q < 4 + kP + kT + 2 * kMaxDim; q += gsize) {
+        if (q < 4) {
+            const double v = q == 0 ? a.cV : (q == 1 ? a.dt : (q == 2 ? a.thdt : a.nudt));
+            T& o = q == 0 ? b->cV : (q == 1 ? b->dt : (q == 2 ? b->thdt : b->nudt));
+            o = (T)v;
+        } else if (q < 4 + kP) {
+            b->rm[q - 4] = (T)a.rm[q - 4];
+        } else if (q < 4 + kP + kT) {
+            b->rh[q - 4 - kP] = (T)a.rh[q - 4 - kP];
+        } else if (q < 4 + kP + kT + kMaxDim) {
+            b->sm[q - 4 - kP - kT] = (T)a.sm[q - 4 - kP - kT];
+        } else {
+            b->g2[q - 4 - kP - kT - kMaxDim] = (T)a.g2[q - 4 - kP - kT - kMaxDim];
+        }
     }
 }
 
@@ -1491,7 +1503,7 @@ __device__ void solve_item(const SolveArgs& a, const Item& it, unsigned char* ba
     gsync<WARP>(gm);
     if constexpr (MIXED) {
         for (int q = rank; q < lay.ntab; q += gsize) tabk[q] = (TK)tabd[q];
-        if (rank == 0) convert_consts<TK>(*cd, ck);
+        convert_consts<TK>(*cd, ck, rank, gsize);
     }
     if constexpr (KIND == kMemGroup) {
         gsync<WARP>(gm);
@@ -1897,7 +1909,7 @@ __device__ void solve_item_mixed(const SolveArgs& a, const Item& it, unsigned ch
     build_tables<N>(s, P, tabd, pay, cd, rank, gsize);
     gsync<WARP>(gm);
     for (int q = rank; q < lay.ntab; q += gsize) tabk[q] = (float)tabd[q];
-    if (rank == 0) convert_consts<float>(*cd, ck);
+    convert_consts<float>(*cd, ck, rank, gsize);
     pcr_setup<N, float, RMAX, float>(s, tabd, *cd, lu, rank, gsize, gm);
     dense_setup<N>(s, tabd, *cd, lu, rank, gsize);
     gsync<WARP>(gm);  // the FP32 tables and constants are complete
