@@ -94,13 +94,17 @@ struct ActAxes {
     int n;                      // active axes, ascending axis order
     int nr;                     // active rate axes (the first nr of them; V, if active, is last)
     float cinact;               // second-difference coefficients of the inactive axes, summed
-    int pad;
+    int ns;                     // directional solves of a stage (the axes not folded into another)
     ActAxis rec[kMaxDim];
     int ax[kMaxDim];            // the axis index
     float g2[kMaxDim];          // 1 / (2 h) (drift gradient)
     float sconst[kMaxDim];      // drift sum: the part of the inactive rates
     float cx[kMaxDim][kMaxDim]; // pair (q, r), q < r: rho/(4 h h) (two rates) or sigma phi/(4 h h_V)
     float drh[kMaxDim][kMaxDim];// drift of active rate q: rho for the active rates r <= q
+    // the solves in ascending axis order, read as one 8-byte load each:
+    // [2q] offset of the axis's factors; [2q + 1] sh | M << 8 | axis << 16 |
+    // (rate axis) << 24 | (solved by its explicit inverse) << 25
+    alignas(8) int sv[2 * kMaxDim];
 };
 
 // Per-grid descriptors the mixed-precision solver keeps in shared memory:

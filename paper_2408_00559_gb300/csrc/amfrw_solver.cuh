@@ -1778,6 +1778,15 @@ __device__ void build_act(const Shape<N>& s, const Consts<float>& c, const float
         }
         A.sconst[q] = sc;
     }
+    int ns = 0;
+    for (int i = 0; i < N; ++i) {
+        if ((s.skip >> i) & 1) continue;  // folded into the solve along s.last
+        A.sv[2 * ns] = s.luoff[i];
+        A.sv[2 * ns + 1] = s.sh[i] | (s.M[i] << 8) | (i << 16) | ((i < N - 1 ? 1 : 0) << 24) |
+                           (((s.dense >> i) & 1) << 25);
+        ++ns;
+    }
+    A.ns = ns;
 }
 
 // Sketch 1 divided by V^2 at two nodes of a lane at once (t[0], t[1];
@@ -2019,10 +2028,11 @@ __device__ void solve_item_mixed(const SolveArgs& a, const Item& it, unsigned ch
             // through shared memory, in place in the phase's target
             float* dst = (ph == 1) ? K1 : (ph == 3 ? K0 : Kw);
             bool in_smem = false;  // the values live in dst, not in x
+            const int ns = A.ns;
 #pragma unroll 1
-            for (int ax = 0; ax < N; ++ax) {
-                if ((s.skip >> ax) & 1) continue;
-                if ((s.dense >> ax) & 1) {
+            for (int q = 0; q < ns; ++q) {
+                const int2 e = reinterpret_cast<const int2*>(A.sv)[q];
+                if ((e.y >> 25) & 1) {
                     if (in_smem) {
 #pragma unroll
                         for (int k = 0; k < 2; ++k) {
@@ -2031,9 +2041,9 @@ __device__ void solve_item_mixed(const SolveArgs& a, const Item& it, unsigned ch
                         }
                         in_smem = false;
                     }
-                    const float* C = lu + s.luoff[ax];
-                    const int sha = s.sh[ax], Ma = s.M[ax];
-                    const bool rate = ax < N - 1;
+                    const float* C = lu + e.x;
+                    const int sha = e.y & 0xff, Ma = (e.y >> 8) & 0xff;
+                    const bool rate = (e.y >> 24) & 1;
                     if (Ma == 2) dense_mix<2>(C, sha, shV, mV, rate, rank, gsize, tlog, two, gm, x);
                     else if (Ma == 4) dense_mix<4>(C, sha, shV, mV, rate, rank, gsize, tlog, two, gm, x);
                     else dense_mix<8>(C, sha, shV, mV, rate, rank, gsize, tlog, two, gm, x);
@@ -2047,7 +2057,7 @@ __device__ void solve_item_mixed(const SolveArgs& a, const Item& it, unsigned ch
                         gsync<WARP>(gm);
                         in_smem = true;
                     }
-                    sweep<N, float, RMAX>(s, ax, lu, dst, dst, rank, gsize, gm, NoEpi());
+                    sweep<N, float, RMAX>(s, (e.y >> 16) & 0xff, lu, dst, dst, rank, gsize, gm, NoEpi());
                     gsync<WARP>(gm);
                 }
             }
