@@ -1977,23 +1977,29 @@ __device__ void solve_item_mixed(const SolveArgs& a, const Item& it, unsigned ch
     // t = rank + gsize (a warp group has at least half as many lanes as its
     // grid has nodes: the host sizes it so).
     const bool two = L > gsize;
+    // The lane's nodes are fixed for the whole time loop: slot k holds node
+    // rank + k gsize when that is below L (its padded index Jo[k], else -1).
+    // The stencil evaluates a slot that is unused or holds Dirichlet data
+    // (eq. bound1_0: its far neighbour is not stored) as node 0 (always Inner
+    // when any node is) and discards the result.
+    int t[2], J[2], Jo[2];
+    bool use[2];
+    float vv[2];  // V^2 of the slot's node
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int tk = rank + k * gsize;
+        const bool in = tk < L;
+        use[k] = in && !dirichlet_node(s, tk);
+        t[k] = use[k] ? tk : 0;
+        J[k] = s.padded(t[k]);
+        Jo[k] = in ? s.padded(tk) : -1;
+        vv[k] = in ? v2[(tk >> shV) & mV] : 0.f;
+    }
+    const bool eval = (use[0] || use[1]) && !all_dir;
     for (int n = 0; n < a.steps; ++n) {
 #pragma unroll 1
         for (int ph = 0; ph < 4; ++ph) {
-            // the stencil for both nodes at once; a node that is unused or
-            // holds Dirichlet data (eq. bound1_0: its far neighbour is not
-            // stored) is evaluated as node 0 (always Inner when any node is)
-            // and discarded
-            int t[2] = {rank, rank + gsize};
-            bool use[2];
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                use[k] = t[k] < L && !dirichlet_node(s, t[k]);
-                if (!use[k]) t[k] = 0;
-            }
-            int J[2] = {s.padded(t[0]), s.padded(t[1])};
             float acc[2];
-            const bool eval = (use[0] || use[1]) && !all_dir;
             acc[0] = acc[1] = 0.f;
             if (eval) {
                 if (ph == 0) stencil_act2(A, tabk, cV, t, J, DFSrc{ZZ}, acc, DR, Lp);
@@ -2005,21 +2011,19 @@ __device__ void solve_item_mixed(const SolveArgs& a, const Item& it, unsigned ch
             float x[2];
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
-                const int tk = rank + k * gsize;
                 x[k] = 0.f;
-                if (tk >= L || !use[k]) continue;
+                if (!use[k]) continue;
                 const int Jk = J[k];
-                const float vv = v2[(tk >> shV) & mV];
                 if (ph == 0) {
-                    x[k] = dt * vv * (H[tk & Lr1] + acc[k]);
+                    x[k] = dt * vv[k] * (H[t[k] & Lr1] + acc[k]);
                     FY[Jk] = x[k];
                 } else if (ph == 1) {
-                    x[k] = 2.f * FY[Jk] - Kw[Jk] + thdt * vv * acc[k];
+                    x[k] = 2.f * FY[Jk] - Kw[Jk] + thdt * vv[k] * acc[k];
                 } else if (ph == 2) {
-                    x[k] = FY[Jk] + a21dt * vv * acc[k] + (float)kQ21 * K1[Jk];
+                    x[k] = FY[Jk] + a21dt * vv[k] * acc[k] + (float)kQ21 * K1[Jk];
                     K0[Jk] = x[k];
                 } else {
-                    x[k] = 2.f * K0[Jk] - Kw[Jk] + thdt * vv * acc[k];
+                    x[k] = 2.f * K0[Jk] - Kw[Jk] + thdt * vv[k] * acc[k];
                 }
             }
             // directional solves in ascending axis order (single-row axes
@@ -2035,10 +2039,8 @@ __device__ void solve_item_mixed(const SolveArgs& a, const Item& it, unsigned ch
                 if ((e.y >> 25) & 1) {
                     if (in_smem) {
 #pragma unroll
-                        for (int k = 0; k < 2; ++k) {
-                            const int tk = rank + k * gsize;
-                            if (tk < L) x[k] = dst[s.padded(tk)];
-                        }
+                        for (int k = 0; k < 2; ++k)
+                            if (Jo[k] >= 0) x[k] = dst[Jo[k]];
                         in_smem = false;
                     }
                     const float* C = lu + e.x;
@@ -2050,10 +2052,8 @@ __device__ void solve_item_mixed(const SolveArgs& a, const Item& it, unsigned ch
                 } else {
                     if (!in_smem) {
 #pragma unroll
-                        for (int k = 0; k < 2; ++k) {
-                            const int tk = rank + k * gsize;
-                            if (tk < L) dst[s.padded(tk)] = x[k];
-                        }
+                        for (int k = 0; k < 2; ++k)
+                            if (Jo[k] >= 0) dst[Jo[k]] = x[k];
                         gsync<WARP>(gm);
                         in_smem = true;
                     }
@@ -2065,9 +2065,8 @@ __device__ void solve_item_mixed(const SolveArgs& a, const Item& it, unsigned ch
             // Z_{n+1} = Z_n + b1 k1 + b2 k2 (FP64 and its float-float copy)
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
-                const int tk = rank + k * gsize;
-                if (tk >= L) continue;
-                const int Jk = s.padded(tk);
+                const int Jk = Jo[k];
+                if (Jk < 0) continue;
                 const float xk = in_smem ? dst[Jk] : x[k];
                 if (!in_smem) dst[Jk] = xk;
                 if (ph == 3) {
