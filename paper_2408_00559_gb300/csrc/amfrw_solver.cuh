@@ -428,6 +428,10 @@ __device__ __noinline__ float payoff_H_fast(const Shape<N>& s, const double* pay
         float inner = 0.f;
         if (j[i] != s.nf[i]) {
             const int oi = s.poff[i] + j[i];
+            // a corner's payoff is S0[i] + c (a_i' + w) with c = P0[i] b_i' of
+            // rate i's neighbour row: S0[i] + c a_i' is formed once per rate i
+            const double cp = P0[i] * Bv[oi + 1], cm = P0[i] * Bv[oi - 1];
+            const double sp = fma(cp, A[oi + 1], S0[i]), sm = fma(cm, A[oi - 1], S0[i]);
             double Q = 1.0, U = 0.0;  // Q_ik, U_ik for the current k
 #pragma unroll
             for (int k = i + 1; k < n; ++k) {
@@ -436,11 +440,10 @@ __device__ __noinline__ float payoff_H_fast(const Shape<N>& s, const double* pay
                     const int ok = s.poff[k] + j[k];
                     const double wp = U + Q * Bv[ok + 1] * (A[ok + 1] + T[k + 1]);
                     const double wm = U + Q * Bv[ok - 1] * (A[ok - 1] + T[k + 1]);
-                    const double cp = P0[i] * Bv[oi + 1], cm = P0[i] * Bv[oi - 1];
-                    const double pp = fmax(fma(cp, A[oi + 1] + wp, S0[i]), 0.0);
-                    const double pm = fmax(fma(cp, A[oi + 1] + wm, S0[i]), 0.0);
-                    const double mp = fmax(fma(cm, A[oi - 1] + wp, S0[i]), 0.0);
-                    const double mm = fmax(fma(cm, A[oi - 1] + wm, S0[i]), 0.0);
+                    const double pp = fmax(fma(cp, wp, sp), 0.0);
+                    const double pm = fmax(fma(cp, wm, sp), 0.0);
+                    const double mp = fmax(fma(cm, wp, sm), 0.0);
+                    const double mm = fmax(fma(cm, wm, sm), 0.0);
                     const float mix = (float)((pp - pm) - (mp - mm));
                     inner += c.rm[upair(i, k)] * tab[s.toff[k] + s.M[k] + j[k] - 1] * mix;
                 }
@@ -1223,7 +1226,11 @@ __device__ __forceinline__ double pow2(int e) { return __longlong_as_double((lon
 // entries of all axes are spread over the group's lanes at once (an entry
 // divides once and takes a square root), and each constant is the instance's
 // level-free factor times an exact power of two (no division per grid).
-template <int N>
+// F32ROOT: F^beta (beta = 1/2) by an FP32 square root, for the mixed
+// precision mode, whose coefficient tables feed FP32 arithmetic only (the
+// stencil, the drift and the line-solve factors, formed from FP32-accurate
+// rows); the payoff tables stay FP64.
+template <int N, bool F32ROOT = false>
 __device__ void build_tables(const Shape<N>& s, const InstDev& P, double* tabd, double* pay,
                              Consts<double>* cd, int rank, int gsize)
 {
@@ -1254,7 +1261,7 @@ __device__ void build_tables(const Shape<N>& s, const InstDev& P, double* tabd, 
         pay[s.phalf + s.poff[a] + jj] = bF;
         if (jj >= 1) {
             const double dcoef = P.dcb[a] * pow2(2 * s.lv[a]);  // alpha^2 rho_aa / (2 h^2)
-            const double Fb = half ? sqrt(F) : pow(F, beta);
+            const double Fb = half ? (F32ROOT ? (double)sqrtf((float)F) : sqrt(F)) : pow(F, beta);
             const double F2b = half ? F : pow(F, 2.0 * beta);
             tabd[s.toff[a] + jj - 1] = dcoef * F2b;
             tabd[s.toff[a] + M + jj - 1] = al * Fb;
@@ -1436,13 +1443,17 @@ __device__ __forceinline__ void interp_spot(const Shape<N>& s, const InstDev& P,
                 u += wt * (g + zv);
                 continue;
             }
+            // the V weights of a rate corner sum to its weight wt; Z is 0 on
+            // Outer nodes, so only a corner whose rate indices are all Inner
+            // reads it
+            u = fma(wt, g, u);
+            if (outer) continue;
 #pragma unroll
             for (int bit = 0; bit < 2; ++bit) {
                 const int jj = c[N - 1] + bit;
                 const double wv = wt * (bit ? w[N - 1] : 1.0 - w[N - 1]);
-                if (wv == 0.0) continue;
-                const double zv = (outer || jj == 0) ? 0.0 : Z[s.padded(t + ((jj - 1) << s.sh[N - 1]))];
-                u += wv * (g + zv);
+                if (wv == 0.0 || jj == 0) continue;
+                u = fma(wv, Z[s.padded(t + ((jj - 1) << s.sh[N - 1]))], u);
             }
         }
         const unsigned im = WARP ? gm : 0xffffffffu;
@@ -1915,7 +1926,7 @@ __device__ void solve_item_mixed(const SolveArgs& a, const Item& it, unsigned ch
     float* Kw = reinterpret_cast<float*>(base + lay.Kw);
 
     // 1. coefficient and payoff tables, constants, line-solve factors
-    build_tables<N>(s, P, tabd, pay, cd, rank, gsize);
+    build_tables<N, true>(s, P, tabd, pay, cd, rank, gsize);
     gsync<WARP>(gm);
     for (int q = rank; q < lay.ntab; q += gsize) tabk[q] = (float)tabd[q];
     convert_consts<float>(*cd, ck, rank, gsize);
