@@ -83,7 +83,7 @@ L2_FLUSH_BYTES = 256 << 20
 CALIB_Q = 0.999
 CALIB_N = 16384
 
-C4_DRAM_BYTES_PER_BATCH = 634624 + 6045696 + 16341504 + 1508864 + 275719424
+C4_DRAM_BYTES_PER_BATCH = 804096 + 5778176 + 13012480 + 292864 + 276690432
 
 
 def parse():
