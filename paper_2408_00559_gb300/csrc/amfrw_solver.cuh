@@ -1368,7 +1368,8 @@ __device__ __forceinline__ void sweeps_into(const Shape<N>& s, const TK* lu, con
 // Multilinear interpolation at the spot x* = (F_1(0), ..., V0) of Y = G + Z
 // (Sec. 5.1).  The 2^N corners of the containing cell are shared among up to
 // 32 lanes of the group (a whole warp group, or the first warp of a CTA),
-// which sum them by a shuffle reduction; corners of weight zero are skipped.
+// which sum them by a shuffle reduction.  Z, zero on Outer nodes, is read
+// only at corners of nonzero weight whose every index is Inner.
 template <int N, bool WARP>
 __device__ __forceinline__ void interp_spot(const Shape<N>& s, const InstDev& P, const double* pay,
                                             const double* Z, double* u_out, int rank, int gsize, unsigned gm)
