@@ -72,17 +72,17 @@ WORKLOADS = {
     "c3": dict(desc=C3_DESC, dtype="f32+f64", batch=4, mixed=True),
 }
 L2_FLUSH_BYTES = 256 << 20
-# DRAM bytes (read + write) of the solver launches of one 256-instance batched
-# mixed-precision batch in its multi-class configuration (one launch per N):
-# one ncu capture, dram__bytes_read.sum 680 448 + 4 588 544 + 12 539 392 and
-# dram__bytes_write.sum 0 + 292 096 + 200 052 224 for N = 4, 6, 8 (the writes:
-# local-memory stack frames of the per-grid setup calls written back from L2).
 # Surrogate fallback calibration: the ensemble spread is scaled so that on a
 # held-out set of solver prices this quantile of the answered queries lies
 # within the 1e-3 bound (the rest fall back to the solver).
 CALIB_Q = 0.999
 CALIB_N = 16384
 
+# DRAM bytes (read + write) of the solver launches of one 256-instance batched
+# mixed-precision batch in its multi-class configuration (one launch per N):
+# one ncu capture, dram__bytes_read.sum 804 096 + 5 778 176 + 13 012 480 and
+# dram__bytes_write.sum 0 + 292 864 + 276 690 432 for N = 4, 6, 8 (the writes:
+# local-memory stack frames of the per-grid setup calls written back from L2).
 C4_DRAM_BYTES_PER_BATCH = 804096 + 5778176 + 13012480 + 292864 + 276690432
 
 
