@@ -4,14 +4,14 @@ afford cudaMalloc/cudaFree and the device-wide synchronisation of a free).
 
 It must price exactly like amfrw_solve_batch, the allocating entry point, and
 keep doing so on a second call in a row, because every call reuses the same
-fixed device array and inherits the previous call's contents.  Two problem
-sets are used: d=4 level-5 swaptions (grids solved one per warp) and the
-65x65 full grid in FP64 (solved by a whole block, whose line-solve factors
-live in the fixed array), a small d=6 modified problem in mixed precision,
-and the largest problem the header promises to fit: one d=6 (5 rates + V)
-modified psi=1 level-6 instance in mixed precision (923 grids of up to 4096
-Inner nodes, solved by whole blocks with their factors in the array).  This
-file is collected last on purpose.
+fixed device array and inherits the previous call's contents.  Four problem
+sets are used: d=4 level-5 swaptions (grids solved one per warp), the 65x65
+full grid in FP64 (solved by a whole block, whose line-solve factors live in
+the fixed array), a small d=6 modified problem in mixed precision, and the
+largest problem the header promises to fit: one d=6 (5 rates + V) modified
+psi=1 level-6 instance in mixed precision (923 grids of up to 4096 Inner
+nodes, solved by whole blocks with their factors in the array).  This file is
+collected last on purpose.
 """
 import numpy as np
 import pytest
